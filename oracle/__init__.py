@@ -1,0 +1,215 @@
+"""FSZ CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+ctypes wrapper around ``fsz_oracle.cpp``, a plain single-threaded C++
+restatement of the FSZ stream (arXiv 2607.15413). Only the tests, the smoke
+check and the benchmark's CPU-baseline leg may import this package; the
+product path (the CUDA library and its binding) never does.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fsz_oracle.cpp")
+_HDR = os.path.join(_HERE, "fsz_oracle.h")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "libfsz_oracle.so")
+
+ABS, REL = 0, 1
+LZ1, LZ2, LZ1C, LZ2C = 0, 1, 2, 3
+OK, ERR_INVALID_ARG, ERR_NONFINITE, ERR_EB_TOO_SMALL, ERR_CAPACITY, ERR_CORRUPT = 0, 1, 3, 4, 5, 6
+
+# -ffp-contract=off keeps every float32 multiply and add a separate IEEE
+# operation (GCC contracts to FMA by default on aarch64).
+CFLAGS = ["-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+          "-Wall", "-Wextra"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/_lib (idempotent)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["g++", *CFLAGS, "-o", tmp, _SRC], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("eb", ctypes.c_double), ("eb_eff", ctypes.c_double), ("K", ctypes.c_double),
+                ("Q", ctypes.c_uint32), ("e", ctypes.c_float), ("s", ctypes.c_float),
+                ("r", ctypes.c_float)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            P, u64, i32, u32, f32, f64 = (ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32,
+                                          ctypes.c_uint32, ctypes.c_float, ctypes.c_double)
+            L.fszo_stats.argtypes = [P, u64, P, P, P]
+            L.fszo_params.argtypes = [ctypes.c_int, f64, f32, f32, ctypes.c_int, u64,
+                                      ctypes.POINTER(Params)]
+            L.fszo_quantize.argtypes = [f32, f32]
+            L.fszo_quantize.restype = i32
+            L.fszo_dequantize.argtypes = [i32, f32]
+            L.fszo_dequantize.restype = f32
+            L.fszo_tile_mu.argtypes = [P, f32]
+            L.fszo_tile_mu.restype = i32
+            L.fszo_tile_residuals.argtypes = [P, i32, ctypes.c_int, P]
+            L.fszo_tile_residuals.restype = None
+            L.fszo_rate.argtypes = [u32]
+            L.fszo_rate.restype = u32
+            L.fszo_block_cost.argtypes = [u32]
+            L.fszo_block_cost.restype = u32
+            L.fszo_tile_costs_single_pass.argtypes = [P, i32, P, P]
+            L.fszo_tile_costs_single_pass.restype = None
+            L.fszo_tile_costs_four_pass.argtypes = [P, i32, P, P]
+            L.fszo_tile_costs_four_pass.restype = None
+            L.fszo_select.argtypes = [P]
+            L.fszo_compress_bound.argtypes = [u64]
+            L.fszo_compress_bound.restype = u64
+            L.fszo_compress.argtypes = [P, u32, P, ctypes.c_int, f64, P, u64, P, ctypes.c_int]
+            L.fszo_read_preamble.argtypes = [P, u64, P, P, P, P, P, P]
+            L.fszo_decompress.argtypes = [P, u64, P, u64, P]
+            L.fszo_decompress_q.argtypes = [P, u64, P, u64, P]
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: oracle status {status}")
+        self.status = status
+
+
+def stats(d: np.ndarray):
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    lo, hi, fin = ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
+    lib().fszo_stats(_ptr(d), d.size, ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(fin))
+    return lo.value, hi.value, bool(fin.value)
+
+
+def params(mode: int, eb: float, vmin: float, vmax: float, finite: bool = True, n: int = 1):
+    p = Params()
+    st = lib().fszo_params(mode, eb, vmin, vmax, int(finite), n, ctypes.byref(p))
+    if st != OK:
+        raise OracleError(st, "params")
+    return p
+
+
+def params_for(d: np.ndarray, mode: int, eb: float) -> Params:
+    lo, hi, fin = stats(d)
+    return params(mode, eb, lo, hi, fin, int(np.asarray(d).size))
+
+
+def quantize(d: np.ndarray, r: float) -> np.ndarray:
+    L = lib()
+    return np.array([L.fszo_quantize(float(x), r) for x in np.asarray(d, np.float32).ravel()],
+                    dtype=np.int32)
+
+
+def tile_mu(d256: np.ndarray, r: float) -> int:
+    d = np.ascontiguousarray(d256, dtype=np.float32)
+    assert d.size == 256
+    return lib().fszo_tile_mu(_ptr(d), r)
+
+
+def tile_residuals(q256: np.ndarray, mu: int, variant: int) -> np.ndarray:
+    q = np.ascontiguousarray(q256, dtype=np.int32)
+    assert q.size == 256
+    out = np.zeros(256, np.int32)
+    lib().fszo_tile_residuals(_ptr(q), mu, variant, _ptr(out))
+    return out
+
+
+def rate(maxabs: int) -> int:
+    return lib().fszo_rate(maxabs)
+
+
+def block_cost(r: int) -> int:
+    return lib().fszo_block_cost(r)
+
+
+def tile_costs(q256: np.ndarray, mu: int, four_pass: bool = False):
+    q = np.ascontiguousarray(q256, dtype=np.int32)
+    assert q.size == 256
+    C = np.zeros(4, np.uint32)
+    rates = np.zeros(32, np.uint8)
+    fn = lib().fszo_tile_costs_four_pass if four_pass else lib().fszo_tile_costs_single_pass
+    fn(_ptr(q), mu, _ptr(C), _ptr(rates))
+    return C, rates.reshape(4, 8)
+
+
+def select(C: np.ndarray) -> int:
+    c = np.ascontiguousarray(C, dtype=np.uint32)
+    return lib().fszo_select(_ptr(c))
+
+
+def compress_bound(n: int) -> int:
+    return lib().fszo_compress_bound(n)
+
+
+def compress(d: np.ndarray, eb: float, mode: int = REL, dims=None, force_variant: int = -1) -> bytes:
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    if dims is None:
+        dims = d.shape if d.ndim >= 1 else (d.size,)
+    dims_arr = np.zeros(3, np.uint64)
+    dims_arr[: len(dims)] = dims
+    cap = compress_bound(d.size)
+    out = np.zeros(cap, np.uint8)
+    nb = ctypes.c_uint64()
+    st = lib().fszo_compress(_ptr(d), len(dims), _ptr(dims_arr), mode, eb, _ptr(out), cap,
+                             ctypes.byref(nb), force_variant)
+    if st != OK:
+        raise OracleError(st, "compress")
+    return out[: nb.value].tobytes()
+
+
+def read_preamble(stream: bytes):
+    buf = np.frombuffer(stream, np.uint8)
+    n, ndim, s, db = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_float(), ctypes.c_uint64()
+    dims = np.zeros(3, np.uint64)
+    eb = ctypes.c_double()
+    st = lib().fszo_read_preamble(_ptr(buf), buf.size, ctypes.byref(n), ctypes.byref(ndim),
+                                  _ptr(dims), ctypes.byref(eb), ctypes.byref(s), ctypes.byref(db))
+    if st != OK:
+        raise OracleError(st, "read_preamble")
+    return dict(n=n.value, ndim=ndim.value, dims=tuple(int(x) for x in dims[: ndim.value]),
+                eb=eb.value, s=s.value, data_bytes=db.value)
+
+
+def decompress(stream: bytes, q: bool = False) -> np.ndarray:
+    buf = np.frombuffer(stream, np.uint8)
+    info = read_preamble(stream)
+    n = info["n"]
+    out = np.zeros(max(n, 1), np.int32 if q else np.float32)
+    nn = ctypes.c_uint64()
+    fn = lib().fszo_decompress_q if q else lib().fszo_decompress
+    st = fn(_ptr(buf), buf.size, _ptr(out), n, ctypes.byref(nn))
+    if st != OK:
+        raise OracleError(st, "decompress")
+    return out[:n]
+
+
+def decompress_status(stream: bytes, cap: int | None = None) -> int:
+    """Status of a decode attempt (corrupt-stream tests); never raises."""
+    buf = np.frombuffer(stream, np.uint8) if len(stream) else np.zeros(1, np.uint8)
+    cap = (1 << 24) if cap is None else cap
+    out = np.zeros(max(cap, 1), np.float32)
+    nn = ctypes.c_uint64()
+    return lib().fszo_decompress(_ptr(buf), len(stream), _ptr(out), cap, ctypes.byref(nn))

@@ -1,0 +1,380 @@
+"""FSZ compress/decompress throughput on GB300.
+
+Workload: the 512^3 float32 Gaussian random field with P(k) ~ k^-3 and its zero-slab
++280 variant, each at REL 1e-2, 1e-3 and 1e-4 (six field/bound pairs). One step runs
+the whole hot path on all six: value-range pass + single-pass compression of each,
+then decompression of each, through the library's C ABI. Inputs (512 MiB each) are
+larger than L2, and each stream is read back only after at least 2.5 GB of other
+traffic, so no timed kernel reads its input from L2.
+
+value  = input bytes of both directions (4n per compression + 4n per decompression)
+         / step time, summed over ranks (replicas, one per GPU).
+e2e    = the same metric through the same calls with pinned host buffers: inputs
+         copied in, streams copied out and back in, reconstructions copied out.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RELS = (1e-2, 1e-3, 1e-4)
+SHAPE = (512, 512, 512)
+NOMINAL_HBM_GBS = 8000.0
+METRIC = "comp/decomp GB/s & % HBM roofline at oracle-exact CR; batched vs per-field"
+WORKLOAD = ("512^3 float32 k^-3 GRF + zero-slab/+280 variant, REL {1e-2,1e-3,1e-4}: "
+            "value-range pass + compress, then decompress, of all six")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"fsz_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def all_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_baseline_run(steps: int, warmup: int):
+    """The oracle, single-threaded on the host, on a bounded sample of the workload:
+    the first 2^23 elements (32 MiB) of each field at each bound, compress + decompress."""
+    import numpy as np
+
+    import oracle
+    from paper_2607_15413_gb300 import inputs
+    oracle.build()
+    g = inputs.grf((128, 256, 256), seed=1)  # same recipe, host-sized (2^23 elements)
+    z = inputs.zero_slabs((128, 256, 256), seed=1, base=g)
+    fields = [g.ravel(), z.ravel()]
+    nbytes = 0
+    t0 = time.perf_counter()
+    for f in fields:
+        for rel in RELS:
+            s = oracle.compress(f, rel, oracle.REL)
+            y = oracle.decompress(s)
+            assert y.size == f.size
+            nbytes += 2 * f.nbytes
+    dt = time.perf_counter() - t0
+    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first 2^23 elements (32 MiB) of both fields (same generator recipe at "
+                      "128x256x256) at REL 1e-2/1e-3/1e-4, compress + decompress, 1 host core",
+            "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        last = cpu_baseline_run(1, 0)
+        if i >= args.warmup:
+            vals.append(last["value"])
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * last["seconds"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (host sample: 2^23 elements per field)",
+                       "parallelism": "single host core"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": value,
+                             "unit": "GB/s"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fsz", choices=["fsz", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2607_15413_gb300 import fsz, inputs
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_run(1, 0)   # on the host, before any GPU work
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    # inputs resident in HBM
+    g = inputs.grf(SHAPE, seed=1, device=str(dev)).reshape(-1)
+    z = inputs.zero_slabs(SHAPE, seed=1, device=str(dev), base=g.reshape(SHAPE)).reshape(-1)
+    fields = [("grf", g), ("zero_slabs", z)]
+    n = g.numel()
+    cap = fsz.fsz_compress_bound(n)
+    jobs = [(name, x, rel) for name, x in fields for rel in RELS]
+    outs = [torch.empty(cap, dtype=torch.uint8, device=dev) for _ in jobs]
+    recon = torch.empty(n, dtype=torch.float32, device=dev)
+    nbytes = torch.zeros(len(jobs), dtype=torch.int64, device=dev)
+    wsb = fsz.fsz_workspace_bytes(n)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    dims = fsz.make_dims(SHAPE)
+    L = fsz.lib()
+    mk = lambda k: [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    ev_steps = [([mk(3) for _ in jobs], [mk(2) for _ in jobs]) for _ in range(args.steps)]
+    launches_per_step = len(jobs) * (3 + 2)   # setup+stats+compress, setup+decompress
+
+    def step(events):
+        record = events is not None
+        ev, evd = events if record else (None, None)
+        for j, (name, x, rel) in enumerate(jobs):
+            e = ev[j] if record else None
+            if record:
+                e[0].record(stream)
+            st = L.fsz_compress_prepare(x.data_ptr(), dims, fsz.EB_REL, rel, outs[j].data_ptr(), cap,
+                                        nbytes[j:].data_ptr(), ws.data_ptr(), wsb, sp)
+            if record:
+                e[1].record(stream)
+            st |= L.fsz_compress_encode(x.data_ptr(), dims, fsz.EB_REL, rel, outs[j].data_ptr(), cap,
+                                        nbytes[j:].data_ptr(), ws.data_ptr(), wsb, sp)
+            if record:
+                e[2].record(stream)
+            if st:
+                raise fsz.FszError(st, "compress")
+        for j, (name, x, rel) in enumerate(jobs):
+            e = evd[j] if record else None
+            if record:
+                e[0].record(stream)
+            st = L.fsz_decompress(outs[j].data_ptr(), cap, recon.data_ptr(), n, ws.data_ptr(), wsb, sp)
+            if record:
+                e[1].record(stream)
+            if st:
+                raise fsz.FszError(st, "decompress")
+
+    for _ in range(max(3, args.warmup)):
+        step(None)
+    st = fsz.fsz_check(ws.data_ptr(), sp)
+    if st != fsz.OK:
+        raise fsz.FszError(st, "warm-up")
+    sizes = nbytes.cpu().tolist()
+    # quick self-check of the last job's reconstruction against its bound
+    p_last = recon.double().sub(jobs[-1][1].double()).abs().max().item()
+
+    comp_ms, enc_ms, stats_ms, dec_ms = ([[] for _ in jobs] for _ in range(4))
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    with ClockSampler(local) as clocks:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        t_start.record(stream)
+        for k in range(args.steps):
+            step(ev_steps[k])
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+    for ev, evd in ev_steps:
+        for j in range(len(jobs)):
+            stats_ms[j].append(ev[j][0].elapsed_time(ev[j][1]))
+            enc_ms[j].append(ev[j][1].elapsed_time(ev[j][2]))
+            comp_ms[j].append(ev[j][0].elapsed_time(ev[j][2]))
+            dec_ms[j].append(evd[j][0].elapsed_time(evd[j][1]))
+    total_ms = t_start.elapsed_time(t_end)
+    ms_step = all_max(total_ms / args.steps, world)
+    bytes_step = 2 * len(jobs) * 4 * n
+    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+
+    # e2e: the same calls with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hin = [torch.empty(n, dtype=torch.float32, pin_memory=True) for _ in fields]
+        for (name, x), h in zip(fields, hin):
+            h.copy_(x.cpu())
+        hstream = [torch.empty(cap, dtype=torch.uint8, pin_memory=True) for _ in jobs]
+        hout = torch.empty(n, dtype=torch.float32, pin_memory=True)
+        hsizes = torch.empty(len(jobs), dtype=torch.int64, pin_memory=True)
+        din = [torch.empty(n, dtype=torch.float32, device=dev) for _ in fields]
+
+        def e2e_step():
+            h2d = d2h = 0
+            for h, d in zip(hin, din):
+                d.copy_(h, non_blocking=True)
+                h2d += 4 * n
+            for j, (name, x, rel) in enumerate(jobs):
+                dx = din[[f[0] for f in fields].index(name)]
+                s1 = L.fsz_compress(dx.data_ptr(), dims, fsz.EB_REL, rel, outs[j].data_ptr(), cap,
+                                    nbytes[j:].data_ptr(), ws.data_ptr(), wsb, sp)
+                if s1:
+                    raise fsz.FszError(s1, "compress")
+            hsizes.copy_(nbytes, non_blocking=True)
+            torch.cuda.current_stream(dev).synchronize()
+            szs = hsizes.tolist()
+            d2h += 8 * len(jobs)
+            for j in range(len(jobs)):
+                hstream[j][: szs[j]].copy_(outs[j][: szs[j]], non_blocking=True)
+                d2h += szs[j]
+            for j in range(len(jobs)):
+                outs[j][: szs[j]].copy_(hstream[j][: szs[j]], non_blocking=True)
+                h2d += szs[j]
+                s2 = L.fsz_decompress(outs[j].data_ptr(), szs[j], recon.data_ptr(), n, ws.data_ptr(),
+                                      wsb, sp)
+                if s2:
+                    raise fsz.FszError(s2, "decompress")
+                hout.copy_(recon, non_blocking=True)
+                d2h += 4 * n
+            return h2d, d2h
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        t0 = time.perf_counter()
+        ksteps = max(1, min(args.steps, 5))
+        for _ in range(ksteps):
+            h2d, d2h = e2e_step()
+        torch.cuda.synchronize(dev)
+        e2e_ms = all_max((time.perf_counter() - t0) * 1e3 / ksteps, world)
+        e2e = {"value": world * bytes_step / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+        del hin, hstream, din
+
+    # roofline of the dominant kernel (algorithmic bytes / CUDA-event duration)
+    peaks, peak_kind = measured_peaks()
+    enc_tot = sum(sum(v) for v in enc_ms)
+    dec_tot = sum(sum(v) for v in dec_ms)
+    comp_bytes = sum(4 * n + sizes[j] for j in range(len(jobs)))
+    dec_bytes = sum(sizes[j] + 4 * n for j in range(len(jobs)))
+    if enc_tot >= dec_tot:
+        kern, algo, dur = "fsz_compress_kernel", comp_bytes * args.steps, enc_tot
+    else:
+        kern, algo, dur = "fsz_decompress_kernel (incl. its 1-thread set-up kernel)", dec_bytes * args.steps, dec_tot
+    achieved = algo / (dur * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS, "traffic": None,
+                "algorithmic_bytes_per_launch": algo / (args.steps * len(jobs))}
+
+    per_job = []
+    for j, (name, x, rel) in enumerate(jobs):
+        med = lambda v: statistics.median(v)
+        per_job.append({"field": name, "rel": rel, "cr": 4 * n / sizes[j], "bytes": sizes[j],
+                        "compress_gbs": 4 * n / med(comp_ms[j]) / 1e6,
+                        "encode_kernel_gbs": 4 * n / med(enc_ms[j]) / 1e6,
+                        "encode_kernel_hbm_gbs": (4 * n + sizes[j]) / med(enc_ms[j]) / 1e6,
+                        "stats_gbs": 4 * n / med(stats_ms[j]) / 1e6,
+                        "decompress_gbs": 4 * n / med(dec_ms[j]) / 1e6,
+                        "decompress_hbm_gbs": (4 * n + sizes[j]) / med(dec_ms[j]) / 1e6})
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_per_field": n, "fields": 2, "rels": list(RELS),
+                           "parallelism": f"replicas x{world} (no data-path collective)",
+                           "l2": "inputs 512 MiB > L2; streams read back after >= 2.5 GB of traffic"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches_per_step * args.steps,
+                "clocks": clocks.summary(), "jobs": per_job,
+                "max_abs_err_last_job": p_last}
+        print(json.dumps(line))
+    barrier(world)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * fsz.h - C ABI of the GB300 (sm_103a) FSZ compressor library.
+ *
+ * FSZ is the error-bounded lossy compressor for float32 arrays of "FSZ:
+ * Breaking the Prediction-Throughput Trade-off in GPU Lossy Compression"
+ * (arXiv 2607.15413). Compression quantizes each value with step 2*eb
+ * (Sec. 4.2.2), runs first- or second-order Lorenzo prediction with the state
+ * carried across the 8 blocks of every 256-element tile (Sec. 4.1), optionally
+ * centred on the tile mean (Sec. 4.2.2), picks the cheapest of the four
+ * variants per tile from one pass (Sec. 4.2.3), bit-plane encodes every
+ * 32-element block (Sec. 4.3) and places the blocks with a device-wide
+ * decoupled-lookback scan (Sec. 4.4). Decompression inverts every step
+ * (Sec. 3.1, "Decompression"). Every reconstructed value d' satisfies
+ * |d - d'| <= eb (Sec. 4.2.2, "Error-bound preservation"; Sec. 5.1).
+ *
+ * Stream layout (Sec. 3.1 "Compressed format", plus a 64-byte preamble of
+ * this library): [preamble 64 B][rate header: 8 B per tile][tile data].
+ * Preamble, little-endian: 0 magic "FSZ1"; 4 version u16 = 1; 6 ndim u8;
+ * 7 eb mode u8; 8 n u64; 16/24/32 dims u64 (unused dims 0); 40 requested eb
+ * f64; 48 step s f32; 52 reserved u32 = 0; 56 data bytes u64.
+ *
+ * Conventions for every call below:
+ *  - Pointers named d_* are device pointers; h_* are host pointers. The caller
+ *    owns every buffer; the library allocates no device memory on these paths.
+ *  - Calls are asynchronous on `stream` and do not synchronise the host, so
+ *    they can be captured into a CUDA graph. The return value reports only
+ *    errors the host can see (arguments, alignment, sizes, launch failures).
+ *    Errors found on the device (non-finite input, an error bound too small
+ *    for the data, a corrupt stream, a lookback wait that ran out) are written
+ *    to a status word inside the workspace and read back by fsz_check().
+ *  - d_in, d_out and d_ws must be 16-byte aligned (FSZ_ERR_ALIGN otherwise).
+ *  - The workspace must not be shared by calls that overlap on the GPU.
+ */
+#ifndef FSZ_H
+#define FSZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Identical to cudaStream_t; declared here so that this header needs no CUDA header. */
+typedef struct CUstream_st* fsz_stream;
+
+typedef enum {
+  FSZ_OK = 0,
+  FSZ_ERR_INVALID_ARG = 1,  /* bad dims, eb <= 0 or not finite, unknown mode, null pointer */
+  FSZ_ERR_ALIGN = 2,        /* a pointer is not 16-byte aligned */
+  FSZ_ERR_NONFINITE = 3,    /* the field holds a NaN or an infinity (device-detected) */
+  FSZ_ERR_EB_TOO_SMALL = 4, /* max|d| / (2 eb) beyond the quantizer's range (device-detected) */
+  FSZ_ERR_CAPACITY = 5,     /* an output buffer is too small */
+  FSZ_ERR_CORRUPT = 6,      /* the compressed stream is malformed (device-detected) */
+  FSZ_ERR_TIMEOUT = 7,      /* a lookback wait ran past its time limit (device-detected) */
+  FSZ_ERR_CUDA = 8,         /* a CUDA runtime call or a kernel launch failed */
+  FSZ_ERR_WORKSPACE = 9     /* the workspace is smaller than fsz_*_workspace_bytes() */
+} fsz_status;
+
+typedef enum { FSZ_EB_ABS = 0, FSZ_EB_REL = 1 } fsz_eb_mode;
+
+/* Shape metadata: n = dims[0] * ... * dims[ndim-1], row-major, dims[ndim-1] fastest.
+ * The method itself is one-dimensional over the flattened array (Sec. 3.1). */
+typedef struct {
+  uint32_t ndim;     /* 1, 2 or 3 */
+  uint32_t reserved; /* must be 0 */
+  uint64_t dims[3];  /* entries beyond ndim are ignored */
+} fsz_dims;
+
+/* One field of a batched compression (lives in DEVICE memory, an array of nfields). */
+typedef struct {
+  const float* in;       /* device, 16-byte aligned, dims product elements */
+  fsz_dims dims;
+  uint32_t mode;         /* fsz_eb_mode */
+  uint32_t reserved;     /* must be 0 */
+  double eb;             /* absolute bound (ABS) or fraction of max - min (REL) */
+  void* out;             /* device, 16-byte aligned */
+  uint64_t out_capacity; /* bytes; fsz_compress_bound(n) always suffices */
+  uint64_t* out_bytes;   /* device u64 receiving this field's stream size, or NULL */
+} fsz_cfield;
+
+/* One field of a batched decompression (lives in DEVICE memory, an array of nfields). */
+typedef struct {
+  const void* in;              /* device, 16-byte aligned stream */
+  uint64_t in_bytes;           /* bytes readable at in (at least the stream size) */
+  float* out;                  /* device, 16-byte aligned */
+  uint64_t out_capacity_elems; /* elements writable at out */
+} fsz_dfield;
+
+/* ------------------------------------------------------------------ sizes */
+
+/* Largest stream for n elements: 64 + 8 T + 708 T bytes, T = ceil(n / 256). A tile
+ * costs at most 8 * (4 + 4 * 21) + 4 bytes because |q| stays below 2^18 (Sec. 4.2.2 Eq. 3). */
+uint64_t fsz_compress_bound(uint64_t n);
+
+/* Workspace for fsz_compress / fsz_decompress of up to n elements. */
+uint64_t fsz_workspace_bytes(uint64_t n);
+
+/* Workspace for a batch of nfields fields holding n_total elements in all. */
+uint64_t fsz_batch_workspace_bytes(uint64_t n_total, uint32_t nfields);
+
+/* ------------------------------------------------------------------ single field */
+
+/* Compress one field (Sec. 3.1 steps 1-5; eb per Sec. 5.1). Runs the value-range pass
+ * (min, max, finiteness, and the step derived from them), then the single-pass
+ * compression kernel. Writes the stream to d_out and its size to *d_out_bytes
+ * (device u64, may be NULL). out_capacity must be at least 64 + 8T; a stream that
+ * would exceed it sets FSZ_ERR_CAPACITY in the workspace status. */
+fsz_status fsz_compress(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                        void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
+                        void* d_ws, uint64_t ws_bytes, fsz_stream stream);
+
+/* The two halves of fsz_compress, for callers that time or schedule them apart.
+ * fsz_compress_prepare: value-range pass (Sec. 5.1: eb = REL x (max - min)) and the
+ * quantization step, written into the workspace. fsz_compress_encode: the single-pass
+ * compression kernel (Sec. 3.1 steps 1-5) using the step in the workspace; it must
+ * follow fsz_compress_prepare on the same workspace with the same arguments. */
+fsz_status fsz_compress_prepare(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                                void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
+                                void* d_ws, uint64_t ws_bytes, fsz_stream stream);
+fsz_status fsz_compress_encode(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                               void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
+                               void* d_ws, uint64_t ws_bytes, fsz_stream stream);
+
+/* Decompress one stream (Sec. 3.1 "Decompression", steps d1-d5) into d_out.
+ * out_capacity_elems also bounds the workspace needed (fsz_workspace_bytes of it). */
+fsz_status fsz_decompress(const void* d_in, uint64_t in_bytes, float* d_out,
+                          uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
+                          fsz_stream stream);
+
+/* ------------------------------------------------------------------ batches */
+
+/* Compress nfields fields in one persistent launch (plus a planning kernel and the
+ * value-range pass): work items (field, chunk) are taken from one device ticket in
+ * field-major order, each field keeps its own lookback flags and its own stream.
+ * Each field's stream is byte-identical to fsz_compress of that field.
+ * d_fields: DEVICE array of nfields fsz_cfield. */
+fsz_status fsz_compress_batched(const fsz_cfield* d_fields, uint32_t nfields, uint64_t n_total,
+                                void* d_ws, uint64_t ws_bytes, fsz_stream stream);
+
+/* Decompress nfields streams in one persistent launch (plus a planning kernel).
+ * d_fields: DEVICE array of nfields fsz_dfield. n_total_capacity = sum of the fields'
+ * out_capacity_elems (sizes the workspace). */
+fsz_status fsz_decompress_batched(const fsz_dfield* d_fields, uint32_t nfields,
+                                  uint64_t n_total_capacity, void* d_ws, uint64_t ws_bytes,
+                                  fsz_stream stream);
+
+/* ------------------------------------------------------------------ status and metadata */
+
+/* Waits for `stream`, then returns the first device-detected error recorded in the
+ * workspace by the last call that used it (FSZ_OK if none). For batches, the first
+ * error of any field. */
+fsz_status fsz_check(const void* d_ws, fsz_stream stream);
+
+/* Per-field status of the last batched call (host array of nfields); waits for stream. */
+fsz_status fsz_check_batched(const void* d_ws, uint32_t nfields, uint32_t* h_status,
+                             fsz_stream stream);
+
+/* Parses a stream's 64-byte preamble from HOST memory. Any output may be NULL. */
+fsz_status fsz_read_header(const void* h_first64, uint64_t* n, fsz_dims* dims, double* eb,
+                           float* step, uint64_t* total_bytes);
+
+/* Test hooks for failure detection (not for production use): the chunk whose global
+ * index equals skip_chunk publishes no lookback flag, so its successor's bounded wait
+ * runs out after timeout_ns and records FSZ_ERR_TIMEOUT; the kernels still finish.
+ * skip_chunk = UINT64_MAX disables the hook; timeout_ns = 0 restores the default (2 s). */
+void fsz_set_test_hooks(uint64_t skip_chunk, uint64_t timeout_ns);
+
+/* Library version and build target, e.g. "fsz 1.0 sm_103a". */
+const char* fsz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSZ_H */

@@ -81,6 +81,7 @@ def lib():
             L.fszo_compress_bound.restype = u64
             L.fszo_compress.argtypes = [P, u32, P, ctypes.c_int, f64, P, u64, P, ctypes.c_int]
             L.fszo_read_preamble.argtypes = [P, u64, P, P, P, P, P, P]
+            L.fszo_compress_tiles.argtypes = [P, u64, f32, u64, u64, P, P, u64, P]
             L.fszo_decompress.argtypes = [P, u64, P, u64, P]
             L.fszo_decompress_q.argtypes = [P, u64, P, u64, P]
             _lib = L
@@ -178,6 +179,20 @@ def compress(d: np.ndarray, eb: float, mode: int = REL, dims=None, force_variant
     if st != OK:
         raise OracleError(st, "compress")
     return out[: nb.value].tobytes()
+
+
+def compress_tiles(d: np.ndarray, r: float, t0: int, t1: int):
+    """Headers (8 bytes per tile) and data of tiles [t0, t1) of field d, given r = 1/s."""
+    d = np.ascontiguousarray(d, dtype=np.float32).ravel()
+    hdr = np.zeros(8 * max(t1 - t0, 1), np.uint8)
+    cap = 708 * max(t1 - t0, 1)
+    data = np.zeros(cap, np.uint8)
+    nb = ctypes.c_uint64()
+    st = lib().fszo_compress_tiles(_ptr(d), d.size, r, t0, t1, _ptr(hdr), _ptr(data), cap,
+                                   ctypes.byref(nb))
+    if st != OK:
+        raise OracleError(st, "compress_tiles")
+    return hdr[: 8 * (t1 - t0)].tobytes(), data[: nb.value].tobytes()
 
 
 def read_preamble(stream: bytes):

@@ -255,6 +255,85 @@ uint64_t fszo_compress_bound(uint64_t n) {
   return kPreamble + 8 * T + 708 * T;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Steps 1-5 of Sec. 3.1 for one tile: quantize, tile mean, four-way costs, select, then the
+// 8 rate-header bytes and the tile's data appended to `data`.
+void encode_tile(const float dt[256], float r, int force_variant, uint8_t header[8],
+                 std::vector<uint8_t>& data) {
+  int32_t q[kTile], l[kTile];
+  // Step 1: quantize (Sec. 3.1, Sec. 4.2.2).
+  for (int i = 0; i < kTile; ++i) q[i] = fszo_quantize(dt[i], r);
+  int32_t mu = fszo_tile_mu(dt, r);
+  // Steps 2-3: four-way evaluation and adaptive select.
+  uint32_t C[4];
+  uint8_t rates[32];
+  fszo_tile_costs_single_pass(q, mu, C, rates);
+  const int v = force_variant >= 0 ? force_variant : fszo_select(C);
+  const bool centred = (v == FSZO_LZ1C || v == FSZO_LZ2C);
+  const bool second = (v == FSZO_LZ2 || v == FSZO_LZ2C);
+  // Rate header (Sec. 3.1 "Compressed format"): block 0 carries bit 7 = LZ order
+  // (set for second order), bit 6 = centring, bits 4-0 = rate; blocks 1-7 the rate.
+  for (int b = 0; b < kBlocksPerTile; ++b) header[b] = rates[v * 8 + b];
+  header[0] = uint8_t(header[0] | (second ? 0x80 : 0) | (centred ? 0x40 : 0));
+  // Step 5: encode with the selected variant.
+  fszo_tile_residuals(q, mu, v, l);
+  if (centred) {
+    // Tile mean: a 4-byte float stored inline, first in the tile's data (reading
+    // of "stored inline"); it holds the integer mu exactly.
+    float muf = float(mu);
+    uint32_t bits;
+    std::memcpy(&bits, &muf, 4);
+    uint8_t tmp[4];
+    put_u32(tmp, bits);
+    data.insert(data.end(), tmp, tmp + 4);
+  }
+  for (int b = 0; b < kBlocksPerTile; ++b) {
+    uint32_t rb = rates[v * 8 + b];
+    if (rb == 0) continue;  // zero-rate blocks store nothing
+    uint32_t sign = 0;
+    for (int j = 0; j < kBlock; ++j)
+      if (l[b * kBlock + j] < 0) sign |= 1u << (31 - j);
+    put_word_be(data, sign);
+    for (uint32_t k = 0; k < rb; ++k) {  // bit-plane k, least significant plane first
+      uint32_t w = 0;
+      for (int j = 0; j < kBlock; ++j)
+        if ((uabs(l[b * kBlock + j]) >> k) & 1u) w |= 1u << (31 - j);
+      put_word_be(data, w);
+    }
+  }
+}
+
+void load_tile(const float* d, uint64_t n, uint64_t t, float dt[256]) {
+  // Zero padding of a partial last tile (reading: the paper is silent).
+  for (int i = 0; i < kTile; ++i) {
+    uint64_t g = t * kTile + uint64_t(i);
+    dt[i] = g < n ? d[g] : 0.0f;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int fszo_compress_tiles(const float* d, uint64_t n, float r, uint64_t t0, uint64_t t1,
+                        uint8_t* header_out, uint8_t* data_out, uint64_t data_cap,
+                        uint64_t* data_bytes) {
+  if (t1 < t0 || t1 > tiles_of(n)) return FSZO_ERR_INVALID_ARG;
+  std::vector<uint8_t> data;
+  float dt[kTile];
+  for (uint64_t t = t0; t < t1; ++t) {
+    load_tile(d, n, t, dt);
+    encode_tile(dt, r, -1, header_out + 8 * (t - t0), data);
+  }
+  if (data_bytes) *data_bytes = data.size();
+  if (data.size() > data_cap) return FSZO_ERR_CAPACITY;
+  if (!data.empty()) std::memcpy(data_out, data.data(), data.size());
+  return FSZO_OK;
+}
+
 int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode, double eb_req,
                   uint8_t* out, uint64_t out_capacity, uint64_t* out_bytes, int force_variant) {
   if (ndim < 1 || ndim > 3 || dims == nullptr) return FSZO_ERR_INVALID_ARG;
@@ -265,7 +344,8 @@ int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode,
     n *= dims[k];
   }
   if (n > kMaxElems) return FSZO_ERR_INVALID_ARG;
-  float vmin, vmax; int fin;
+  float vmin, vmax;
+  int fin;
   fszo_stats(d, n, &vmin, &vmax, &fin);
   fszo_params_t p;
   int st = fszo_params(mode, eb_req, vmin, vmax, fin, n, &p);
@@ -276,50 +356,9 @@ int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode,
   std::vector<uint8_t> data;
   data.reserve(size_t(n));
   float dt[kTile];
-  int32_t q[kTile], l[kTile];
   for (uint64_t t = 0; t < T; ++t) {
-    // Zero padding of a partial last tile (reading: the paper is silent).
-    for (int i = 0; i < kTile; ++i) {
-      uint64_t g = t * kTile + uint64_t(i);
-      dt[i] = g < n ? d[g] : 0.0f;
-    }
-    // Step 1: quantize (Sec. 3.1, Sec. 4.2.2).
-    for (int i = 0; i < kTile; ++i) q[i] = fszo_quantize(dt[i], p.r);
-    int32_t mu = fszo_tile_mu(dt, p.r);
-    // Steps 2-3: four-way evaluation and adaptive select.
-    uint32_t C[4]; uint8_t rates[32];
-    fszo_tile_costs_single_pass(q, mu, C, rates);
-    int v = force_variant >= 0 ? force_variant : fszo_select(C);
-    const bool centred = (v == FSZO_LZ1C || v == FSZO_LZ2C);
-    const bool second = (v == FSZO_LZ2 || v == FSZO_LZ2C);
-    // Rate header (Sec. 3.1 "Compressed format"): block 0 carries bit 7 = LZ order
-    // (set for second order), bit 6 = centring, bits 4-0 = rate; blocks 1-7 the rate.
-    for (int b = 0; b < kBlocksPerTile; ++b) header[8 * t + b] = rates[v * 8 + b];
-    header[8 * t] = uint8_t(header[8 * t] | (second ? 0x80 : 0) | (centred ? 0x40 : 0));
-    // Step 5: encode with the selected variant.
-    fszo_tile_residuals(q, mu, v, l);
-    if (centred) {
-      // Tile mean: a 4-byte float stored inline, first in the tile's data (reading
-      // of "stored inline"); it holds the integer mu exactly.
-      float muf = float(mu);
-      uint32_t bits; std::memcpy(&bits, &muf, 4);
-      uint8_t tmp[4]; put_u32(tmp, bits);
-      data.insert(data.end(), tmp, tmp + 4);
-    }
-    for (int b = 0; b < kBlocksPerTile; ++b) {
-      uint32_t rb = rates[v * 8 + b];
-      if (rb == 0) continue;  // zero-rate blocks store nothing
-      uint32_t sign = 0;
-      for (int j = 0; j < kBlock; ++j)
-        if (l[b * kBlock + j] < 0) sign |= 1u << (31 - j);
-      put_word_be(data, sign);
-      for (uint32_t k = 0; k < rb; ++k) {  // bit-plane k, least significant plane first
-        uint32_t w = 0;
-        for (int j = 0; j < kBlock; ++j)
-          if ((uabs(l[b * kBlock + j]) >> k) & 1u) w |= 1u << (31 - j);
-        put_word_be(data, w);
-      }
-    }
+    load_tile(d, n, t, dt);
+    encode_tile(dt, p.r, force_variant, header.data() + 8 * t, data);
   }
   const uint64_t total = kPreamble + 8 * T + uint64_t(data.size());
   if (out_bytes) *out_bytes = total;
@@ -332,8 +371,12 @@ int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode,
   out[7] = uint8_t(mode);
   put_u64(out + 8, n);
   for (uint32_t k = 0; k < 3; ++k) put_u64(out + 16 + 8 * k, k < ndim ? dims[k] : 0);
-  uint64_t ebits; std::memcpy(&ebits, &eb_req, 8); put_u64(out + 40, ebits);
-  uint32_t sbits; std::memcpy(&sbits, &p.s, 4); put_u32(out + 48, sbits);
+  uint64_t ebits;
+  std::memcpy(&ebits, &eb_req, 8);
+  put_u64(out + 40, ebits);
+  uint32_t sbits;
+  std::memcpy(&sbits, &p.s, 4);
+  put_u32(out + 48, sbits);
   put_u32(out + 52, 0);
   put_u64(out + 56, uint64_t(data.size()));
   if (T) std::memcpy(out + kPreamble, header.data(), header.size());

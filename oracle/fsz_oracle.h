@@ -85,6 +85,12 @@ uint64_t fszo_compress_bound(uint64_t n);
 int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode, double eb_req,
                   uint8_t* out, uint64_t out_capacity, uint64_t* out_bytes, int force_variant);
 
+/* Tiles [t0, t1) of a field, encoded with the given r = 1/s: their 8-byte rate headers
+ * (8 (t1 - t0) bytes) and their data, as they appear in the whole field's stream. */
+int fszo_compress_tiles(const float* d, uint64_t n, float r, uint64_t t0, uint64_t t1,
+                        uint8_t* header_out, uint8_t* data_out, uint64_t data_cap,
+                        uint64_t* data_bytes);
+
 /* Parses the 64-byte preamble. */
 int fszo_read_preamble(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint32_t* ndim,
                        uint64_t dims[3], double* eb_req, float* s, uint64_t* data_bytes);

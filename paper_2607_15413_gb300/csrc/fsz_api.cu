@@ -1,0 +1,240 @@
+// C ABI of the FSZ library (declared in include/fsz.h): argument checks on the host,
+// workspace layout, and the launch sequence of each call. No call allocates memory or
+// synchronises the host except fsz_check / fsz_check_batched.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fsz_internal.cuh"
+
+namespace {
+
+using namespace fsz;
+
+uint64_t g_skip_chunk = ~uint64_t(0);
+uint64_t g_timeout_ns = kDefaultTimeoutNs;
+
+bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
+
+fsz_status dims_count(const fsz_dims& dims, uint64_t* n) {
+  if (dims.ndim < 1 || dims.ndim > 3 || dims.reserved != 0) return FSZ_ERR_INVALID_ARG;
+  uint64_t p = 1;
+  for (uint32_t k = 0; k < dims.ndim; ++k) {
+    const uint64_t dk = dims.dims[k];
+    if (dk != 0 && p > kMaxElems / dk) return FSZ_ERR_INVALID_ARG;
+    p *= dk;
+  }
+  if (p > kMaxElems) return FSZ_ERR_INVALID_ARG;
+  *n = p;
+  return FSZ_OK;
+}
+
+KernelArgs make_args(void* d_ws, const WsLayout& L) {
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  KernelArgs a;
+  a.ctrl = reinterpret_cast<Ctrl*>(ws);
+  a.fields = reinterpret_cast<FieldInfo*>(ws + L.fields_off);
+  a.chunk_field = reinterpret_cast<const uint32_t*>(ws + L.map_off);
+  a.flags = reinterpret_cast<uint64_t*>(ws + L.flags_off);
+  a.skip_chunk = g_skip_chunk;
+  a.timeout_ns = g_timeout_ns;
+  return a;
+}
+
+fsz_status launched() {
+  return cudaGetLastError() == cudaSuccess ? FSZ_OK : FSZ_ERR_CUDA;
+}
+
+struct CompressCall {
+  WsLayout L;
+  FieldInfo desc;
+};
+
+fsz_status check_compress(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb, void* d_out,
+                          uint64_t out_capacity, void* d_ws, uint64_t ws_bytes, CompressCall* call) {
+  uint64_t n = 0;
+  fsz_status st = dims_count(dims, &n);
+  if (st != FSZ_OK) return st;
+  if (mode != FSZ_EB_ABS && mode != FSZ_EB_REL) return FSZ_ERR_INVALID_ARG;
+  if (!(eb > 0.0) || !std::isfinite(eb)) return FSZ_ERR_INVALID_ARG;
+  if (d_out == nullptr || d_ws == nullptr || (n > 0 && d_in == nullptr)) return FSZ_ERR_INVALID_ARG;
+  if (misaligned(d_in) || misaligned(d_out) || misaligned(d_ws)) return FSZ_ERR_ALIGN;
+  const uint64_t T = (n + kTile - 1) / kTile;
+  if (out_capacity < 64 + 8 * T) return FSZ_ERR_CAPACITY;
+  call->L = ws_layout(T, 1);
+  if (ws_bytes < call->L.bytes) return FSZ_ERR_WORKSPACE;
+  FieldInfo& d = call->desc;
+  std::memset(&d, 0, sizeof(d));
+  d.in = d_in;
+  d.out = static_cast<uint8_t*>(d_out);
+  d.cap = out_capacity;
+  d.n = n;
+  d.T = T;
+  for (uint32_t k = 0; k < dims.ndim; ++k) d.dims[k] = dims.dims[k];
+  d.ndim = dims.ndim;
+  d.mode = uint32_t(mode);
+  d.eb_req = eb;
+  d.nchunks = (T + kChunkTiles - 1) / kChunkTiles;
+  return FSZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t fsz_compress_bound(uint64_t n) {
+  const uint64_t T = (n + kTile - 1) / kTile;
+  return 64 + 8 * T + uint64_t(kMaxTileBytes) * T;
+}
+
+uint64_t fsz_workspace_bytes(uint64_t n) { return ws_layout((n + kTile - 1) / kTile, 1).bytes; }
+
+uint64_t fsz_batch_workspace_bytes(uint64_t n_total, uint32_t nfields) {
+  return ws_layout(n_total / kTile + nfields, nfields).bytes;
+}
+
+fsz_status fsz_compress_prepare(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                                void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
+                                void* d_ws, uint64_t ws_bytes, fsz_stream stream) {
+  CompressCall call;
+  fsz_status st = check_compress(d_in, dims, mode, eb, d_out, out_capacity, d_ws, ws_bytes, &call);
+  if (st != FSZ_OK) return st;
+  call.desc.out_bytes = d_out_bytes;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_ws, 0, call.L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
+  const KernelArgs a = make_args(d_ws, call.L);
+  launch_setup_compress(a, call.desc, s);
+  if (call.desc.nchunks > 0) launch_stats(a, s);
+  return launched();
+}
+
+fsz_status fsz_compress_encode(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                               void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
+                               void* d_ws, uint64_t ws_bytes, fsz_stream stream) {
+  (void)d_out_bytes;
+  CompressCall call;
+  fsz_status st = check_compress(d_in, dims, mode, eb, d_out, out_capacity, d_ws, ws_bytes, &call);
+  if (st != FSZ_OK) return st;
+  if (call.desc.nchunks == 0) return FSZ_OK;
+  launch_compress(make_args(d_ws, call.L), reinterpret_cast<cudaStream_t>(stream));
+  return launched();
+}
+
+fsz_status fsz_compress(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb, void* d_out,
+                        uint64_t out_capacity, uint64_t* d_out_bytes, void* d_ws, uint64_t ws_bytes,
+                        fsz_stream stream) {
+  fsz_status st = fsz_compress_prepare(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws,
+                                       ws_bytes, stream);
+  if (st != FSZ_OK) return st;
+  return fsz_compress_encode(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes,
+                             stream);
+}
+
+fsz_status fsz_decompress(const void* d_in, uint64_t in_bytes, float* d_out, uint64_t out_capacity_elems,
+                          void* d_ws, uint64_t ws_bytes, fsz_stream stream) {
+  if (d_in == nullptr || d_out == nullptr || d_ws == nullptr) return FSZ_ERR_INVALID_ARG;
+  if (misaligned(d_in) || misaligned(d_out) || misaligned(d_ws)) return FSZ_ERR_ALIGN;
+  if (out_capacity_elems > kMaxElems) out_capacity_elems = kMaxElems;
+  const WsLayout L = ws_layout((out_capacity_elems + kTile - 1) / kTile, 1);
+  if (ws_bytes < L.bytes) return FSZ_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_ws, 0, L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
+  const KernelArgs a = make_args(d_ws, L);
+  launch_setup_decompress(a, static_cast<const uint8_t*>(d_in), in_bytes, d_out, out_capacity_elems,
+                          L.chunk_cap, s);
+  launch_decompress(a, s);
+  return launched();
+}
+
+fsz_status fsz_compress_batched(const fsz_cfield* d_fields, uint32_t nfields, uint64_t n_total,
+                                void* d_ws, uint64_t ws_bytes, fsz_stream stream) {
+  if (d_fields == nullptr || d_ws == nullptr || nfields == 0) return FSZ_ERR_INVALID_ARG;
+  if (misaligned(d_ws)) return FSZ_ERR_ALIGN;
+  const WsLayout L = ws_layout(n_total / kTile + nfields, nfields);
+  if (ws_bytes < L.bytes) return FSZ_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_ws, 0, L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
+  const KernelArgs a = make_args(d_ws, L);
+  launch_plan_compress(a, d_fields, nfields, L.chunk_cap, s);
+  launch_stats(a, s);
+  launch_compress(a, s);
+  return launched();
+}
+
+fsz_status fsz_decompress_batched(const fsz_dfield* d_fields, uint32_t nfields,
+                                  uint64_t n_total_capacity, void* d_ws, uint64_t ws_bytes,
+                                  fsz_stream stream) {
+  if (d_fields == nullptr || d_ws == nullptr || nfields == 0) return FSZ_ERR_INVALID_ARG;
+  if (misaligned(d_ws)) return FSZ_ERR_ALIGN;
+  const WsLayout L = ws_layout(n_total_capacity / kTile + nfields, nfields);
+  if (ws_bytes < L.bytes) return FSZ_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_ws, 0, L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
+  const KernelArgs a = make_args(d_ws, L);
+  launch_plan_decompress(a, d_fields, nfields, L.chunk_cap, s);
+  launch_decompress(a, s);
+  return launched();
+}
+
+fsz_status fsz_check(const void* d_ws, fsz_stream stream) {
+  if (d_ws == nullptr) return FSZ_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FSZ_ERR_CUDA;
+  uint32_t status = 0;
+  if (cudaMemcpy(&status, d_ws, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FSZ_ERR_CUDA;
+  return static_cast<fsz_status>(status);
+}
+
+fsz_status fsz_check_batched(const void* d_ws, uint32_t nfields, uint32_t* h_status, fsz_stream stream) {
+  if (d_ws == nullptr || (nfields > 0 && h_status == nullptr)) return FSZ_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FSZ_ERR_CUDA;
+  std::vector<FieldInfo> fields(nfields);
+  const uint8_t* ws = static_cast<const uint8_t*>(d_ws);
+  if (nfields > 0 &&
+      cudaMemcpy(fields.data(), ws + 256, sizeof(FieldInfo) * nfields, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FSZ_ERR_CUDA;
+  for (uint32_t f = 0; f < nfields; ++f) h_status[f] = fields[f].status;
+  uint32_t status = 0;
+  if (cudaMemcpy(&status, d_ws, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return FSZ_ERR_CUDA;
+  return static_cast<fsz_status>(status);
+}
+
+fsz_status fsz_read_header(const void* h_first64, uint64_t* n, fsz_dims* dims, double* eb, float* step,
+                           uint64_t* total_bytes) {
+  if (h_first64 == nullptr) return FSZ_ERR_INVALID_ARG;
+  const uint8_t* p = static_cast<const uint8_t*>(h_first64);
+  auto u16 = [&](int o) { return uint32_t(p[o]) | (uint32_t(p[o + 1]) << 8); };
+  auto u32 = [&](int o) { uint32_t v; std::memcpy(&v, p + o, 4); return v; };
+  auto u64 = [&](int o) { uint64_t v; std::memcpy(&v, p + o, 8); return v; };
+  if (std::memcmp(p, "FSZ1", 4) != 0 || u16(4) != 1) return FSZ_ERR_CORRUPT;
+  const uint32_t nd = p[6];
+  if (nd < 1 || nd > 3 || p[7] > 1) return FSZ_ERR_CORRUPT;
+  const uint64_t nn = u64(8);
+  fsz_dims d;
+  std::memset(&d, 0, sizeof(d));
+  d.ndim = nd;
+  for (uint32_t k = 0; k < nd; ++k) d.dims[k] = u64(16 + 8 * k);
+  uint64_t prod = 0;
+  if (dims_count(d, &prod) != FSZ_OK || prod != nn) return FSZ_ERR_CORRUPT;
+  double e;
+  std::memcpy(&e, p + 40, 8);
+  float sv;
+  uint32_t sb = u32(48);
+  std::memcpy(&sv, &sb, 4);
+  if (n) *n = nn;
+  if (dims) *dims = d;
+  if (eb) *eb = e;
+  if (step) *step = sv;
+  if (total_bytes) *total_bytes = 64 + 8 * ((nn + kTile - 1) / kTile) + u64(56);
+  return FSZ_OK;
+}
+
+void fsz_set_test_hooks(uint64_t skip_chunk, uint64_t timeout_ns) {
+  g_skip_chunk = skip_chunk;
+  g_timeout_ns = timeout_ns ? timeout_ns : kDefaultTimeoutNs;
+}
+
+const char* fsz_version(void) { return "fsz 1.0 sm_103a"; }
+
+}  // extern "C"

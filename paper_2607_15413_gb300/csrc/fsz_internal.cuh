@@ -1,0 +1,322 @@
+// Internal definitions shared by the FSZ CUDA kernels (sm_103a).
+//
+// Work decomposition (GB300 design, not the paper's): a persistent CTA takes chunks of
+// kChunkTiles tiles by an atomic ticket, stages each chunk in shared memory with 1-D
+// TMA bulk copies (double-buffered, mbarrier-tracked) and gives each warp one 256-element
+// tile at a time. Lane j of the warp owns the 8 consecutive elements 8j..8j+7, so the
+// 4 lanes 4g..4g+3 hold block g (Sec. 3.1: a tile is 8 blocks of 32 elements). Residual
+// chains stay in registers; a shuffle carries the state across lane and block boundaries.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fsz.h"
+
+namespace fsz {
+
+constexpr int kTile = 256;
+constexpr int kMaxTileBytes = 708;    // 8 * (4 + 4 * 21) + 4, Eq. 3 with rate <= 21
+constexpr int kMaxDecTileBytes = 1028;  // any header-valid tile: 8 * (4 + 4 * 31) + 4
+constexpr uint32_t kQmax = 174761;    // largest Q with (3Q + 4) 2^-23 <= 2^-4
+constexpr int kMinChunkTiles = 16;    // smallest chunk any kernel uses (workspace sizing)
+constexpr int kChunkTiles = 32;       // tiles per work item of every kernel (32 KiB of input)
+constexpr int kChunkElems = kChunkTiles * kTile;
+constexpr uint64_t kMaxElems = uint64_t(1) << 40;
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
+
+// Adding 1.5 * 2^23 to a float t with |t| < 2^22 rounds it to the nearest integer, ties to
+// even, and leaves that integer in the low mantissa bits: bits(t + M) - bits(M) = rint(t).
+constexpr float kMagic = 12582912.0f;
+constexpr int kMagicBits = 0x4B400000;
+
+// Decoupled-lookback flag word (Sec. 4.4): 2-bit state and a 62-bit byte count.
+constexpr uint64_t kFlagAgg = uint64_t(1) << 62;   // local sum available
+constexpr uint64_t kFlagIncl = uint64_t(2) << 62;  // inclusive prefix available
+constexpr uint64_t kFlagValue = (uint64_t(1) << 62) - 1;
+
+// Per-field state in the workspace: descriptor, value-range accumulators, derived step.
+struct alignas(16) FieldInfo {
+  // compression descriptor
+  const float* in;
+  uint8_t* out;
+  uint64_t cap;
+  uint64_t* out_bytes;
+  // decompression descriptor
+  const uint8_t* sin;
+  uint64_t in_bytes;
+  float* dout;
+  uint64_t data_bytes;
+  // shape
+  uint64_t n;
+  uint64_t T;
+  uint64_t dims[3];
+  uint32_t ndim;
+  uint32_t mode;
+  double eb_req;
+  // chunk range of this field in the global ticket order
+  uint64_t chunk_first;
+  uint64_t nchunks;
+  // value range (ordered-integer keys; the minimum is kept as the max of ~key)
+  uint32_t min_inv_key;
+  uint32_t max_key;
+  uint32_t max_abs_bits;  // max of (bits & 0x7fffffff): >= 0x7f800000 means non-finite
+  uint32_t done_chunks;
+  // quantization step (valid once status == 0 after the value-range pass)
+  double eb;
+  float e, s, r;
+  uint32_t Q;
+  uint32_t status;
+  uint32_t pad;
+};
+
+struct alignas(64) Ctrl {
+  uint32_t status;       // first device-detected error of the call
+  uint32_t ticket;       // chunk ticket (compress / decompress)
+  uint32_t nfields;
+  uint32_t pad0;
+  uint64_t total_chunks;
+  uint64_t chunk_cap;    // chunk slots available in the workspace
+  uint32_t plan_done;
+  uint32_t pad1[7];
+};
+
+// Workspace layout: [Ctrl][FieldInfo x nfields][u32 chunk->field x cap][u64 flags x cap].
+struct WsLayout {
+  uint64_t fields_off, map_off, flags_off, bytes;
+  uint64_t chunk_cap;
+};
+
+inline WsLayout ws_layout(uint64_t tiles_upper, uint32_t nfields) {
+  WsLayout L;
+  L.chunk_cap = (tiles_upper + kMinChunkTiles - 1) / kMinChunkTiles + nfields + 1;
+  L.fields_off = 256;
+  L.map_off = L.fields_off + uint64_t(nfields) * sizeof(FieldInfo);
+  L.flags_off = (L.map_off + 4 * L.chunk_cap + 15) & ~uint64_t(15);
+  L.bytes = L.flags_off + 8 * L.chunk_cap;
+  return L;
+}
+
+struct KernelArgs {
+  Ctrl* ctrl;
+  FieldInfo* fields;
+  const uint32_t* chunk_field;
+  uint64_t* flags;
+  uint64_t skip_chunk;  // test hook: this chunk publishes no flag
+  uint64_t timeout_ns;  // bound on every spin-wait
+};
+
+// ------------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// 1-D TMA bulk copy global -> shared (16-byte aligned ends, size a multiple of 16).
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 1-D TMA bulk copy shared -> global, tracked by bulk groups.
+__device__ __forceinline__ void tma_store_1d(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void tma_store_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void set_error(Ctrl* ctrl, FieldInfo* fi, uint32_t code) {
+  if (fi) atomicCAS(&fi->status, 0u, code);
+  atomicCAS(&ctrl->status, 0u, code);
+}
+
+__device__ __forceinline__ uint32_t uabs32(int32_t v) {
+  return v < 0 ? 0u - static_cast<uint32_t>(v) : static_cast<uint32_t>(v);
+}
+
+// 8x8 bit-matrix transpose of the 64-bit word hi:lo: bit 8r + c <-> bit 8c + r.
+// Three delta swaps (Hacker's Delight, "transposing a bit matrix"), on 32-bit halves.
+__device__ __forceinline__ void transpose8x8(uint32_t& lo, uint32_t& hi) {
+  uint32_t t;
+  t = (lo ^ (lo >> 7)) & 0x00AA00AAu; lo = lo ^ t ^ (t << 7);
+  t = (hi ^ (hi >> 7)) & 0x00AA00AAu; hi = hi ^ t ^ (t << 7);
+  t = (lo ^ (lo >> 14)) & 0x0000CCCCu; lo = lo ^ t ^ (t << 14);
+  t = (hi ^ (hi >> 14)) & 0x0000CCCCu; hi = hi ^ t ^ (t << 14);
+  t = (lo ^ (hi << 4)) & 0xF0F0F0F0u; lo ^= t; hi ^= (t >> 4);
+}
+
+// 4x4 byte transpose across the 4 lanes of a group (t = lane & 3): afterwards byte k of
+// lane t's word is byte t of lane k's word. Two exchange steps (xor 1, xor 2).
+__device__ __forceinline__ uint32_t transpose4x4_bytes(uint32_t w, int t) {
+  uint32_t x = __shfl_xor_sync(0xffffffffu, w, 1);
+  w = __byte_perm(w, x, (t & 1) ? 0x3715 : 0x6240);
+  x = __shfl_xor_sync(0xffffffffu, w, 2);
+  w = __byte_perm(w, x, (t & 2) ? 0x3276 : 0x5410);
+  return w;
+}
+
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Exclusive prefix of the chunks before `gchunk` within its field (Sec. 4.4, device
+// level: decoupled lookback over the 3-state flags). Called by one whole warp; every
+// spin is bounded by `deadline`; a wait that runs out reads as a zero inclusive prefix
+// and sets *timed_out (the caller records FSZ_ERR_TIMEOUT and still publishes, so that
+// no successor waits forever).
+__device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchunk, int64_t first,
+                                             uint64_t deadline, bool* timed_out) {
+  const int lane = threadIdx.x & 31;
+  uint64_t excl = 0;
+  bool to = false;
+  int64_t pos = gchunk - 1;
+  while (pos >= first) {
+    const int64_t idx = pos - lane;
+    uint64_t f = kFlagIncl;  // before the field's first chunk: prefix 0
+    if (idx >= first) {
+      f = ld_acquire_u64(flags + idx);
+      uint32_t spins = 0;
+      while ((f >> 62) == 0) {
+        if ((++spins & 63u) == 0 && globaltimer_ns() > deadline) {
+          to = true;
+          f = kFlagIncl;
+          break;
+        }
+        __nanosleep(32);
+        f = ld_acquire_u64(flags + idx);
+      }
+    }
+    __syncwarp();
+    const uint32_t incl = __ballot_sync(0xffffffffu, (f >> 62) >= 2);
+    const int stop = incl ? __ffs(incl) - 1 : 31;
+    excl += warp_sum_u64(lane <= stop ? (f & kFlagValue) : 0);
+    if (incl) break;
+    pos -= 32;
+  }
+  *timed_out = __any_sync(0xffffffffu, to);
+  return excl;
+}
+
+// ------------------------------------------------------------------ float keys
+
+__device__ __forceinline__ uint32_t float_key(float x) {
+  uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+  return __uint_as_float(u);
+}
+
+// 64-byte preamble of this library's stream (little-endian; written once per field by the
+// CTA that finishes the field's last chunk), and the field's total size.
+__device__ __forceinline__ void write_preamble(FieldInfo* fi, uint64_t data_bytes) {
+  uint32_t w[16];
+  w[0] = 0x315A5346u;  // "FSZ1"
+  w[1] = 1u | (fi->ndim << 16) | (fi->mode << 24);
+  w[2] = uint32_t(fi->n);
+  w[3] = uint32_t(fi->n >> 32);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint64_t dk = uint32_t(k) < fi->ndim ? fi->dims[k] : 0;
+    w[4 + 2 * k] = uint32_t(dk);
+    w[5 + 2 * k] = uint32_t(dk >> 32);
+  }
+  const uint64_t eb = static_cast<uint64_t>(__double_as_longlong(fi->eb_req));
+  w[10] = uint32_t(eb);
+  w[11] = uint32_t(eb >> 32);
+  w[12] = __float_as_uint(fi->s);
+  w[13] = 0;
+  w[14] = uint32_t(data_bytes);
+  w[15] = uint32_t(data_bytes >> 32);
+  uint4* dst = reinterpret_cast<uint4*>(fi->out);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) dst[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+  const uint64_t total = 64 + 8 * fi->T + data_bytes;
+  fi->data_bytes = data_bytes;
+  if (fi->out_bytes) *fi->out_bytes = total;
+}
+
+// ------------------------------------------------------------------ launch helpers (host)
+
+struct LaunchCfg {
+  int grid;
+  int smem;
+};
+
+LaunchCfg stats_cfg();
+LaunchCfg compress_cfg();
+LaunchCfg decompress_cfg();
+
+void launch_stats(const KernelArgs& a, cudaStream_t st);
+void launch_compress(const KernelArgs& a, cudaStream_t st);
+void launch_decompress(const KernelArgs& a, cudaStream_t st);
+void launch_setup_compress(const KernelArgs& a, const FieldInfo& fi, cudaStream_t st);
+void launch_setup_decompress(const KernelArgs& a, const uint8_t* in, uint64_t in_bytes, float* out,
+                             uint64_t cap_elems, uint64_t chunk_cap, cudaStream_t st);
+void launch_plan_compress(const KernelArgs& a, const fsz_cfield* d_fields, uint32_t nfields,
+                          uint64_t chunk_cap, cudaStream_t st);
+void launch_plan_decompress(const KernelArgs& a, const fsz_dfield* d_fields, uint32_t nfields,
+                            uint64_t chunk_cap, cudaStream_t st);
+
+}  // namespace fsz

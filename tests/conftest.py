@@ -17,3 +17,12 @@ def oracle():
     import oracle as o
     o.lib()
     return o
+
+
+@pytest.fixture(scope="session")
+def fszlib():
+    """The CUDA library, built in-tree for sm_103a (no CPU fallback exists)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2607_15413_gb300 import fsz
+    return fsz

@@ -159,6 +159,32 @@ fsz_status fsz_check_batched(const void* d_ws, uint32_t nfields, uint32_t* h_sta
 fsz_status fsz_read_header(const void* h_first64, uint64_t* n, fsz_dims* dims, double* eb,
                            float* step, uint64_t* total_bytes);
 
+/* ------------------------------------------------------------------ no-allocation variant */
+
+/* Largest field fsz_compress_noalloc accepts (2^28 elements, 1 GiB of float32). */
+#define FSZ_NOALLOC_MAX_ELEMS (1ull << 28)
+
+/* fsz_compress for callers that cannot allocate device memory (no counterpart in the
+ * paper; an addition of this library). Examples: code that compresses while a stream is
+ * captured in the default global capture mode, where cudaMalloc/cudaFree are not
+ * allowed; plugins whose host framework owns all device memory through its own pool;
+ * latency-critical paths that cannot take the synchronisation an allocation may cause.
+ * The caller passes only the input and output buffers; the scratch the kernels need
+ * lives in a fixed device array of about 0.8 MiB inside the library, which every GPU that
+ * loads the library holds until the process exits. The function allocates nothing.
+ *  - n above FSZ_NOALLOC_MAX_ELEMS returns FSZ_ERR_WORKSPACE; other argument errors as
+ *    fsz_compress.
+ *  - The first call on each device looks up that array's device address (a one-time,
+ *    non-stream runtime call); make that first call before any stream capture begins.
+ *  - All calls share the one array and each clears the part it uses on `stream`. Calls
+ *    whose work overlaps on the GPU (different streams or threads without ordering)
+ *    race on it and produce wrong streams: order them on one stream or serialise them.
+ *  - d_status (device u32, may be NULL) receives the device-detected status of this
+ *    call (0 = FSZ_OK); the stream and d_out_bytes are as for fsz_compress. */
+fsz_status fsz_compress_noalloc(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                                void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
+                                uint32_t* d_status, fsz_stream stream);
+
 /* Test hooks for failure detection (not for production use): the chunk whose global
  * index equals skip_chunk publishes no lookback flag, so its successor's bounded wait
  * runs out after timeout_ns and records FSZ_ERR_TIMEOUT; the kernels still finish.

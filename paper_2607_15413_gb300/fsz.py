@@ -26,7 +26,7 @@ EB_ABS, EB_REL = 0, 1
 EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_bytes", "fsz_compress",
            "fsz_compress_prepare", "fsz_compress_encode", "fsz_decompress", "fsz_compress_batched",
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
-           "fsz_set_test_hooks", "fsz_version"]
+           "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc"]
 
 
 class FszDims(ctypes.Structure):
@@ -90,6 +90,8 @@ def lib():
             L.fsz_read_header.restype = i32
             L.fsz_set_test_hooks.argtypes = [u64, u64]
             L.fsz_set_test_hooks.restype = None
+            L.fsz_compress_noalloc.argtypes = [P, FszDims, i32, f64, P, u64, P, P, P]
+            L.fsz_compress_noalloc.restype = i32
             L.fsz_version.argtypes = []
             L.fsz_version.restype = ctypes.c_char_p
             _lib = L
@@ -169,6 +171,13 @@ def fsz_read_header(h_first64: bytes):
         raise FszError(st, "fsz_read_header")
     return dict(n=n.value, dims=tuple(dims.dims[k] for k in range(dims.ndim)), eb=eb.value,
                 step=step.value, total_bytes=total.value)
+
+
+def fsz_compress_noalloc(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_status,
+                         stream) -> int:
+    """fsz_compress with the library's built-in scratch, for callers that cannot allocate."""
+    return lib().fsz_compress_noalloc(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes,
+                                      d_status, stream)
 
 
 def fsz_set_test_hooks(skip_chunk: int, timeout_ns: int) -> None:

@@ -44,7 +44,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -60,7 +60,7 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                 stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -121,48 +121,63 @@ def barrier(world: int):
         dist.barrier()
 
 
-def cpu_baseline_run(steps: int, warmup: int):
-    """The oracle, single-threaded on the host, on a bounded sample of the workload:
-    the first 2^23 elements (32 MiB) of each field at each bound, compress + decompress."""
-    import numpy as np
+CPU_SAMPLE_SHAPE = (256, 512, 512)  # 2^26 elements per field: about 10-30 s of oracle work
 
-    import oracle
+
+def cpu_sample_fields():
+    """Host copies of the workload's recipe at 2^26 elements per field (numpy, seed 1)."""
     from paper_2607_15413_gb300 import inputs
+    g = inputs.grf(CPU_SAMPLE_SHAPE, seed=1)
+    z = inputs.zero_slabs(CPU_SAMPLE_SHAPE, seed=1, base=g)
+    return [g.ravel(), z.ravel()]
+
+
+def cpu_baseline_run(fields, elems=None):
+    """The oracle, single-threaded on the host, compressing and decompressing the first
+    `elems` elements of each sample field at each of the three bounds."""
+    import oracle
     oracle.build()
-    g = inputs.grf((128, 256, 256), seed=1)  # same recipe, host-sized (2^23 elements)
-    z = inputs.zero_slabs((128, 256, 256), seed=1, base=g)
-    fields = [g.ravel(), z.ravel()]
     nbytes = 0
     t0 = time.perf_counter()
     for f in fields:
+        x = f if elems is None else f[:elems]
         for rel in RELS:
-            s = oracle.compress(f, rel, oracle.REL)
+            s = oracle.compress(x, rel, oracle.REL)
             y = oracle.decompress(s)
-            assert y.size == f.size
-            nbytes += 2 * f.nbytes
+            assert y.size == x.size
+            nbytes += 2 * x.nbytes
     dt = time.perf_counter() - t0
+    n = fields[0].size if elems is None else elems
     return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "first 2^23 elements (32 MiB) of both fields (same generator recipe at "
-                      "128x256x256) at REL 1e-2/1e-3/1e-4, compress + decompress, 1 host core",
+            "sample": f"first {n} elements of both fields (k^-3 GRF and its zero-slab/+280 "
+                      f"variant, same recipe at 256x512x512) at REL 1e-2/1e-3/1e-4, "
+                      f"compress + decompress, 1 host core",
             "seconds": dt}
 
 
 def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle as it stands, one host core. The 2^26-element
+    sample is split across the warm-up and timed steps so any --steps/--warmup stays
+    bounded (about 10-30 s of oracle work in all)."""
     if rank != 0:
         return 0
-    import numpy as np  # noqa: F401
-    vals = []
+    fields = cpu_sample_fields()
+    per = max(1 << 16, (fields[0].size // (args.steps + args.warmup)) // 256 * 256)
+    vals, secs = [], []
     last = None
     for i in range(args.warmup + args.steps):
-        last = cpu_baseline_run(1, 0)
+        k = i % max(1, fields[0].size // per)
+        part = [f[k * per:(k + 1) * per] for f in fields]
+        last = cpu_baseline_run(part)
         if i >= args.warmup:
             vals.append(last["value"])
-    value = statistics.mean(vals)
+            secs.append(last["seconds"])
+    value = len(vals) / sum(1.0 / v for v in vals)  # throughput over the timed steps
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * last["seconds"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (host sample: 2^23 elements per field)",
+            "ms_per_step": 1000.0 * statistics.mean(secs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD + f" (host sample: {per} elements per field per step)",
                        "parallelism": "single host core"},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": value,
                              "unit": "GB/s"},
@@ -174,11 +189,15 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fsz", choices=["fsz", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fields", default="grf,zero_slabs",
+                    help="subset of grf,zero_slabs (smaller cases for profiling)")
+    ap.add_argument("--rels", default=",".join(str(r) for r in RELS),
+                    help="subset of the error bounds (smaller cases for profiling)")
     args = ap.parse_args()
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
@@ -193,7 +212,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_run(1, 0)   # on the host, before any GPU work
+        cpu = cpu_baseline_run(cpu_sample_fields())   # on the host, before any GPU work
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -201,12 +220,19 @@ def main():
     sp = stream.cuda_stream
 
     # inputs resident in HBM
+    want = args.fields.split(",")
     g = inputs.grf(SHAPE, seed=1, device=str(dev)).reshape(-1)
-    z = inputs.zero_slabs(SHAPE, seed=1, device=str(dev), base=g.reshape(SHAPE)).reshape(-1)
-    fields = [("grf", g), ("zero_slabs", z)]
+    fields = []
+    if "grf" in want:
+        fields.append(("grf", g))
+    if "zero_slabs" in want:
+        fields.append(("zero_slabs",
+                       inputs.zero_slabs(SHAPE, seed=1, device=str(dev), base=g.reshape(SHAPE)).reshape(-1)))
+    torch.cuda.empty_cache()
+    rels = [float(r) for r in args.rels.split(",")]
     n = g.numel()
     cap = fsz.fsz_compress_bound(n)
-    jobs = [(name, x, rel) for name, x in fields for rel in RELS]
+    jobs = [(name, x, rel) for name, x in fields for rel in rels]
     outs = [torch.empty(cap, dtype=torch.uint8, device=dev) for _ in jobs]
     recon = torch.empty(n, dtype=torch.float32, device=dev)
     nbytes = torch.zeros(len(jobs), dtype=torch.int64, device=dev)
@@ -344,9 +370,25 @@ def main():
     else:
         kern, algo, dur = "fsz_decompress_kernel (incl. its 1-thread set-up kernel)", dec_bytes * args.steps, dec_tot
     achieved = algo / (dur * 1e-3) / 1e9
+    traffic = None
+    try:  # DRAM bytes of one ncu capture, valid while the kernel's sources are unchanged
+        import hashlib
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kern)
+        if rec:
+            h = hashlib.sha256()
+            for src in rec["sources"]:
+                with open(os.path.join(ROOT, src), "rb") as f:
+                    h.update(f.read())
+            if h.hexdigest() == rec["sha256"]:
+                traffic = rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    except (OSError, KeyError, ValueError):
+        traffic = None
     roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
-                "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS, "traffic": None,
+                "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS, "traffic": traffic,
+                "traffic_note": "dram read+write bytes of one captured launch (512^3 GRF, REL 1e-3; "
+                                "profiles/traffic.json), null once the kernel source changed",
                 "algorithmic_bytes_per_launch": algo / (args.steps * len(jobs))}
 
     per_job = []
@@ -364,7 +406,9 @@ def main():
                 "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_per_field": n, "fields": 2, "rels": list(RELS),
+                "config": {"workload": WORKLOAD if len(jobs) == 6 else
+                           f"subset: fields {args.fields}, REL {args.rels} of: " + WORKLOAD,
+                           "n_per_field": n, "fields": len(fields), "rels": rels,
                            "parallelism": f"replicas x{world} (no data-path collective)",
                            "l2": "inputs 512 MiB > L2; streams read back after >= 2.5 GB of traffic"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

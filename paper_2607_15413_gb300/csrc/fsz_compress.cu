@@ -1,42 +1,75 @@
 // FSZ single-pass compression kernel (Sec. 3.1 steps 1-5, Sec. 4).
 //
-// One persistent CTA of 8 warps loops over chunks of 32 tiles taken from a device
-// ticket. Per chunk:
-//   1. the chunk's 32 KiB were staged in shared memory by a 1-D TMA bulk copy issued
-//      one chunk ahead (double buffer, mbarrier completion);
-//   2. each warp quantizes, predicts, evaluates the four variants, selects and encodes
-//      one tile at a time, entirely from registers, into a per-tile slot in shared
-//      memory (steps 1-3 and 5 of Sec. 3.1: the tile is read once, from shared memory);
-//   3. warp 0 scans the 32 tile sizes, publishes the chunk's aggregate, looks back over
-//      the predecessors' flags for the chunk's exclusive byte offset (step 4, Sec. 4.4)
-//      and publishes the inclusive prefix; the other warps write the rate header;
-//   4. all warps copy the encoded tiles to their final place in the stream.
+// Persistent, warp-specialised CTAs (no CTA-wide barrier in the main loop; the roles
+// hand chunks to one another through mbarriers):
+//   producer warp  takes chunk tickets and stages each chunk of kChunkTiles tiles in
+//                  shared memory with a 1-D TMA bulk copy, kStages chunks ahead;
+//   compute warps  (8) quantize, predict, evaluate the four variants, select and encode
+//                  one tile at a time from registers into a per-tile slot in shared
+//                  memory, and write the tile's rate header (steps 1-3 and 5; the tile is
+//                  read from HBM once);
+//   scanner warp   scans the chunk's tile sizes, publishes the chunk's aggregate flag,
+//                  looks back for the chunk's exclusive byte offset (step 4, Sec. 4.4) and
+//                  publishes the inclusive prefix;
+//   compute warps  copy each chunk's slots to their place in the stream kDefer chunks
+//                  later, by which time the scanner has resolved the chunk's offset.
 #include "fsz_internal.cuh"
 
 namespace fsz {
 
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
+constexpr int kComputeWarps = 8;
+constexpr int kProducerWarp = kComputeWarps;
+constexpr int kScannerWarp = kComputeWarps + 1;
+constexpr int kThreads = (kComputeWarps + 2) * 32;
+constexpr int kStages = 2;            // TMA input stages
+constexpr int kSets = 3;              // slot sets of encoded tiles
+constexpr int kDefer = kSets - 1;     // chunk j is copied out while computing chunk j + kDefer
+constexpr uint32_t kNone = 0xffffffffu;
 constexpr int kSlot = kMaxTileBytes;
-static_assert(kChunkTiles == 32, "one lane per tile in the chunk scan");
+static_assert(kChunkTiles <= 32, "one lane per tile in the chunk scan");
 static_assert(kSlot % 4 == 0, "slots hold 32-bit words");
 
-struct __align__(16) CompressSmem {
-  float in[2][kChunkElems];
-  uint8_t slot[kChunkTiles][kSlot];
-  uint8_t hdr[kChunkTiles * 8];
-  uint32_t tbytes[kChunkTiles];
-  uint32_t toff[kChunkTiles];
-  uint64_t bar[2];
-  uint64_t excl;
-  uint32_t chunk[2];
-  uint32_t total;
-  uint32_t abort;
+// A chunk's parameters, read once from the field record by the producer and handed to the
+// other warps through shared memory (keeps dependent global loads off the compute path).
+constexpr uint32_t kInfoOk = 1u, kInfoLast = 2u, kInfoFirst = 4u, kInfoSkip = 8u;
+struct ChunkInfo {
+  const float* in;       // the chunk's first element
+  uint8_t* out;          // the field's stream
+  FieldInfo* fi;
+  uint64_t tile0;        // field-local index of the chunk's first tile
+  uint64_t data_base;    // 64 + 8T: start of the field's tile data
+  uint64_t cap;          // the field's output capacity
+  uint64_t chunk_first;  // global index of the field's first chunk
+  uint32_t chunk;        // global ticket, or kNone
+  uint32_t ntiles;
+  uint32_t cnt;          // valid elements in the chunk
+  uint32_t bulk_elems;   // elements covered by the TMA copy
+  float r;
+  uint32_t flags;        // kInfo* bits
 };
 
-__device__ __forceinline__ uint32_t block_cost(int R) { return R ? 4u + 4u * uint32_t(R) : 0u; }
+struct __align__(16) CompressSmem {
+  float in[kStages][kChunkElems];            // TMA stages
+  uint8_t slot[kSets][kChunkTiles][kSlot];   // encoded tiles awaiting their offset
+  uint64_t hdr[kComputeWarps];               // per-warp scratch: one tile's 8 header bytes
+  uint32_t tbytes[kSets][kChunkTiles];
+  uint32_t toff[kSets][kChunkTiles];
+  uint64_t set_excl[kSets];
+  uint32_t set_total[kSets];
+  ChunkInfo stage_info[kStages];             // producer -> compute warps
+  ChunkInfo pre[2];                          // producer's tickets taken ahead
+  ChunkInfo set_info[kSets];                 // compute warp 0 -> scanner
+  ChunkInfo warp_info[kComputeWarps][kSets]; // each compute warp's own copy, for its copy-out
+  uint64_t full[kStages], empty[kStages], computed[kSets], resolved[kSets];
+};
+
+// Eq. 3: S_b = 0 for r_b = 0, else 4 + 4 r_b.
+__device__ __forceinline__ uint32_t block_cost(int R) { return (uint32_t(R) + (R != 0 ? 1u : 0u)) << 2; }
+
+// v = 2|l| + sign: bit 0 is the sign-map bit, bit k + 1 magnitude bit-plane k (Sec. 4.3).
+__device__ __forceinline__ uint32_t sign_mag(int l) { return (uabs32(l) << 1) | (uint32_t(l) >> 31); }
 
 // Compresses the 256-element tile at `tile` (shared memory) with one warp. Lane j owns
 // elements 8j..8j+7; the 4 lanes 4g..4g+3 own block g. Writes the tile's 8 rate-header
@@ -144,14 +177,16 @@ __device__ __forceinline__ uint32_t compress_tile(const float* __restrict__ tile
   // Step 5: residuals of the selected variant as sign-magnitude words v = 2|l| + sign,
   // so that bit 0 is the sign map and bit k + 1 is magnitude bit-plane k (Sec. 4.3).
   uint32_t vv[8];
+  if (second) {  // the variant is warp-uniform
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    int l = second ? l2[i] : l1[i];
-    if (centred && lane == 0) {
-      if (i == 0) l = q0 - mu;
-      if (i == 1 && second) l = l2[1] + mu;
-    }
-    vv[i] = (uabs32(l) << 1) | (uint32_t(l) >> 31);
+    for (int i = 0; i < 8; ++i) vv[i] = sign_mag(l2[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) vv[i] = sign_mag(l1[i]);
+  }
+  if (centred && lane == 0) {
+    vv[0] = sign_mag(q0 - mu);
+    if (second) vv[1] = sign_mag(l2[1] + mu);
   }
 
   // Byte offset of block g inside the tile's data (after mu when centred).
@@ -188,150 +223,237 @@ __device__ __forceinline__ uint32_t compress_tile(const float* __restrict__ tile
   return uint32_t(best);
 }
 
-__global__ void __launch_bounds__(kThreads, 2) fsz_compress_kernel(KernelArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   CompressSmem& S = *reinterpret_cast<CompressSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t total = a.ctrl->total_chunks;
+  // mbarrier waits outlast the longest lookback wait, so a lookback that runs out is
+  // reported as such rather than as a stalled pipeline.
+  const uint64_t wait_ns = 4 * a.timeout_ns;
 
   if (tid == 0) {
-    mbar_init(&S.bar[0], 1);
-    mbar_init(&S.bar[1], 1);
-    fence_mbar_init();
-    S.abort = 0;
-  }
-  __syncthreads();
-
-  // Takes the next ticket into stage s and starts its TMA load (thread 0).
-  auto issue = [&](int s) {
-    const uint32_t c = atomicAdd(&a.ctrl->ticket, 1u);
-    S.chunk[s] = c;
-    if (c < total) {
-      const FieldInfo* fi = a.fields + a.chunk_field[c];
-      const uint64_t e0 = (c - fi->chunk_first) * uint64_t(kChunkElems);
-      const uint64_t cnt = min(fi->n - e0, uint64_t(kChunkElems));
-      uint32_t bulk = uint32_t(cnt * 4) & ~15u;
-      if (!(fi->s > 0.0f)) bulk = 0;  // field without a step: nothing to load
-      fence_proxy_async();
-      mbar_arrive_expect_tx(&S.bar[s], bulk);
-      if (bulk) tma_load_1d(S.in[s], fi->in + e0, bulk, &S.bar[s]);
+    for (int k = 0; k < kStages; ++k) {
+      mbar_init(&S.full[k], 1);
+      mbar_init(&S.empty[k], kComputeWarps);
     }
-  };
-
-  if (tid == 0) {
-    issue(0);
-    issue(1);
+    for (int k = 0; k < kSets; ++k) {
+      mbar_init(&S.computed[k], kComputeWarps);
+      mbar_init(&S.resolved[k], 1);
+    }
+    fence_mbar_init();
   }
   __syncthreads();
 
-  for (uint32_t it = 0;; ++it) {
-    const int s = it & 1;
-    const uint32_t c = S.chunk[s];
-    if (c >= total) break;
-    FieldInfo* fi = a.fields + a.chunk_field[c];
-    const float r = fi->r;
-    const bool ok = fi->s > 0.0f;
-    const uint64_t lc = c - fi->chunk_first;
-    const uint64_t T = fi->T;
-    const uint64_t tile0 = lc * kChunkTiles;
-    const int ntiles = int(min(uint64_t(kChunkTiles), T - tile0));
-    const uint64_t e0 = tile0 * kTile;
-    const uint32_t cnt = uint32_t(min(fi->n - e0, uint64_t(kChunkElems)));
+  if (warp == kProducerWarp) {
+    // ---------------------------------------------------------------- producer
+    // Tickets are taken two chunks ahead, so the ticket atomic and the field-record loads
+    // overlap the wait for a free stage; a free stage is refilled at once.
+    if (lane != 0) return;
+    const bool single = a.ctrl->nfields == 1;
+    auto fetch = [&](ChunkInfo& ci) {
+      const uint32_t c = atomicAdd(&a.ctrl->ticket, 1u);
+      ci.chunk = c;
+      if (c >= total) return;
+      FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
+      const uint64_t first = fi->chunk_first;
+      const uint64_t lc = c - first;
+      const uint64_t tile0 = lc * kChunkTiles;
+      const uint64_t e0 = tile0 * kTile;
+      const uint64_t T = fi->T;
+      const uint32_t cnt = uint32_t(min(fi->n - e0, uint64_t(kChunkElems)));
+      const bool ok = fi->s > 0.0f;  // a field without a step has nothing to load
+      ci.in = fi->in + e0;
+      ci.out = fi->out;
+      ci.fi = fi;
+      ci.tile0 = tile0;
+      ci.data_base = 64 + 8 * T;
+      ci.cap = fi->cap;
+      ci.chunk_first = first;
+      ci.ntiles = uint32_t(min(uint64_t(kChunkTiles), T - tile0));
+      ci.cnt = cnt;
+      ci.bulk_elems = ok ? ((cnt * 4) & ~15u) / 4 : 0u;
+      ci.r = fi->r;
+      ci.flags = (ok ? kInfoOk : 0u) | (lc + 1 == fi->nchunks ? kInfoLast : 0u) |
+                 (lc == 0 ? kInfoFirst : 0u) | (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
+    };
+    fetch(S.pre[0]);
+    fetch(S.pre[1]);
+    for (uint32_t j = 0;; ++j) {
+      const int s = int(j % kStages);
+      if (j >= uint32_t(kStages) && !mbar_wait(&S.empty[s], ((j / kStages) - 1) & 1u, wait_ns)) {
+        set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      ChunkInfo& q = S.pre[j & 1];
+      S.stage_info[s] = q;
+      if (q.chunk >= total) {
+        S.stage_info[s].chunk = kNone;
+        mbar_arrive(&S.full[s]);
+        return;
+      }
+      const uint32_t bulk = q.bulk_elems * 4;
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&S.full[s], bulk);
+      if (bulk) tma_load_1d(S.in[s], q.in, bulk, &S.full[s]);
+      fetch(q);  // the ticket two chunks ahead
+    }
+  }
 
-    // Wait for the stage (bounded); one thread waits, the barrier publishes the data.
-    if (tid == 0) {
-      const uint32_t parity = (it >> 1) & 1u;
-      uint64_t deadline = 0;
-      uint32_t spins = 0;
-      while (!mbar_try_wait(&S.bar[s], parity)) {
-        if ((++spins & 255u) == 0) {
-          const uint64_t now = globaltimer_ns();
-          if (deadline == 0) {
-            deadline = now + a.timeout_ns;
-          } else if (now > deadline) {
-            set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
-            S.abort = 1;
-            break;
-          }
+  if (warp == kScannerWarp) {
+    // ---------------------------------------------------------------- scanner
+    // Chunk j's aggregate is published as soon as its tiles are encoded; chunk j's
+    // lookback waits until chunk j + 1 is encoded, so that the chunks ticketed next to
+    // chunk j on other SMs have published theirs by then.
+    uint32_t prev_c = kNone, prev_tot = 0, prev_flags = 0;
+    uint64_t prev_first = 0;
+    FieldInfo* prev_fi = nullptr;
+    int prev_b = 0;
+    auto resolve = [&](uint32_t c, uint64_t first, uint32_t flags, FieldInfo* fi, uint32_t tot, int b) {
+      uint64_t excl = 0;
+      if (!(flags & kInfoFirst)) {
+        bool to = false;
+        excl = lookback(a.flags, int64_t(c), int64_t(first), globaltimer_ns() + a.timeout_ns, &to);
+        if (lane == 0) {
+          if (to) set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
+          if (!(flags & kInfoSkip)) st_flag(a.flags + c, kFlagIncl | (excl + tot));
         }
       }
-    }
-    __syncthreads();
-    if (S.abort) return;
-
-    // Ragged end of a field: the bytes past the last 16-byte boundary by plain loads, and
-    // zero padding up to the tile boundary (padding elements quantize to 0).
-    if (ok && cnt < uint32_t(ntiles) * kTile) {
-      const uint32_t bulk_elems = (cnt * 4 & ~15u) / 4;
-      float* buf = S.in[s];
-      for (uint32_t k = bulk_elems + tid; k < uint32_t(ntiles) * kTile; k += kThreads)
-        buf[k] = k < cnt ? fi->in[e0 + k] : 0.0f;
-      __syncthreads();
-    }
-
-    if (ok) {
-      for (int tl = warp; tl < ntiles; tl += kWarps) {
-        const uint32_t b = compress_tile(S.in[s] + tl * kTile, S.slot[tl], S.hdr + tl * 8, r, lane);
-        if (lane == 0) S.tbytes[tl] = b;
+      __syncwarp();
+      if (lane == 0) {
+        S.set_excl[b] = excl;
+        S.set_total[b] = tot;
+        mbar_arrive(&S.resolved[b]);
       }
-    }
-    __syncthreads();
-    if (tid == 32) issue(s);  // the stage is consumed: refill it (warp 0 scans meanwhile)
-
-    if (warp == 0) {
-      // Step 4 (Sec. 4.4): thread/warp level over the chunk's tiles, then device level.
-      const uint32_t mine = (ok && lane < ntiles) ? S.tbytes[lane] : 0u;
+    };
+    for (uint32_t j = 0;; ++j) {
+      const int b = int(j % kSets);
+      if (!mbar_wait(&S.computed[b], (j / kSets) & 1u, wait_ns)) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      const ChunkInfo& ci = S.set_info[b];
+      const uint32_t c = ci.chunk;
+      if (c == kNone) break;
+      const uint32_t flags = ci.flags;
+      const int ntiles = int(ci.ntiles);
+      // Thread and warp levels of the scan over the chunk's tiles; the chunk's aggregate.
+      const uint32_t mine = ((flags & kInfoOk) && lane < ntiles) ? S.tbytes[b][lane] : 0u;
       uint32_t inc = mine;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += x;
       }
-      if (lane < ntiles) S.toff[lane] = inc - mine;
+      if (lane < kChunkTiles) S.toff[b][lane] = inc - mine;
       const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-      const bool skip = (uint64_t(c) == a.skip_chunk);
-      const bool first = (lc == 0);
-      if (lane == 0 && !skip) st_release_u64(a.flags + c, (first ? kFlagIncl : kFlagAgg) | tot);
-      uint64_t excl = 0;
-      if (!first) {
-        bool to = false;
-        excl = lookback(a.flags, int64_t(c), int64_t(fi->chunk_first),
-                        globaltimer_ns() + a.timeout_ns, &to);
-        if (lane == 0) {
-          if (to) set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
-          if (!skip) st_release_u64(a.flags + c, kFlagIncl | (excl + tot));
-        }
-      }
-      if (lane == 0) {
-        S.excl = excl;
-        S.total = tot;
-      }
-    } else if (ok) {
-      // Rate header of the chunk's tiles: 8 bytes per tile at 64 + 8 * tile.
-      const uint32_t* h32 = reinterpret_cast<const uint32_t*>(S.hdr);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(fi->out + 64 + 8 * tile0);
-      for (int k = tid - 32; k < 2 * ntiles; k += kThreads - 32) dst[k] = h32[k];
+      if (lane == 0 && !(flags & kInfoSkip))
+        st_flag(a.flags + c, ((flags & kInfoFirst) ? kFlagIncl : kFlagAgg) | tot);
+      // Device level for the previous chunk.
+      if (prev_c != kNone) resolve(prev_c, prev_first, prev_flags, prev_fi, prev_tot, prev_b);
+      prev_c = c;
+      prev_first = ci.chunk_first;
+      prev_flags = flags;
+      prev_fi = ci.fi;
+      prev_tot = tot;
+      prev_b = b;
     }
-    __syncthreads();
+    if (prev_c != kNone) resolve(prev_c, prev_first, prev_flags, prev_fi, prev_tot, prev_b);
+    return;
+  }
 
-    if (ok && uint64_t(c) != a.skip_chunk) {
-      const uint64_t excl = S.excl;
-      const uint32_t tot = S.total;
-      const uint64_t data_base = 64 + 8 * T;
-      if (data_base + excl + tot > fi->cap) {
-        if (tid == 0) set_error(a.ctrl, fi, FSZ_ERR_CAPACITY);
-      } else {
-        uint8_t* base = fi->out + data_base + excl;
-        for (int tl = warp; tl < ntiles; tl += kWarps) {
-          const uint32_t nw = S.tbytes[tl] >> 2;
-          const uint32_t* src = reinterpret_cast<const uint32_t*>(S.slot[tl]);
-          uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[tl]);
-          for (uint32_t k = lane; k < nw; k += 32) dst[k] = src[k];
-        }
+  // ------------------------------------------------------------------ compute warps
+  // Copies this warp's tiles of chunk k (slot set k % kSets) into the stream.
+  auto copy_out = [&](uint32_t k) -> bool {
+    const int b = int(k % kSets);
+    if (!mbar_wait(&S.resolved[b], (k / kSets) & 1u, wait_ns)) return false;
+    const ChunkInfo& ci = S.warp_info[warp][b];
+    if ((ci.flags & (kInfoOk | kInfoSkip)) != kInfoOk) return true;
+    const uint64_t excl = S.set_excl[b];
+    const uint32_t tot = S.set_total[b];
+    if (ci.data_base + excl + tot > ci.cap) {
+      if (lane == 0) set_error(a.ctrl, ci.fi, FSZ_ERR_CAPACITY);
+    } else {
+      uint8_t* base = ci.out + ci.data_base + excl;
+      for (int tl = warp; tl < int(ci.ntiles); tl += kComputeWarps) {
+        const uint32_t nw = S.tbytes[b][tl] >> 2;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(S.slot[b][tl]);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][tl]);
+        for (uint32_t q = lane; q < nw; q += 32) dst[q] = src[q];
       }
-      if (tid == 0 && lc + 1 == fi->nchunks) write_preamble(fi, excl + tot);
+      if (warp == 0 && lane == 0 && (ci.flags & kInfoLast)) write_preamble(ci.fi, excl + tot);
     }
-    __syncthreads();
+    return true;
+  };
+
+  uint32_t j = 0;
+  for (;; ++j) {
+    const int s = int(j % kStages), b = int(j % kSets);
+    if (!mbar_wait(&S.full[s], (j / kStages) & 1u, wait_ns)) {
+      if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+      return;
+    }
+    const ChunkInfo& ci = S.stage_info[s];
+    // Keep the chunk's parameters past the stage's reuse: this warp's copy, and warp 0's
+    // copy for the scanner (16 lanes copy 4 bytes each).
+    static_assert(sizeof(ChunkInfo) % 4 == 0 && sizeof(ChunkInfo) <= 128, "ChunkInfo copy");
+    if (lane < int(sizeof(ChunkInfo) / 4)) {
+      const uint32_t w = reinterpret_cast<const uint32_t*>(&ci)[lane];
+      reinterpret_cast<uint32_t*>(&S.warp_info[warp][b])[lane] = w;
+      if (warp == 0) reinterpret_cast<uint32_t*>(&S.set_info[b])[lane] = w;
+    }
+    if (warp == 0) __threadfence_block();  // all lanes' copies before lane 0's arrival
+    const uint32_t c = ci.chunk;
+    if (c == kNone) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.computed[b]);  // tells the scanner to stop
+      break;
+    }
+    const uint32_t flags = ci.flags;
+    if (flags & kInfoOk) {
+      const float r = ci.r;
+      const int ntiles = int(ci.ntiles);
+      const uint32_t cnt = ci.cnt, bulk_elems = ci.bulk_elems;
+      const float* gin = ci.in;
+      uint64_t* hdr_out = reinterpret_cast<uint64_t*>(ci.out + 64) + ci.tile0;
+      for (int tl = warp; tl < ntiles; tl += kComputeWarps) {
+        float* tile = S.in[s] + tl * kTile;
+        // Ragged end of a field: this lane's elements past the last 16-byte boundary of
+        // the bulk copy by plain loads; padding elements are zeros (they quantize to 0).
+        const uint32_t k0 = uint32_t(tl) * kTile + 8u * uint32_t(lane);
+        if (k0 + 8 > bulk_elems) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const uint32_t k = k0 + uint32_t(i);
+            if (k >= bulk_elems) tile[8 * lane + i] = k < cnt ? gin[k] : 0.0f;
+          }
+        }
+        const uint32_t nb = compress_tile(tile, S.slot[b][tl],
+                                          reinterpret_cast<uint8_t*>(&S.hdr[warp]), r, lane);
+        __syncwarp();
+        if (lane == 0) {
+          S.tbytes[b][tl] = nb;
+          hdr_out[tl] = S.hdr[warp];
+        }
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&S.empty[s]);     // done reading the stage
+      mbar_arrive(&S.computed[b]);  // tile sizes ready for the scanner
+    }
+    if (j >= uint32_t(kDefer) && !copy_out(j - kDefer)) {
+      if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+      return;
+    }
+  }
+  // Chunks computed but not yet placed.
+  for (uint32_t k = j >= uint32_t(kDefer) ? j - kDefer : 0; k < j; ++k) {
+    if (!copy_out(k)) {
+      if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+      return;
+    }
   }
 }
 

@@ -1,42 +1,55 @@
 // FSZ decompression kernel (Sec. 3.1 "Decompression", steps d1-d5).
 //
-// One persistent CTA of 8 warps, software-pipelined over chunks of 32 tiles:
-//   prepare(next)  [warp 0]  d1 read the chunk's rate header, d2 tile sizes, d3 scan:
-//                            warp scan over tiles, then decoupled lookback over chunks;
-//                            then a 1-D TMA bulk load of the chunk's payload into the
-//                            other shared-memory stage;
-//   decode(cur)    [warps]   d4 bit-unshuffle each tile with one warp (lane j owns
-//                            elements 8j..8j+7), d5 inverse prediction as warp-wide
-//                            prefix sums (once for LZ1, twice for LZ2), + mu, then
-//                            d' = fl(float(q) s) into shared memory;
-//   store(cur)               1-D TMA bulk store of the decoded floats.
-// Warp 0 joins the tile queue once its prepare step is done.
+// Persistent, warp-specialised CTAs; the roles hand chunks to one another through
+// mbarriers, kStages chunks deep:
+//   header warp   takes a ticket, d1 reads the chunk's rate header, d2 derives the tile
+//                 sizes and scans them, and publishes the chunk's aggregate flag at once;
+//   loader warp   d3 looks back for the chunk's byte offset (decoupled lookback), publishes
+//                 the inclusive prefix and loads the chunk's payload into shared memory
+//                 with a 1-D TMA bulk copy;
+//   decode warps  (8) d4 bit-unshuffle one tile at a time (lane j owns elements 8j..8j+7),
+//                 d5 invert the prediction as warp-wide prefix sums (once for LZ1, twice
+//                 for LZ2), add mu, d' = fl(float(q) s), and store the tile with a 1-D TMA
+//                 bulk store from a per-warp double buffer.
 #include "fsz_internal.cuh"
 
 namespace fsz {
 
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
+constexpr int kDecodeWarps = 8;
+constexpr int kHeaderWarp = kDecodeWarps;
+constexpr int kLoaderWarp = kDecodeWarps + 1;
+constexpr int kThreads = (kDecodeWarps + 2) * 32;
+constexpr int kStages = 3;
 constexpr int kPayloadBytes = kChunkTiles * kMaxDecTileBytes + 32;
-static_assert(kChunkTiles == 32, "one lane per tile in the chunk scan");
+static_assert(kChunkTiles <= 32, "one lane per tile in the chunk scan");
 static_assert(kPayloadBytes % 16 == 0, "stage size");
+constexpr uint32_t kNoneChunk = 0xffffffffu;
+
+// A chunk's header and parameters, handed from the header warp to the loader and the
+// decode warps through shared memory (keeps dependent global loads off the decode path).
+struct StageInfo {
+  uint64_t hdr[kChunkTiles];
+  uint32_t toff[kChunkTiles];
+  FieldInfo* fi;
+  float* dout;     // the chunk's first output element
+  uint32_t chunk;  // ticket held by the stage
+  uint32_t tot;    // payload bytes of the chunk
+  uint32_t bad;    // reserved header bits seen
+  uint32_t valid;  // payload loaded and decodable
+  uint32_t shift;  // payload start inside the stage
+  uint32_t ntiles;
+  uint32_t cnt;    // valid elements of the chunk
+  float step;
+};
 
 struct __align__(16) DecompressSmem {
-  uint8_t payload[2][kPayloadBytes];
-  float out[kChunkElems];
-  uint64_t hdr[2][kChunkTiles];
-  uint32_t toff[2][kChunkTiles];
-  uint64_t bar[2];
-  uint64_t gbase[2];      // 16-byte aligned global address the stage starts at
-  uint32_t chunk[2];      // ticket held by the stage
-  uint32_t shift[2];      // payload start inside the stage
-  uint32_t tail_lo[2];    // [tail_lo, tail_hi): bytes after the bulk part, plain loads
-  uint32_t tail_hi[2];
-  uint32_t valid[2];
-  uint32_t next_tile;
-  uint32_t abort;
+  uint8_t payload[kStages][kPayloadBytes];
+  float out[kDecodeWarps][2][kTile];  // per-warp double buffer for the TMA stores
+  StageInfo st[kStages];
+  StageInfo pre[2];                   // the header warp's tickets taken ahead
+  uint64_t hready[kStages], full[kStages], empty[kStages];
 };
 
 // Bytes of a tile from its 8 header bytes: sum of S_b (Eq. 3) + 4 for a centred tile.
@@ -140,152 +153,198 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint8_t*
   return __all_sync(FULL, good);
 }
 
-__global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   DecompressSmem& S = *reinterpret_cast<DecompressSmem*>(smem_raw);
   constexpr uint32_t FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t total = a.ctrl->total_chunks;
+  const uint64_t wait_ns = 4 * a.timeout_ns;
 
   if (tid == 0) {
-    mbar_init(&S.bar[0], 1);
-    mbar_init(&S.bar[1], 1);
+    for (int k = 0; k < kStages; ++k) {
+      mbar_init(&S.hready[k], 1);
+      mbar_init(&S.full[k], 1);
+      mbar_init(&S.empty[k], kDecodeWarps);
+    }
     fence_mbar_init();
-    S.abort = 0;
-    S.next_tile = 0;
   }
   __syncthreads();
 
-  // d1-d3 for the next ticket, and the payload load into stage s (one whole warp).
-  auto prepare = [&](int s) {
-    uint32_t c = 0;
-    if (lane == 0) c = atomicAdd(&a.ctrl->ticket, 1u);
-    c = __shfl_sync(FULL, c, 0);
-    if (lane == 0) S.chunk[s] = c;
-    if (c >= total) return;
-    FieldInfo* fi = a.fields + a.chunk_field[c];
-    const uint64_t lc = c - fi->chunk_first;
-    const uint64_t T = fi->T;
-    const uint64_t tile0 = lc * kChunkTiles;
-    const int ntiles = int(min(uint64_t(kChunkTiles), T - tile0));
-    uint64_t h = 0;
-    if (lane < ntiles) h = __ldg(reinterpret_cast<const unsigned long long*>(fi->sin + 64) + tile0 + lane);
-    S.hdr[s][lane] = h;
-    const bool bad_hdr = __any_sync(FULL, lane < ntiles && header_reserved_bits_set(h));
-    const uint32_t mine = lane < ntiles ? tile_bytes_from_header(h) : 0u;
-    uint32_t inc = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += y;
-    }
-    S.toff[s][lane] = inc - mine;
-    const uint32_t tot = __shfl_sync(FULL, inc, 31);
-    const bool skip = (uint64_t(c) == a.skip_chunk);
-    const bool first = (lc == 0);
-    if (lane == 0 && !skip) st_release_u64(a.flags + c, (first ? kFlagIncl : kFlagAgg) | tot);
-    uint64_t excl = 0;
-    if (!first) {
-      bool to = false;
-      excl = lookback(a.flags, int64_t(c), int64_t(fi->chunk_first), globaltimer_ns() + a.timeout_ns,
-                      &to);
-      if (lane == 0) {
-        if (to) set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
-        if (!skip) st_release_u64(a.flags + c, kFlagIncl | (excl + tot));
+  if (warp == kHeaderWarp) {
+    // ---------------------------------------------------------------- header warp
+    // Tickets are taken two chunks ahead: d1-d2 and the chunk's aggregate flag happen at
+    // once, so successors find the aggregate early; a freed stage is refilled from there.
+    const bool single = a.ctrl->nfields == 1;
+    auto fetch = [&](StageInfo& q) {
+      uint32_t c = 0;
+      if (lane == 0) c = atomicAdd(&a.ctrl->ticket, 1u);
+      c = __shfl_sync(FULL, c, 0);
+      if (c >= total) {
+        if (lane == 0) q.chunk = kNoneChunk;
+        return;
       }
-    }
-    if (lane == 0) {
-      const uint64_t data_base = 64 + 8 * T;
-      bool valid = !bad_hdr && !skip;
-      if (data_base + excl + tot > fi->in_bytes) valid = false;
-      if (lc + 1 == fi->nchunks && excl + tot != fi->data_bytes) valid = false;
-      if (!valid && !skip) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
-      const uint64_t src = reinterpret_cast<uint64_t>(fi->sin) + data_base + excl;
-      const uint64_t a0 = src & ~uint64_t(15);
-      const uint64_t a1 = (src + tot) & ~uint64_t(15);
-      const uint32_t bulk = (valid && a1 > a0) ? uint32_t(a1 - a0) : 0u;
-      S.gbase[s] = a0;
-      S.shift[s] = uint32_t(src - a0);
-      S.tail_lo[s] = uint32_t(max(a1, src) - a0);
-      S.tail_hi[s] = uint32_t(src + tot - a0);
-      S.valid[s] = valid ? 1u : 0u;
-      fence_proxy_async();
-      mbar_arrive_expect_tx(&S.bar[s], bulk);
-      if (bulk) tma_load_1d(S.payload[s], reinterpret_cast<const void*>(a0), bulk, &S.bar[s]);
-    }
+      FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
+      const uint64_t lc = c - fi->chunk_first;
+      const uint64_t tile0 = lc * kChunkTiles;
+      const int ntiles = int(min(uint64_t(kChunkTiles), fi->T - tile0));
+      uint64_t hb = 0;
+      if (lane < ntiles) hb = __ldg(reinterpret_cast<const unsigned long long*>(fi->sin + 64) + tile0 + lane);
+      if (lane < kChunkTiles) q.hdr[lane] = hb;
+      const bool bad_hdr = __any_sync(FULL, lane < ntiles && header_reserved_bits_set(hb));
+      const uint32_t mine = lane < ntiles ? tile_bytes_from_header(hb) : 0u;
+      uint32_t inc = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane < kChunkTiles) q.toff[lane] = inc - mine;
+      const uint32_t tot = __shfl_sync(FULL, inc, 31);
+      if (lane == 0) {
+        q.chunk = c;
+        q.tot = tot;
+        q.bad = bad_hdr ? 1u : 0u;
+        q.fi = fi;
+        q.dout = fi->dout + tile0 * kTile;
+        q.ntiles = uint32_t(ntiles);
+        q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kChunkElems)));
+        q.step = fi->s;
+        if (uint64_t(c) != a.skip_chunk) st_flag(a.flags + c, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
+      }
+    };
+    fetch(S.pre[0]);
+    fetch(S.pre[1]);
     __syncwarp();
-  };
+    for (uint32_t j = 0;; ++j) {
+      const int p = int(j % kStages);
+      if (j >= uint32_t(kStages) && !mbar_wait(&S.empty[p], ((j / kStages) - 1) & 1u, wait_ns)) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      StageInfo& q = S.pre[j & 1];
+      StageInfo& st = S.st[p];
+      // hand the prefetched chunk to the loader (32 lanes copy the record)
+      constexpr int kWords = int(sizeof(StageInfo) / 4);
+      static_assert(sizeof(StageInfo) % 4 == 0, "StageInfo copy");
+      for (int w = lane; w < kWords; w += 32)
+        reinterpret_cast<uint32_t*>(&st)[w] = reinterpret_cast<const uint32_t*>(&q)[w];
+      __threadfence_block();
+      __syncwarp();
+      const bool none = st.chunk == kNoneChunk;
+      if (lane == 0) mbar_arrive(&S.hready[p]);
+      if (none) return;
+      fetch(q);  // the ticket two chunks ahead
+      __syncwarp();
+    }
+  }
 
-  if (warp == 0) prepare(0);
-  __syncthreads();
-
-  for (uint32_t it = 0;; ++it) {
-    const int s = it & 1;
-    const uint32_t c = S.chunk[s];
-    if (c >= total) break;
-    FieldInfo* fi = a.fields + a.chunk_field[c];
-    const float step = fi->s;
-    const uint64_t lc = c - fi->chunk_first;
-    const uint64_t tile0 = lc * kChunkTiles;
-    const int ntiles = int(min(uint64_t(kChunkTiles), fi->T - tile0));
-    const uint64_t e0 = tile0 * kTile;
-    const uint32_t cnt = uint32_t(min(fi->n - e0, uint64_t(kChunkElems)));
-
-    if (tid == 0) {
-      const uint32_t parity = (it >> 1) & 1u;
-      uint64_t deadline = 0;
-      uint32_t spins = 0;
-      while (!mbar_try_wait(&S.bar[s], parity)) {
-        if ((++spins & 255u) == 0) {
-          const uint64_t now = globaltimer_ns();
-          if (deadline == 0) {
-            deadline = now + a.timeout_ns;
-          } else if (now > deadline) {
-            set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
-            S.abort = 1;
-            break;
-          }
+  if (warp == kLoaderWarp) {
+    // ---------------------------------------------------------------- loader warp
+    for (uint32_t j = 0;; ++j) {
+      const int p = int(j % kStages);
+      if (!mbar_wait(&S.hready[p], (j / kStages) & 1u, wait_ns)) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      StageInfo& st = S.st[p];
+      const uint32_t c = st.chunk;
+      if (c == kNoneChunk) {
+        if (lane == 0) mbar_arrive(&S.full[p]);
+        return;
+      }
+      FieldInfo* fi = st.fi;
+      const uint64_t lc = c - fi->chunk_first;
+      const uint32_t tot = st.tot;
+      const bool skip = (uint64_t(c) == a.skip_chunk);
+      uint64_t excl = 0;
+      if (lc != 0) {
+        bool to = false;
+        excl = lookback(a.flags, int64_t(c), int64_t(fi->chunk_first), globaltimer_ns() + a.timeout_ns,
+                        &to);
+        if (lane == 0) {
+          if (to) set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
+          if (!skip) st_flag(a.flags + c, kFlagIncl | (excl + tot));
         }
       }
-      tma_store_wait_read_all();  // the previous chunk's store has read S.out
-      S.next_tile = 0;
-    }
-    __syncthreads();
-    if (S.abort) break;
-    const bool valid = S.valid[s] != 0;
-    if (valid) {
-      // Payload bytes past the last 16-byte boundary of the bulk copy.
-      const uint8_t* gb = reinterpret_cast<const uint8_t*>(S.gbase[s]);
-      for (uint32_t k = S.tail_lo[s] + 4 * tid; k < S.tail_hi[s]; k += 4 * kThreads)
-        *reinterpret_cast<uint32_t*>(S.payload[s] + k) = *reinterpret_cast<const uint32_t*>(gb + k);
-    }
-    __syncthreads();
-
-    if (warp == 0) prepare(s ^ 1);
-    if (valid) {
-      bool good = true;
-      for (;;) {
-        uint32_t tl = 0;
-        if (lane == 0) tl = atomicAdd(&S.next_tile, 1u);
-        tl = __shfl_sync(FULL, tl, 0);
-        if (tl >= uint32_t(ntiles)) break;
-        good &= decompress_tile(S.hdr[s][tl], S.payload[s] + S.shift[s] + S.toff[s][tl],
-                                S.out + tl * kTile, step, lane);
+      const uint64_t data_base = 64 + 8 * fi->T;
+      bool valid = st.bad == 0 && !skip;
+      if (data_base + excl + tot > fi->in_bytes) valid = false;
+      if (lc + 1 == fi->nchunks && excl + tot != fi->data_bytes) valid = false;
+      const uint64_t src = reinterpret_cast<uint64_t>(fi->sin) + data_base + excl;
+      const uint64_t a0 = src & ~uint64_t(15);
+      // Round the copy's end up to 16 bytes while that stays inside the stream buffer;
+      // otherwise the last few bytes come by plain loads.
+      const uint64_t end_up = (src + tot + 15) & ~uint64_t(15);
+      const uint64_t a1 = end_up <= reinterpret_cast<uint64_t>(fi->sin) + fi->in_bytes
+                              ? end_up : ((src + tot) & ~uint64_t(15));
+      const uint32_t bulk = (valid && a1 > a0) ? uint32_t(a1 - a0) : 0u;
+      if (lane == 0) {
+        if (!valid && !skip) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
+        st.shift = uint32_t(src - a0);
+        st.valid = valid ? 1u : 0u;
+        if (bulk) {
+          fence_proxy_async();
+          mbar_expect_tx(&S.full[p], bulk);
+          tma_load_1d(S.payload[p], reinterpret_cast<const void*>(a0), bulk, &S.full[p]);
+        }
       }
-      if (!good && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
-      fence_proxy_async();
-    }
-    __syncthreads();
-    if (valid) {
-      const uint32_t bulk = (cnt * 4) & ~15u;
-      if (tid == 0 && bulk) {
-        tma_store_1d(fi->dout + e0, S.out, bulk);
-        tma_store_commit();
+      if (valid) {
+        // Payload bytes past the last 16-byte boundary of the bulk copy: plain loads.
+        const uint32_t lo = uint32_t(max(a1, src) - a0), hi = uint32_t(src + tot - a0);
+        const uint8_t* gb = reinterpret_cast<const uint8_t*>(a0);
+        for (uint32_t k = lo + 4 * uint32_t(lane); k < hi; k += 128)
+          *reinterpret_cast<uint32_t*>(S.payload[p] + k) = *reinterpret_cast<const uint32_t*>(gb + k);
       }
-      for (uint32_t k = bulk / 4 + tid; k < cnt; k += kThreads) fi->dout[e0 + k] = S.out[k];
+      __threadfence_block();  // every lane's tail bytes before lane 0's arrival
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.full[p]);
     }
   }
-  if (tid == 0) tma_store_wait_all();
+
+  // ------------------------------------------------------------------ decode warps
+  uint32_t nstore = 0;
+  bool good = true;
+  for (uint32_t j = 0;; ++j) {
+    const int p = int(j % kStages);
+    if (!mbar_wait(&S.full[p], (j / kStages) & 1u, wait_ns)) {
+      if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+      break;
+    }
+    const StageInfo& st = S.st[p];
+    const uint32_t c = st.chunk;
+    if (c == kNoneChunk) break;
+    FieldInfo* fi = st.fi;
+    if (st.valid) {
+      const float step = st.step;
+      const int ntiles = int(st.ntiles);
+      const uint32_t cnt = st.cnt;
+      float* dout = st.dout;
+      const uint8_t* pay = S.payload[p] + st.shift;
+      for (int tl = warp; tl < ntiles; tl += kDecodeWarps) {
+        float* buf = S.out[warp][nstore & 1u];
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+        good &= decompress_tile(st.hdr[tl], pay + st.toff[tl], buf, step, lane);
+        fence_proxy_async();
+        __syncwarp();
+        const uint32_t k0 = uint32_t(tl) * kTile;
+        const uint32_t valid_elems = min(uint32_t(kTile), cnt - k0);
+        const uint32_t bulk = (valid_elems * 4) & ~15u;
+        if (lane == 0 && bulk) {
+          tma_store_1d(dout + k0, buf, bulk);
+          tma_store_commit();
+        }
+        for (uint32_t k = bulk / 4 + lane; k < valid_elems; k += 32) dout[k0 + k] = buf[k];
+        ++nstore;
+      }
+    }
+    if (!good && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
+    good = true;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.empty[p]);
+  }
+  if (lane == 0) tma_store_wait_all();
 }
 
 }  // namespace

@@ -20,7 +20,10 @@ constexpr int kMaxTileBytes = 708;    // 8 * (4 + 4 * 21) + 4, Eq. 3 with rate <
 constexpr int kMaxDecTileBytes = 1028;  // any header-valid tile: 8 * (4 + 4 * 31) + 4
 constexpr uint32_t kQmax = 174761;    // largest Q with (3Q + 4) 2^-23 <= 2^-4
 constexpr int kMinChunkTiles = 16;    // smallest chunk any kernel uses (workspace sizing)
-constexpr int kChunkTiles = 32;       // tiles per work item of every kernel (32 KiB of input)
+#ifndef FSZ_CHUNK_TILES
+#define FSZ_CHUNK_TILES 16
+#endif
+constexpr int kChunkTiles = FSZ_CHUNK_TILES;  // tiles per work item of every kernel
 constexpr int kChunkElems = kChunkTiles * kTile;
 constexpr uint64_t kMaxElems = uint64_t(1) << 40;
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
@@ -118,14 +121,16 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t* p) {
+// Lookback flags carry their whole message (state and byte count) in one 64-bit word and
+// guard no other data, so relaxed device-scope accesses are enough.
+__device__ __forceinline__ uint64_t ld_flag(const uint64_t* p) {
   uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_flag(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -146,6 +151,17 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Adds to the transaction count of the current phase without arriving.
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -156,6 +172,30 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return ok != 0;
+}
+
+// try_wait that may suspend the thread for up to ~1 ms while the phase is incomplete
+// (instead of spinning): it returns as soon as the phase completes.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(1000000u)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase of `bar` with the given parity; false if `timeout_ns` ran out first.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
+  if (mbar_try_wait_sleep(bar, parity)) return true;
+  const uint64_t deadline = globaltimer_ns() + timeout_ns;
+  for (;;) {
+    if (mbar_try_wait_sleep(bar, parity)) return true;
+    if (globaltimer_ns() > deadline) return false;
+  }
 }
 
 // 1-D TMA bulk copy global -> shared (16-byte aligned ends, size a multiple of 16).
@@ -220,40 +260,86 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 }
 
 // Exclusive prefix of the chunks before `gchunk` within its field (Sec. 4.4, device
-// level: decoupled lookback over the 3-state flags). Called by one whole warp; every
-// spin is bounded by `deadline`; a wait that runs out reads as a zero inclusive prefix
-// and sets *timed_out (the caller records FSZ_ERR_TIMEOUT and still publishes, so that
-// no successor waits forever).
+// level: decoupled lookback over the 3-state flags). Called by one whole warp. A window
+// holds the 32 * kLookbackPerLane nearest predecessors not yet summed (128 by default:
+// wider windows measured slower, because more of the flags they cover belong to chunks
+// still queued behind other CTAs' prefetched tickets) (lane L holds
+// distances kLookbackPerLane * L + k, nearest first). The warp waits only for flags that
+// are still unpublished AND nearer than the nearest inclusive prefix; then it sums every
+// flag up to that prefix, or the whole window and moves on. Every spin is bounded by
+// `deadline`; a wait that runs out reads as a zero inclusive prefix and sets *timed_out
+// (the caller records FSZ_ERR_TIMEOUT and still publishes, so no successor waits forever).
+#ifndef FSZ_LOOKBACK_PER_LANE
+#define FSZ_LOOKBACK_PER_LANE 4
+#endif
+constexpr int kLookbackPerLane = FSZ_LOOKBACK_PER_LANE;
+
 __device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchunk, int64_t first,
                                              uint64_t deadline, bool* timed_out) {
+  constexpr uint32_t FULL = 0xffffffffu;
+  constexpr uint32_t kNoIncl = 1u << 20, kNoWait = 1u << 21;  // beyond any window distance
+  static_assert(kLookbackPerLane <= 32, "per-lane state masks are 32 bits");
   const int lane = threadIdx.x & 31;
   uint64_t excl = 0;
   bool to = false;
   int64_t pos = gchunk - 1;
   while (pos >= first) {
-    const int64_t idx = pos - lane;
-    uint64_t f = kFlagIncl;  // before the field's first chunk: prefix 0
-    if (idx >= first) {
-      f = ld_acquire_u64(flags + idx);
-      uint32_t spins = 0;
-      while ((f >> 62) == 0) {
-        if ((++spins & 63u) == 0 && globaltimer_ns() > deadline) {
-          to = true;
-          f = kFlagIncl;
-          break;
-        }
-        __nanosleep(32);
-        f = ld_acquire_u64(flags + idx);
+    // Aggregates are a chunk's byte count (< 2^16), so a slot keeps its value's low 32 bits
+    // and the lane keeps, as bit masks, which slots are unpublished or inclusive; the full
+    // value of the lane's nearest inclusive prefix is kept aside.
+    uint32_t lo[kLookbackPerLane];
+    uint32_t wait_mask = 0, incl_mask = 0;
+    uint64_t incl_val = 0;
+    auto take = [&](int k, uint64_t f) {
+      const uint32_t st = uint32_t(f >> 62);
+      lo[k] = uint32_t(f);
+      const uint32_t bit = 1u << k;
+      wait_mask = (st == 0) ? (wait_mask | bit) : (wait_mask & ~bit);
+      if (st >= 2) {
+        if ((incl_mask & ((bit << 1) - 1u)) == 0) incl_val = f & kFlagValue;  // nearest so far
+        incl_mask |= bit;
+      }
+    };
+#pragma unroll
+    for (int k = 0; k < kLookbackPerLane; ++k) {
+      const int64_t idx = pos - (kLookbackPerLane * lane + k);
+      take(k, idx >= first ? ld_flag(flags + idx) : kFlagIncl);  // before the field: 0
+    }
+    uint32_t d_incl;
+    for (uint32_t spins = 0;; ++spins) {
+      const uint32_t my_incl = incl_mask ? uint32_t(kLookbackPerLane * lane + __ffs(incl_mask) - 1) : kNoIncl;
+      const uint32_t my_wait = wait_mask ? uint32_t(kLookbackPerLane * lane + __ffs(wait_mask) - 1) : kNoWait;
+      d_incl = __reduce_min_sync(FULL, my_incl);
+      const uint32_t d_wait = __reduce_min_sync(FULL, my_wait);
+      if (d_wait > d_incl) break;  // everything up to the nearest inclusive prefix is in
+      if ((spins & 15u) == 15u && globaltimer_ns() > deadline) {
+        to = true;  // give up: unpublished flags read as a zero inclusive prefix
+#pragma unroll
+        for (int k = 0; k < kLookbackPerLane; ++k)
+          if (wait_mask & (1u << k)) take(k, kFlagIncl);
+        continue;
+      }
+      __nanosleep(64);
+#pragma unroll
+      for (int k = 0; k < kLookbackPerLane; ++k) {
+        const uint32_t d = uint32_t(kLookbackPerLane * lane + k);
+        if ((wait_mask & (1u << k)) && d < d_incl) take(k, ld_flag(flags + (pos - int64_t(d))));
       }
     }
-    __syncwarp();
-    const uint32_t incl = __ballot_sync(0xffffffffu, (f >> 62) >= 2);
-    const int stop = incl ? __ffs(incl) - 1 : 31;
-    excl += warp_sum_u64(lane <= stop ? (f & kFlagValue) : 0);
-    if (incl) break;
-    pos -= 32;
+    // Sum the aggregates nearer than the nearest inclusive prefix, then that prefix.
+    uint32_t agg = 0;
+#pragma unroll
+    for (int k = 0; k < kLookbackPerLane; ++k)
+      if (uint32_t(kLookbackPerLane * lane + k) < d_incl) agg += lo[k];
+    uint64_t mine = agg;
+    if (d_incl != kNoIncl && uint32_t(kLookbackPerLane * lane) <= d_incl &&
+        d_incl < uint32_t(kLookbackPerLane * (lane + 1)))
+      mine += incl_val;
+    excl += warp_sum_u64(mine);
+    if (d_incl != kNoIncl) break;
+    pos -= 32 * kLookbackPerLane;
   }
-  *timed_out = __any_sync(0xffffffffu, to);
+  *timed_out = __any_sync(FULL, to);
   return excl;
 }
 

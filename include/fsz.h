@@ -144,6 +144,32 @@ fsz_status fsz_decompress_batched(const fsz_dfield* d_fields, uint32_t nfields,
                                   uint64_t n_total_capacity, void* d_ws, uint64_t ws_bytes,
                                   fsz_stream stream);
 
+/* ------------------------------------------------------------------ graphs and schedules */
+
+/* A CUDA graph holding one batched call (no counterpart in the paper: it removes the
+ * host launch cost of the call's memset and kernels). The graph records the pointers and
+ * sizes given here; the field tables and buffers they point to are read when the graph
+ * runs, so their contents may change between launches, but not their addresses or the
+ * number of fields. The graph itself holds host-side and driver resources only. */
+typedef struct fsz_graph_s* fsz_graph;
+fsz_status fsz_graph_compress_batched(const fsz_cfield* d_fields, uint32_t nfields, uint64_t n_total,
+                                      void* d_ws, uint64_t ws_bytes, fsz_graph* out);
+fsz_status fsz_graph_decompress_batched(const fsz_dfield* d_fields, uint32_t nfields,
+                                        uint64_t n_total_capacity, void* d_ws, uint64_t ws_bytes,
+                                        fsz_graph* out);
+/* Runs the graph on `stream` (asynchronous); device status as for the captured call. */
+fsz_status fsz_graph_launch(fsz_graph g, fsz_stream stream);
+void fsz_graph_destroy(fsz_graph g);
+
+/* Launch schedule for later calls in this process: persistent CTAs per SM for the
+ * value-range, compression and decompression kernels; 0 = as many as fit (the default).
+ * Values above what fits are clamped. Used by the autotuner; not thread-safe. */
+fsz_status fsz_set_schedule(uint32_t stats_ctas_per_sm, uint32_t compress_ctas_per_sm,
+                            uint32_t decompress_ctas_per_sm);
+/* How many CTAs of each kernel fit per SM, and the SM count, on the current device. */
+fsz_status fsz_get_schedule_limits(uint32_t* stats_max, uint32_t* compress_max,
+                                   uint32_t* decompress_max, uint32_t* sms);
+
 /* ------------------------------------------------------------------ status and metadata */
 
 /* Waits for `stream`, then returns the first device-detected error recorded in the

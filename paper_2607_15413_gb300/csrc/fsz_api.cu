@@ -7,6 +7,18 @@
 
 #include "fsz_internal.cuh"
 
+static_assert(sizeof(fsz_dims) == 32 && sizeof(fsz_cfield) == 80 && sizeof(fsz_dfield) == 32,
+              "C ABI struct layouts");
+
+namespace fsz {
+int g_sched[3] = {0, 0, 0};
+}
+
+// A captured batched call (fsz_graph in the C ABI).
+struct fsz_graph_s {
+  cudaGraphExec_t exec;
+};
+
 namespace {
 
 using namespace fsz;
@@ -78,6 +90,32 @@ fsz_status check_compress(const float* d_in, fsz_dims dims, fsz_eb_mode mode, do
   return FSZ_OK;
 }
 
+template <typename F>
+fsz_status capture_graph(F&& record, fsz_graph* out) {
+  if (out == nullptr) return FSZ_ERR_INVALID_ARG;
+  *out = nullptr;
+  // Kernel attributes are set before the capture begins.
+  (void)stats_cfg();
+  (void)compress_cfg();
+  (void)decompress_cfg();
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FSZ_ERR_CUDA;
+  fsz_status st = FSZ_OK;
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    st = FSZ_ERR_CUDA;
+  } else {
+    st = record(reinterpret_cast<fsz_stream>(s));
+    if (cudaStreamEndCapture(s, &graph) != cudaSuccess && st == FSZ_OK) st = FSZ_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (st == FSZ_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) st = FSZ_ERR_CUDA;
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(s);
+  if (st != FSZ_OK) return st;
+  *out = new fsz_graph_s{exec};
+  return FSZ_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -228,6 +266,54 @@ fsz_status fsz_read_header(const void* h_first64, uint64_t* n, fsz_dims* dims, d
   if (step) *step = sv;
   if (total_bytes) *total_bytes = 64 + 8 * ((nn + kTile - 1) / kTile) + u64(56);
   return FSZ_OK;
+}
+
+fsz_status fsz_set_schedule(uint32_t stats_ctas_per_sm, uint32_t compress_ctas_per_sm,
+                            uint32_t decompress_ctas_per_sm) {
+  if (stats_ctas_per_sm > 64 || compress_ctas_per_sm > 64 || decompress_ctas_per_sm > 64)
+    return FSZ_ERR_INVALID_ARG;
+  g_sched[kSchedStats] = int(stats_ctas_per_sm);
+  g_sched[kSchedCompress] = int(compress_ctas_per_sm);
+  g_sched[kSchedDecompress] = int(decompress_ctas_per_sm);
+  return FSZ_OK;
+}
+
+fsz_status fsz_get_schedule_limits(uint32_t* stats_max, uint32_t* compress_max, uint32_t* decompress_max,
+                                   uint32_t* sms) {
+  const LaunchCfg a = stats_cfg(), b = compress_cfg(), c = decompress_cfg();
+  if (cudaGetLastError() != cudaSuccess) return FSZ_ERR_CUDA;
+  if (stats_max) *stats_max = uint32_t(a.per);
+  if (compress_max) *compress_max = uint32_t(b.per);
+  if (decompress_max) *decompress_max = uint32_t(c.per);
+  if (sms) *sms = uint32_t(b.sms);
+  return FSZ_OK;
+}
+
+fsz_status fsz_graph_compress_batched(const fsz_cfield* d_fields, uint32_t nfields, uint64_t n_total,
+                                      void* d_ws, uint64_t ws_bytes, fsz_graph* out) {
+  return capture_graph([&](fsz_stream s) {
+    return fsz_compress_batched(d_fields, nfields, n_total, d_ws, ws_bytes, s);
+  }, out);
+}
+
+fsz_status fsz_graph_decompress_batched(const fsz_dfield* d_fields, uint32_t nfields,
+                                        uint64_t n_total_capacity, void* d_ws, uint64_t ws_bytes,
+                                        fsz_graph* out) {
+  return capture_graph([&](fsz_stream s) {
+    return fsz_decompress_batched(d_fields, nfields, n_total_capacity, d_ws, ws_bytes, s);
+  }, out);
+}
+
+fsz_status fsz_graph_launch(fsz_graph g, fsz_stream stream) {
+  if (g == nullptr) return FSZ_ERR_INVALID_ARG;
+  return cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? FSZ_OK
+                                                                                     : FSZ_ERR_CUDA;
+}
+
+void fsz_graph_destroy(fsz_graph g) {
+  if (g == nullptr) return;
+  cudaGraphExecDestroy(g->exec);
+  delete g;
 }
 
 void fsz_set_test_hooks(uint64_t skip_chunk, uint64_t timeout_ns) {

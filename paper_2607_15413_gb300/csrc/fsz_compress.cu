@@ -468,7 +468,9 @@ LaunchCfg compress_cfg() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_compress_kernel, kThreads, c.smem);
-    c.grid = sms * (per > 0 ? per : 1);
+    c.sms = sms;
+    c.per = per > 0 ? per : 1;
+    c.grid = sms * c.per;
     return c;
   }();
   return cfg;
@@ -476,7 +478,7 @@ LaunchCfg compress_cfg() {
 
 void launch_compress(const KernelArgs& a, cudaStream_t st) {
   const LaunchCfg c = compress_cfg();
-  fsz_compress_kernel<<<c.grid, kThreads, c.smem, st>>>(a);
+  fsz_compress_kernel<<<sched_grid(c, kSchedCompress), kThreads, c.smem, st>>>(a);
 }
 
 }  // namespace fsz

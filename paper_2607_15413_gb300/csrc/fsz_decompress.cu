@@ -358,7 +358,9 @@ LaunchCfg decompress_cfg() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_decompress_kernel, kThreads, c.smem);
-    c.grid = sms * (per > 0 ? per : 1);
+    c.sms = sms;
+    c.per = per > 0 ? per : 1;
+    c.grid = sms * c.per;
     return c;
   }();
   return cfg;
@@ -366,7 +368,7 @@ LaunchCfg decompress_cfg() {
 
 void launch_decompress(const KernelArgs& a, cudaStream_t st) {
   const LaunchCfg c = decompress_cfg();
-  fsz_decompress_kernel<<<c.grid, kThreads, c.smem, st>>>(a);
+  fsz_decompress_kernel<<<sched_grid(c, kSchedDecompress), kThreads, c.smem, st>>>(a);
 }
 
 }  // namespace fsz

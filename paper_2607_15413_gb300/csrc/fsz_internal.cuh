@@ -386,9 +386,20 @@ __device__ __forceinline__ void write_preamble(FieldInfo* fi, uint64_t data_byte
 // ------------------------------------------------------------------ launch helpers (host)
 
 struct LaunchCfg {
-  int grid;
+  int grid;  // SMs x CTAs that fit per SM
   int smem;
+  int sms;
+  int per;   // CTAs per SM that fit
 };
+
+// Persistent CTAs per SM chosen by fsz_set_schedule (0 = as many as fit), per kernel.
+enum { kSchedStats = 0, kSchedCompress = 1, kSchedDecompress = 2 };
+extern int g_sched[3];
+inline int sched_grid(const LaunchCfg& c, int which) {
+  const int want = g_sched[which];
+  const int per = (want > 0 && want < c.per) ? want : c.per;
+  return c.sms * (per > 0 ? per : 1);
+}
 
 LaunchCfg stats_cfg();
 LaunchCfg compress_cfg();

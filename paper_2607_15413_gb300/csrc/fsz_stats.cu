@@ -369,7 +369,9 @@ LaunchCfg stats_cfg() {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_stats_kernel, kStatsThreads, 0);
     LaunchCfg c;
-    c.grid = sms * (per > 0 ? per : 1);
+    c.sms = sms;
+    c.per = per > 0 ? per : 1;
+    c.grid = sms * c.per;
     c.smem = 0;
     return c;
   }();
@@ -377,7 +379,7 @@ LaunchCfg stats_cfg() {
 }
 
 void launch_stats(const KernelArgs& a, cudaStream_t st) {
-  fsz_stats_kernel<<<stats_cfg().grid, kStatsThreads, 0, st>>>(a);
+  fsz_stats_kernel<<<sched_grid(stats_cfg(), kSchedStats), kStatsThreads, 0, st>>>(a);
 }
 
 void launch_setup_compress(const KernelArgs& a, const FieldInfo& fi, cudaStream_t st) {

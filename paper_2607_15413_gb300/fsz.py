@@ -26,7 +26,9 @@ EB_ABS, EB_REL = 0, 1
 EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_bytes", "fsz_compress",
            "fsz_compress_prepare", "fsz_compress_encode", "fsz_decompress", "fsz_compress_batched",
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
-           "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc"]
+           "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc",
+           "fsz_graph_compress_batched", "fsz_graph_decompress_batched", "fsz_graph_launch",
+           "fsz_graph_destroy", "fsz_set_schedule", "fsz_get_schedule_limits"]
 
 
 class FszDims(ctypes.Structure):
@@ -92,6 +94,18 @@ def lib():
             L.fsz_set_test_hooks.restype = None
             L.fsz_compress_noalloc.argtypes = [P, FszDims, i32, f64, P, u64, P, P, P]
             L.fsz_compress_noalloc.restype = i32
+            L.fsz_graph_compress_batched.argtypes = [P, u32, u64, P, u64, P]
+            L.fsz_graph_compress_batched.restype = i32
+            L.fsz_graph_decompress_batched.argtypes = [P, u32, u64, P, u64, P]
+            L.fsz_graph_decompress_batched.restype = i32
+            L.fsz_graph_launch.argtypes = [P, P]
+            L.fsz_graph_launch.restype = i32
+            L.fsz_graph_destroy.argtypes = [P]
+            L.fsz_graph_destroy.restype = None
+            L.fsz_set_schedule.argtypes = [u32, u32, u32]
+            L.fsz_set_schedule.restype = i32
+            L.fsz_get_schedule_limits.argtypes = [P, P, P, P]
+            L.fsz_get_schedule_limits.restype = i32
             L.fsz_version.argtypes = []
             L.fsz_version.restype = ctypes.c_char_p
             _lib = L
@@ -180,6 +194,41 @@ def fsz_compress_noalloc(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes,
                                       d_status, stream)
 
 
+def fsz_graph_compress_batched(d_fields, nfields, n_total, d_ws, ws_bytes):
+    """Captures fsz_compress_batched into a CUDA graph; returns the graph handle."""
+    g = ctypes.c_void_p()
+    _check(lib().fsz_graph_compress_batched(d_fields, nfields, n_total, d_ws, ws_bytes,
+                                            ctypes.byref(g)), "fsz_graph_compress_batched")
+    return g.value
+
+
+def fsz_graph_decompress_batched(d_fields, nfields, n_total_capacity, d_ws, ws_bytes):
+    g = ctypes.c_void_p()
+    _check(lib().fsz_graph_decompress_batched(d_fields, nfields, n_total_capacity, d_ws, ws_bytes,
+                                              ctypes.byref(g)), "fsz_graph_decompress_batched")
+    return g.value
+
+
+def fsz_graph_launch(g, stream) -> int:
+    return lib().fsz_graph_launch(g, stream)
+
+
+def fsz_graph_destroy(g) -> None:
+    lib().fsz_graph_destroy(g)
+
+
+def fsz_set_schedule(stats_ctas_per_sm: int, compress_ctas_per_sm: int,
+                     decompress_ctas_per_sm: int) -> int:
+    return lib().fsz_set_schedule(stats_ctas_per_sm, compress_ctas_per_sm, decompress_ctas_per_sm)
+
+
+def fsz_get_schedule_limits():
+    vals = [ctypes.c_uint32() for _ in range(4)]
+    _check(lib().fsz_get_schedule_limits(*[ctypes.byref(v) for v in vals]), "fsz_get_schedule_limits")
+    return dict(stats=vals[0].value, compress=vals[1].value, decompress=vals[2].value,
+                sms=vals[3].value)
+
+
 def fsz_set_test_hooks(skip_chunk: int, timeout_ns: int) -> None:
     lib().fsz_set_test_hooks(skip_chunk, timeout_ns)
 
@@ -262,3 +311,133 @@ def decompress(stream_bytes, n: int | None = None, ws: Workspace | None = None, 
     if check:
         _check(fsz_check(ws.ptr, sp), "fsz_decompress (device)")
     return out[:n]
+
+
+# ------------------------------------------------------------------ batches
+
+def _align16(x: int) -> int:
+    return (x + 15) // 16 * 16
+
+
+class CompressBatch:
+    """Buffers and the device field table for fsz_compress_batched over a fixed set of
+    fields: one output arena (each field's slot fsz_compress_bound(n) bytes, 16-byte
+    aligned), per-field stream sizes and a batch workspace. run() launches one batched
+    call; graph() captures it once into a CUDA graph for repeated launches."""
+
+    def __init__(self, fields, device="cuda"):
+        import torch
+        self.device = torch.device(device)
+        self.fields = list(fields)  # (tensor, shape, mode, eb)
+        self.n = [int(x.numel()) for x, *_ in self.fields]
+        self.n_total = sum(self.n)
+        caps = [_align16(fsz_compress_bound(k)) for k in self.n]
+        self.offsets = [0]
+        for c in caps:
+            self.offsets.append(self.offsets[-1] + c)
+        self.caps = caps
+        self.arena = torch.empty(max(16, self.offsets[-1]), dtype=torch.uint8, device=self.device)
+        self.sizes = torch.zeros(len(self.fields), dtype=torch.int64, device=self.device)
+        arr = (FszCField * len(self.fields))()
+        for i, (x, shape, mode, eb) in enumerate(self.fields):
+            assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
+            arr[i].in_ = x.data_ptr() if x.numel() else 0
+            arr[i].dims = make_dims(shape)
+            arr[i].mode = int(mode)
+            arr[i].reserved = 0
+            arr[i].eb = float(eb)
+            arr[i].out = self.arena.data_ptr() + self.offsets[i]
+            arr[i].out_capacity = caps[i]
+            arr[i].out_bytes = self.sizes.data_ptr() + 8 * i
+        raw = bytes(arr)
+        self.table = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(self.device)
+        self.ws_bytes = fsz_batch_workspace_bytes(self.n_total, len(self.fields))
+        self.ws = _dev_buffer(self.ws_bytes, self.device)
+        self._graph = None
+
+    def run(self, stream=None) -> int:
+        return fsz_compress_batched(self.table.data_ptr(), len(self.fields), self.n_total,
+                                    self.ws.data_ptr(), self.ws_bytes, _stream_ptr(stream))
+
+    def graph(self):
+        if self._graph is None:
+            self._graph = fsz_graph_compress_batched(self.table.data_ptr(), len(self.fields),
+                                                     self.n_total, self.ws.data_ptr(), self.ws_bytes)
+        return self._graph
+
+    def launch_graph(self, stream=None) -> int:
+        return fsz_graph_launch(self.graph(), _stream_ptr(stream))
+
+    def status(self, stream=None):
+        """(first device status, per-field statuses); waits for the stream."""
+        per = (ctypes.c_uint32 * len(self.fields))()
+        st = fsz_check_batched(self.ws.data_ptr(), len(self.fields), per, _stream_ptr(stream))
+        return st, list(per)
+
+    def stream(self, i: int, sizes=None):
+        k = int(self.sizes[i].item()) if sizes is None else int(sizes[i])
+        return self.arena[self.offsets[i]:self.offsets[i] + k]
+
+    def __del__(self):
+        if getattr(self, "_graph", None) is not None:
+            try:
+                fsz_graph_destroy(self._graph)
+            except Exception:
+                pass
+
+
+class DecompressBatch:
+    """Buffers and the device field table for fsz_decompress_batched: streams (device
+    byte tensors, 16-byte aligned) and their element counts."""
+
+    def __init__(self, streams, counts, device="cuda"):
+        import torch
+        self.device = torch.device(device)
+        self.streams = [s if s.data_ptr() % 16 == 0 else s.clone() for s in streams]
+        self.counts = [int(c) for c in counts]
+        caps = [_align16(max(4 * c, 16)) // 4 for c in self.counts]
+        self.offsets = [0]
+        for c in caps:
+            self.offsets.append(self.offsets[-1] + c)
+        self.caps = caps
+        self.arena = torch.empty(max(4, self.offsets[-1]), dtype=torch.float32, device=self.device)
+        arr = (FszDField * len(self.streams))()
+        for i, s in enumerate(self.streams):
+            arr[i].in_ = s.data_ptr()
+            arr[i].in_bytes = s.numel()
+            arr[i].out = self.arena.data_ptr() + 4 * self.offsets[i]
+            arr[i].out_capacity_elems = caps[i]
+        self.table = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(self.device)
+        self.cap_total = sum(caps)
+        self.ws_bytes = fsz_batch_workspace_bytes(self.cap_total, len(self.streams))
+        self.ws = _dev_buffer(self.ws_bytes, self.device)
+        self._graph = None
+
+    def run(self, stream=None) -> int:
+        return fsz_decompress_batched(self.table.data_ptr(), len(self.streams), self.cap_total,
+                                      self.ws.data_ptr(), self.ws_bytes, _stream_ptr(stream))
+
+    def graph(self):
+        if self._graph is None:
+            self._graph = fsz_graph_decompress_batched(self.table.data_ptr(), len(self.streams),
+                                                       self.cap_total, self.ws.data_ptr(),
+                                                       self.ws_bytes)
+        return self._graph
+
+    def launch_graph(self, stream=None) -> int:
+        return fsz_graph_launch(self.graph(), _stream_ptr(stream))
+
+    def status(self, stream=None):
+        per = (ctypes.c_uint32 * len(self.streams))()
+        st = fsz_check_batched(self.ws.data_ptr(), len(self.streams), per, _stream_ptr(stream))
+        return st, list(per)
+
+    def output(self, i: int):
+        return self.arena[self.offsets[i]:self.offsets[i] + self.counts[i]]
+
+    def __del__(self):
+        if getattr(self, "_graph", None) is not None:
+            try:
+                fsz_graph_destroy(self._graph)
+            except Exception:
+                pass

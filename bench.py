@@ -121,7 +121,7 @@ def barrier(world: int):
         dist.barrier()
 
 
-CPU_SAMPLE_SHAPE = (256, 512, 512)  # 2^26 elements per field: about 10-30 s of oracle work
+CPU_SAMPLE_SHAPE = (384, 512, 512)  # 3 x 2^25 elements per field: about 10-30 s of oracle work
 
 
 def cpu_sample_fields():
@@ -150,7 +150,7 @@ def cpu_baseline_run(fields, elems=None):
     n = fields[0].size if elems is None else elems
     return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"first {n} elements of both fields (k^-3 GRF and its zero-slab/+280 "
-                      f"variant, same recipe at 256x512x512) at REL 1e-2/1e-3/1e-4, "
+                      f"variant, same recipe at 384x512x512) at REL 1e-2/1e-3/1e-4, "
                       f"compress + decompress, 1 host core",
             "seconds": dt}
 
@@ -186,6 +186,83 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_batched(fsz, inputs, dev, reps: int = 3):
+    """Batched workload: 512 fields (seed 3) of log-uniform size 64 KiB - 64 MiB, mixed
+    classes and REL bounds, compressed and decompressed in one batched call (a CUDA graph,
+    autotuned schedule) vs one call per field on the same stream, same schedule."""
+    import torch
+    from paper_2607_15413_gb300 import tune
+    L = fsz.lib()
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    specs = inputs.field_mix_specs(512, seed=3)
+    fields = [(inputs.make_field(spec, device=str(dev)).contiguous(), spec["dims"], fsz.EB_REL,
+               spec["rel"]) for spec in specs]
+    torch.cuda.empty_cache()
+    nbytes_in = sum(4 * f.numel() for f, *_ in fields)
+    cb = fsz.CompressBatch(fields, dev)
+    assert cb.run() == fsz.OK and cb.status()[0] == fsz.OK
+    sizes = cb.sizes.cpu().tolist()
+    streams = [cb.stream(i, sizes) for i in range(len(fields))]
+    db = fsz.DecompressBatch(streams, [f.numel() for f, *_ in fields], dev)
+    tuned = tune.tune(cb, db, reps=2)
+    tune.apply(tuned["best"])
+    ws1_bytes = fsz.fsz_workspace_bytes(max(f.numel() for f, *_ in fields))
+    ws1 = torch.empty(ws1_bytes, dtype=torch.uint8, device=dev)
+    dims = [fsz.make_dims(d) for _, d, *_ in fields]
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts[1:])
+
+    def per_field_compress():
+        for i, (x, _, mode, eb) in enumerate(fields):
+            st = L.fsz_compress(x.data_ptr(), dims[i], mode, eb, cb.arena.data_ptr() + cb.offsets[i],
+                                cb.caps[i], cb.sizes.data_ptr() + 8 * i, ws1.data_ptr(), ws1_bytes, sp)
+            if st:
+                raise fsz.FszError(st, "per-field compress")
+
+    def per_field_decompress():
+        for i, s_i in enumerate(streams):
+            st = L.fsz_decompress(s_i.data_ptr(), s_i.numel(), db.arena.data_ptr() + 4 * db.offsets[i],
+                                  db.caps[i], ws1.data_ptr(), ws1_bytes, sp)
+            if st:
+                raise fsz.FszError(st, "per-field decompress")
+
+    t_pf_c = timed(per_field_compress)
+    pf_arena = cb.arena.clone()
+    t_b_c = timed(lambda: cb.launch_graph())
+    exact = all(torch.equal(pf_arena[cb.offsets[i]:cb.offsets[i] + sizes[i]], streams[i])
+                for i in range(len(fields)))
+    t_pf_d = timed(per_field_decompress)
+    pf_out = db.arena.clone()
+    t_b_d = timed(lambda: db.launch_graph())
+    exact = exact and torch.equal(pf_out, db.arena) and cb.status()[0] == fsz.OK and db.status()[0] == fsz.OK
+    fsz.fsz_set_schedule(0, 0, 0)
+    comp_bytes = sum(sizes)
+    out = {"workload": "512 fields, seed 3: log-uniform 64 KiB-64 MiB, 1-3-D, 40% k^-3 GRF / "
+                       "40% particle-like / 20% zero-slab, REL in {1e-2,1e-3,1e-4}",
+           "nfields": len(fields), "input_bytes": nbytes_in, "stream_bytes": comp_bytes,
+           "compress": {"batched_gbs": nbytes_in / t_b_c / 1e6, "per_field_gbs": nbytes_in / t_pf_c / 1e6,
+                        "batched_ms": t_b_c, "per_field_ms": t_pf_c, "ratio": t_pf_c / t_b_c},
+           "decompress": {"batched_gbs": nbytes_in / t_b_d / 1e6, "per_field_gbs": nbytes_in / t_pf_d / 1e6,
+                          "batched_ms": t_b_d, "per_field_ms": t_pf_d, "ratio": t_pf_d / t_b_d},
+           "schedule": tuned["best"], "tuning_ms": {"compress": tuned["compress"],
+                                                    "decompress": tuned["decompress"]},
+           "bit_exact_vs_per_field": bool(exact),
+           "notes": "batched = value-range pass + compression of all fields in one graph launch; "
+                    "per-field = fsz_compress / fsz_decompress once per field on one stream"}
+    del cb, db, fields, streams, pf_arena, pf_out
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,6 +271,8 @@ def main():
     ap.add_argument("--impl", default="fsz", choices=["fsz", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 512-field batched vs per-field comparison")
     ap.add_argument("--fields", default="grf,zero_slabs",
                     help="subset of grf,zero_slabs (smaller cases for profiling)")
     ap.add_argument("--rels", default=",".join(str(r) for r in RELS),
@@ -401,19 +480,26 @@ def main():
                         "stats_gbs": 4 * n / med(stats_ms[j]) / 1e6,
                         "decompress_gbs": 4 * n / med(dec_ms[j]) / 1e6,
                         "decompress_hbm_gbs": (4 * n + sizes[j]) / med(dec_ms[j]) / 1e6})
+    njobs, nfields_main = len(jobs), len(fields)
+    clock_summary = clocks.summary()
+    batched = None
+    if not args.no_batched:
+        del fields, jobs, outs, recon, g
+        torch.cuda.empty_cache()
+        batched = run_batched(fsz, inputs, dev)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
                 "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD if len(jobs) == 6 else
+                "config": {"workload": WORKLOAD if njobs == 6 else
                            f"subset: fields {args.fields}, REL {args.rels} of: " + WORKLOAD,
-                           "n_per_field": n, "fields": len(fields), "rels": rels,
+                           "n_per_field": n, "fields": nfields_main, "rels": rels,
                            "parallelism": f"replicas x{world} (no data-path collective)",
                            "l2": "inputs 512 MiB > L2; streams read back after >= 2.5 GB of traffic"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps,
-                "clocks": clocks.summary(), "jobs": per_job,
+                "clocks": clock_summary, "jobs": per_job, "batched": batched,
                 "max_abs_err_last_job": p_last}
         print(json.dumps(line))
     barrier(world)

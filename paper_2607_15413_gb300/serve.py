@@ -1,0 +1,263 @@
+"""Continuous-batching request loop for compress / decompress requests.
+
+Clients submit requests whose inputs already live on the device (a float32 field to
+compress, or a stream plus its element count to decompress) and get a future back. One
+scheduler thread owns every GPU call:
+
+* Admission: requests are admitted in arrival order while the device-memory budget
+  allows. The budget counts the buffers the server allocates for a request (the output,
+  and the stream-size word); inputs belong to the client. A request larger than the
+  whole budget is rejected at once. A request that does not fit yet waits at the head of
+  the queue: later requests do not overtake it, so nothing starves, and since in-flight
+  work always completes and returns its memory, nothing deadlocks.
+* Batching: admitted requests of the head's kind (compress or decompress) form one batch
+  of up to `max_batch` requests, launched as one batched C-ABI call on the first free
+  stream slot. With several slots, batches overlap on the device; requests that arrive
+  while batches run are admitted and launched as soon as a slot and budget free up
+  (continuous batching), instead of waiting for the queue to drain.
+* Completion: a CUDA event per batch; each request's future receives its result
+  (the stream bytes for a compression, the decoded field for a decompression), its status
+  and its latency (arrival to completion observed on the host).
+
+The backend is pluggable: GpuBackend drives the CUDA library; tests use a fake backend
+on the CPU to check the scheduling rules alone.
+"""
+from __future__ import annotations
+
+import collections
+import concurrent.futures as cf
+import ctypes
+import threading
+import time
+from dataclasses import dataclass, field
+
+COMPRESS, DECOMPRESS = "compress", "decompress"
+
+
+@dataclass
+class Request:
+    kind: str                 # COMPRESS or DECOMPRESS
+    data: object              # device tensor: float32 field, or uint8 stream
+    shape: tuple = ()         # field shape (compress)
+    eb: float = 1e-3          # error bound (compress)
+    mode: int = 1             # FSZ_EB_REL (1) or FSZ_EB_ABS (0)
+    n: int = 0                # element count (decompress: from the compress result)
+    arrival: float = 0.0      # host time.perf_counter() at submission
+    future: cf.Future = field(default_factory=cf.Future)
+    cost: int = 0             # device bytes the server allocates for it
+    seq: int = 0
+
+
+@dataclass
+class Result:
+    status: int
+    latency_s: float
+    output: object = None     # compress: uint8 stream tensor; decompress: float32 tensor
+    nbytes: int = 0           # compress: stream size
+    batch_size: int = 1
+
+
+def _align16(x: int) -> int:
+    return (x + 15) // 16 * 16
+
+
+class GpuBackend:
+    """Runs batches through the CUDA library, one CUDA stream and workspace per slot."""
+
+    def __init__(self, n_slots: int, max_batch: int, max_elems: int, device="cuda"):
+        import torch
+
+        from . import fsz
+        self.torch, self.fsz = torch, fsz
+        self.device = torch.device(device)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(n_slots)]
+        self.ws_bytes = fsz.fsz_batch_workspace_bytes(max_elems, max_batch)
+        self.ws = [torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+                   for _ in range(n_slots)]
+        self.max_batch = max_batch
+
+    def cost(self, req: Request) -> int:
+        if req.kind == COMPRESS:
+            n = 1
+            for s in req.shape:
+                n *= int(s)
+            return _align16(self.fsz.fsz_compress_bound(n)) + 16
+        return _align16(4 * max(req.n, 4))
+
+    def launch(self, slot: int, kind: str, reqs):
+        torch, fsz = self.torch, self.fsz
+        st = self.streams[slot]
+        with torch.cuda.stream(st):
+            if kind == COMPRESS:
+                outs, table = [], (fsz.FszCField * len(reqs))()
+                sizes = torch.zeros(len(reqs), dtype=torch.int64, device=self.device)
+                n_total = 0
+                for i, r in enumerate(reqs):
+                    n = r.data.numel()
+                    n_total += n
+                    cap = _align16(fsz.fsz_compress_bound(n))
+                    out = torch.empty(cap, dtype=torch.uint8, device=self.device)
+                    outs.append(out)
+                    table[i].in_ = r.data.data_ptr() if n else 0
+                    table[i].dims = fsz.make_dims(r.shape)
+                    table[i].mode, table[i].reserved, table[i].eb = int(r.mode), 0, float(r.eb)
+                    table[i].out, table[i].out_capacity = out.data_ptr(), cap
+                    table[i].out_bytes = sizes.data_ptr() + 8 * i
+                dtab = torch.frombuffer(bytearray(bytes(table)), dtype=torch.uint8).pin_memory()
+                dtab = dtab.to(self.device, non_blocking=True)
+                code = fsz.fsz_compress_batched(dtab.data_ptr(), len(reqs), n_total,
+                                                self.ws[slot].data_ptr(), self.ws_bytes,
+                                                st.cuda_stream)
+                hsizes = torch.empty(len(reqs), dtype=torch.int64, pin_memory=True)
+                hsizes.copy_(sizes, non_blocking=True)
+                keep = (outs, sizes, dtab, hsizes)
+            else:
+                outs, table = [], (fsz.FszDField * len(reqs))()
+                cap_total = 0
+                for i, r in enumerate(reqs):
+                    cap = _align16(4 * max(r.n, 4)) // 4
+                    cap_total += cap
+                    out = torch.empty(cap, dtype=torch.float32, device=self.device)
+                    outs.append(out)
+                    src = r.data if r.data.data_ptr() % 16 == 0 else r.data.clone()
+                    table[i].in_, table[i].in_bytes = src.data_ptr(), src.numel()
+                    table[i].out, table[i].out_capacity_elems = out.data_ptr(), cap
+                    outs.append(src)
+                dtab = torch.frombuffer(bytearray(bytes(table)), dtype=torch.uint8).pin_memory()
+                dtab = dtab.to(self.device, non_blocking=True)
+                code = fsz.fsz_decompress_batched(dtab.data_ptr(), len(reqs), cap_total,
+                                                  self.ws[slot].data_ptr(), self.ws_bytes,
+                                                  st.cuda_stream)
+                keep = (outs, dtab)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return {"event": ev, "code": code, "keep": keep, "kind": kind, "slot": slot}
+
+    def done(self, h) -> bool:
+        return h["event"].query()
+
+    def results(self, h, reqs):
+        fsz = self.fsz
+        per = (ctypes.c_uint32 * len(reqs))()
+        first = fsz.fsz_check_batched(self.ws[h["slot"]].data_ptr(), len(reqs), per,
+                                      self.streams[h["slot"]].cuda_stream)
+        out = []
+        for i, r in enumerate(reqs):
+            status = h["code"] if h["code"] else (int(per[i]) if first != fsz.ERR_CUDA else first)
+            if h["kind"] == COMPRESS:
+                outs, sizes, dtab, hsizes = h["keep"]
+                nb = int(hsizes[i])
+                out.append((status, outs[i][:nb], nb))
+            else:
+                outs, dtab = h["keep"]
+                out.append((status, outs[2 * i][: r.n], 0))
+        return out
+
+
+class Server:
+    """The scheduler. `submit()` is thread-safe; `close()` drains and stops."""
+
+    def __init__(self, backend, budget_bytes: int, n_slots: int = 4, max_batch: int = 64,
+                 poll_s: float = 5e-5):
+        self.backend = backend
+        self.budget = int(budget_bytes)
+        self.free_budget = int(budget_bytes)
+        self.n_slots = n_slots
+        self.max_batch = max_batch
+        self.poll_s = poll_s
+        self._arrivals = collections.deque()
+        self._lock = threading.Lock()
+        self._wake = threading.Event()
+        self._pending = collections.deque()
+        self._inflight = {}          # slot -> (handle, reqs)
+        self._stop = False
+        self._seq = 0
+        self.stats = {"completed": 0, "rejected": 0, "batches": 0, "max_inflight": 0,
+                      "admitted_while_busy": 0, "bytes_in": 0, "max_batch_seen": 0}
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
+
+    # -------------------------------------------------------------- client side
+    def submit(self, req: Request) -> cf.Future:
+        req.arrival = req.arrival or time.perf_counter()
+        req.cost = self.backend.cost(req)
+        with self._lock:
+            req.seq = self._seq
+            self._seq += 1
+            self._arrivals.append(req)
+        self._wake.set()
+        return req.future
+
+    def close(self, timeout: float = 60.0) -> None:
+        with self._lock:
+            self._stop = True
+        self._wake.set()
+        self._thread.join(timeout)
+
+    # -------------------------------------------------------------- scheduler
+    def _run(self) -> None:
+        while True:
+            with self._lock:
+                while self._arrivals:
+                    r = self._arrivals.popleft()
+                    if r.cost > self.budget:          # can never fit: reject now
+                        self.stats["rejected"] += 1
+                        r.future.set_result(Result(status=-1, latency_s=time.perf_counter() - r.arrival))
+                        continue
+                    self._pending.append(r)
+                stop = self._stop
+            progressed = self._complete()
+            progressed |= self._launch()
+            if stop and not self._pending and not self._inflight:
+                with self._lock:
+                    if not self._arrivals:
+                        return
+            if not progressed:
+                self._wake.wait(self.poll_s)
+                self._wake.clear()
+
+    def _complete(self) -> bool:
+        done = [s for s, (h, _) in self._inflight.items() if self.backend.done(h)]
+        for s in done:
+            h, reqs = self._inflight.pop(s)
+            now = time.perf_counter()
+            for r, (status, output, nb) in zip(reqs, self.backend.results(h, reqs)):
+                self.free_budget += r.cost
+                self.stats["completed"] += 1
+                r.future.set_result(Result(status=status, latency_s=now - r.arrival, output=output,
+                                           nbytes=nb, batch_size=len(reqs)))
+        return bool(done)
+
+    def _launch(self) -> bool:
+        launched = False
+        while self._pending and len(self._inflight) < self.n_slots:
+            head = self._pending[0]
+            if head.cost > self.free_budget:
+                break                                  # wait for in-flight work to free memory
+            kind = head.kind
+            batch = []
+            while (self._pending and len(batch) < self.max_batch and self._pending[0].kind == kind
+                   and self._pending[0].cost <= self.free_budget):
+                r = self._pending.popleft()
+                self.free_budget -= r.cost
+                batch.append(r)
+            slot = next(s for s in range(self.n_slots) if s not in self._inflight)
+            if self._inflight:
+                self.stats["admitted_while_busy"] += len(batch)
+            h = self.backend.launch(slot, kind, batch)
+            self._inflight[slot] = (h, batch)
+            self.stats["batches"] += 1
+            self.stats["max_inflight"] = max(self.stats["max_inflight"], len(self._inflight))
+            self.stats["max_batch_seen"] = max(self.stats["max_batch_seen"], len(batch))
+            for r in batch:
+                self.stats["bytes_in"] += 4 * (r.data.numel() if kind == COMPRESS else r.n)
+            launched = True
+        return launched
+
+
+def percentile(xs, q: float) -> float:
+    xs = sorted(xs)
+    if not xs:
+        return float("nan")
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]

@@ -263,6 +263,128 @@ def run_batched(fsz, inputs, dev, reps: int = 3):
     return out
 
 
+def run_serving(fsz, inputs, dev, nreq: int = 200, seed: int = 4):
+    """Serving workload (bounded): requests of log-uniform 16 KiB-256 MiB cut from a
+    device-resident pool of the batched mix's classes, 60 % compress / 40 % decompress of
+    an earlier result, REL from {1e-2,1e-3,1e-4}, 40 GB admission budget. First the closed
+    loop (all requests at once: the peak), then Poisson arrivals at 25/50/75/100 % of that
+    peak; p50/p99 latency from host arrival to completion, sustained GB/s."""
+    import math
+    import random
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2607_15413_gb300 import serve
+    pool_shape = (256, 512, 512)
+    g = inputs.grf(pool_shape, seed=seed, device=str(dev))
+    pool = [g.reshape(-1).contiguous(),
+            inputs.particles(g.numel(), seed=seed, device=str(dev)),
+            inputs.zero_slabs(pool_shape, seed=seed, device=str(dev), base=g).reshape(-1).contiguous()]
+    del g
+    torch.cuda.empty_cache()
+    rng = random.Random(seed)
+
+    def make_requests():
+        out = []
+        for _ in range(nreq):
+            src = pool[rng.randrange(3)]
+            n = int(math.exp(rng.uniform(math.log(4096), math.log(64 << 20))))
+            n = max(4, min(n, src.numel()) // 4 * 4)
+            off = rng.randrange(0, (src.numel() - n) // 4 + 1) * 4
+            out.append((src[off:off + n], rng.choice([1e-2, 1e-3, 1e-4]),
+                        rng.random() < 0.4))
+        return out
+
+    backend = serve.GpuBackend(n_slots=4, max_batch=32, max_elems=10 << 30, device=dev)
+
+    def run(reqs, rate=None):
+        """rate None: closed loop; else Poisson arrivals at `rate` requests/s."""
+        srv = serve.Server(backend, budget_bytes=40 << 30, n_slots=4, max_batch=32)
+        done_streams = []          # compressed results still resident (for decompress requests)
+        lock = threading.Lock()
+        futs, nbytes = [], 0
+        t0 = time.perf_counter()
+        t_arr = t0
+        for x, rel, want_dec in reqs:
+            if rate is not None:
+                t_arr += rng.expovariate(rate)
+                delay = t_arr - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            with lock:
+                prev = done_streams[rng.randrange(len(done_streams))] if (want_dec and done_streams) else None
+            if prev is not None:
+                req = serve.Request(kind=serve.DECOMPRESS, data=prev[0], n=prev[1],
+                                    arrival=t_arr if rate is not None else 0.0)
+            else:
+                req = serve.Request(kind=serve.COMPRESS, data=x, shape=(x.numel(),), eb=rel, mode=1,
+                                    arrival=t_arr if rate is not None else 0.0)
+
+                def keep(f, n=x.numel()):
+                    r = f.result()
+                    if r.status == 0:
+                        with lock:
+                            done_streams.append((r.output, n))
+                            if len(done_streams) > 64:
+                                done_streams.pop(0)      # LRU: oldest result evicted
+                futs_cb.append((req, keep))
+            nbytes += 4 * (req.n if req.kind == serve.DECOMPRESS else x.numel())
+            f = srv.submit(req)
+            if req.kind == serve.COMPRESS:
+                f.add_done_callback(futs_cb[-1][1])
+            futs.append(f)
+        res = [f.result(timeout=300) for f in futs]
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = [r.latency_s * 1e3 for r in res if r.status == 0]
+        return {"gbs": nbytes / wall / 1e9, "p50_ms": serve.percentile(lat, 50),
+                "p99_ms": serve.percentile(lat, 99), "requests": len(res),
+                "refused": sum(1 for r in res if r.status != 0), "bytes": nbytes,
+                "batches": srv.stats["batches"], "max_inflight": srv.stats["max_inflight"],
+                "admitted_while_busy": srv.stats["admitted_while_busy"]}
+
+    futs_cb = []
+    reqs = make_requests()
+    run(reqs[: nreq // 4])                       # warm-up
+    closed = run(reqs)
+    # one call per request, same requests, one stream (the per-request baseline)
+    L = fsz.lib()
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    nmax = max(x.numel() for x, _, _ in reqs)
+    ws_b = fsz.fsz_workspace_bytes(nmax)
+    ws = torch.empty(ws_b, dtype=torch.uint8, device=dev)
+    cap = fsz.fsz_compress_bound(nmax)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    nb = torch.zeros(1, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    tot = 0
+    for x, rel, _ in reqs:
+        L.fsz_compress(x.data_ptr(), fsz.make_dims((x.numel(),)), 1, rel, out.data_ptr(), cap,
+                       nb.data_ptr(), ws.data_ptr(), ws_b, sp)
+        tot += 4 * x.numel()
+    torch.cuda.synchronize(dev)
+    per_req_gbs = tot / (time.perf_counter() - t0) / 1e9
+    mean_bytes = closed["bytes"] / closed["requests"]
+    levels = []
+    for load in (0.25, 0.5, 0.75, 1.0):
+        rate = load * closed["gbs"] * 1e9 / mean_bytes
+        r = run(make_requests(), rate=rate)
+        r["load"] = load
+        r["offered_gbs"] = load * closed["gbs"]
+        levels.append(r)
+    del pool
+    torch.cuda.empty_cache()
+    return {"workload": f"{nreq} requests per level, seed {seed}: log-uniform 16 KiB-256 MiB windows "
+                        "of a device pool (k^-3 GRF, particle-like, zero-slab), 60% compress / 40% "
+                        "decompress of an earlier result, REL in {1e-2,1e-3,1e-4}, 40 GB budget, "
+                        "4 streams, batches of up to 32",
+            "closed_loop": closed, "per_request_compress_gbs": per_req_gbs,
+            "closed_loop_vs_per_request": closed["gbs"] / per_req_gbs, "loads": levels}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +395,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-field batched vs per-field comparison")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the continuous-batching serving measurement")
     ap.add_argument("--fields", default="grf,zero_slabs",
                     help="subset of grf,zero_slabs (smaller cases for profiling)")
     ap.add_argument("--rels", default=",".join(str(r) for r in RELS),
@@ -487,6 +611,9 @@ def main():
         del fields, jobs, outs, recon, g
         torch.cuda.empty_cache()
         batched = run_batched(fsz, inputs, dev)
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(fsz, inputs, dev)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
                 "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
@@ -499,7 +626,7 @@ def main():
                            "l2": "inputs 512 MiB > L2; streams read back after >= 2.5 GB of traffic"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps,
-                "clocks": clock_summary, "jobs": per_job, "batched": batched,
+                "clocks": clock_summary, "jobs": per_job, "batched": batched, "serving": serving,
                 "max_abs_err_last_job": p_last}
         print(json.dumps(line))
     barrier(world)

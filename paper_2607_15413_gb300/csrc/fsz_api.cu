@@ -214,27 +214,31 @@ fsz_status fsz_decompress_batched(const fsz_dfield* d_fields, uint32_t nfields,
   return launched();
 }
 
+// The status words are read on the caller's stream (an asynchronous copy, then a wait on
+// that stream only), so a check never waits for work queued on other streams.
 fsz_status fsz_check(const void* d_ws, fsz_stream stream) {
   if (d_ws == nullptr) return FSZ_ERR_INVALID_ARG;
-  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FSZ_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   uint32_t status = 0;
-  if (cudaMemcpy(&status, d_ws, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (cudaMemcpyAsync(&status, d_ws, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return FSZ_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FSZ_ERR_CUDA;
   return static_cast<fsz_status>(status);
 }
 
 fsz_status fsz_check_batched(const void* d_ws, uint32_t nfields, uint32_t* h_status, fsz_stream stream) {
   if (d_ws == nullptr || (nfields > 0 && h_status == nullptr)) return FSZ_ERR_INVALID_ARG;
-  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return FSZ_ERR_CUDA;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::vector<FieldInfo> fields(nfields);
   const uint8_t* ws = static_cast<const uint8_t*>(d_ws);
-  if (nfields > 0 &&
-      cudaMemcpy(fields.data(), ws + 256, sizeof(FieldInfo) * nfields, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return FSZ_ERR_CUDA;
-  for (uint32_t f = 0; f < nfields; ++f) h_status[f] = fields[f].status;
   uint32_t status = 0;
-  if (cudaMemcpy(&status, d_ws, sizeof(status), cudaMemcpyDeviceToHost) != cudaSuccess)
+  if (nfields > 0 && cudaMemcpyAsync(fields.data(), ws + 256, sizeof(FieldInfo) * nfields,
+                                     cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return FSZ_ERR_CUDA;
+  if (cudaMemcpyAsync(&status, d_ws, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return FSZ_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FSZ_ERR_CUDA;
+  for (uint32_t f = 0; f < nfields; ++f) h_status[f] = fields[f].status;
   return static_cast<fsz_status>(status);
 }
 

@@ -62,7 +62,8 @@ def _align16(x: int) -> int:
 
 
 class GpuBackend:
-    """Runs batches through the CUDA library, one CUDA stream and workspace per slot."""
+    """Runs batches through the CUDA library: per slot a CUDA stream, a batch workspace, and
+    preallocated pinned/device buffers for the field table and the stream sizes."""
 
     def __init__(self, n_slots: int, max_batch: int, max_elems: int, device="cuda"):
         import torch
@@ -70,11 +71,18 @@ class GpuBackend:
         from . import fsz
         self.torch, self.fsz = torch, fsz
         self.device = torch.device(device)
+        self.max_batch = max_batch
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_slots)]
         self.ws_bytes = fsz.fsz_batch_workspace_bytes(max_elems, max_batch)
         self.ws = [torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
                    for _ in range(n_slots)]
-        self.max_batch = max_batch
+        tb = max_batch * ctypes.sizeof(fsz.FszCField)
+        self.h_table = [torch.empty(tb, dtype=torch.uint8, pin_memory=True) for _ in range(n_slots)]
+        self.d_table = [torch.empty(tb, dtype=torch.uint8, device=self.device) for _ in range(n_slots)]
+        self.d_sizes = [torch.zeros(max_batch, dtype=torch.int64, device=self.device)
+                        for _ in range(n_slots)]
+        self.h_sizes = [torch.zeros(max_batch, dtype=torch.int64, pin_memory=True)
+                        for _ in range(n_slots)]
 
     def cost(self, req: Request) -> int:
         if req.kind == COMPRESS:
@@ -87,48 +95,46 @@ class GpuBackend:
     def launch(self, slot: int, kind: str, reqs):
         torch, fsz = self.torch, self.fsz
         st = self.streams[slot]
+        k = len(reqs)
         with torch.cuda.stream(st):
+            keep = []
             if kind == COMPRESS:
-                outs, table = [], (fsz.FszCField * len(reqs))()
-                sizes = torch.zeros(len(reqs), dtype=torch.int64, device=self.device)
+                table = (fsz.FszCField * k).from_address(self.h_table[slot].data_ptr())
+                sizes = self.d_sizes[slot]
                 n_total = 0
                 for i, r in enumerate(reqs):
                     n = r.data.numel()
                     n_total += n
                     cap = _align16(fsz.fsz_compress_bound(n))
                     out = torch.empty(cap, dtype=torch.uint8, device=self.device)
-                    outs.append(out)
+                    keep.append(out)
                     table[i].in_ = r.data.data_ptr() if n else 0
                     table[i].dims = fsz.make_dims(r.shape)
                     table[i].mode, table[i].reserved, table[i].eb = int(r.mode), 0, float(r.eb)
                     table[i].out, table[i].out_capacity = out.data_ptr(), cap
                     table[i].out_bytes = sizes.data_ptr() + 8 * i
-                dtab = torch.frombuffer(bytearray(bytes(table)), dtype=torch.uint8).pin_memory()
-                dtab = dtab.to(self.device, non_blocking=True)
-                code = fsz.fsz_compress_batched(dtab.data_ptr(), len(reqs), n_total,
+                nb = k * ctypes.sizeof(fsz.FszCField)
+                self.d_table[slot][:nb].copy_(self.h_table[slot][:nb], non_blocking=True)
+                code = fsz.fsz_compress_batched(self.d_table[slot].data_ptr(), k, n_total,
                                                 self.ws[slot].data_ptr(), self.ws_bytes,
                                                 st.cuda_stream)
-                hsizes = torch.empty(len(reqs), dtype=torch.int64, pin_memory=True)
-                hsizes.copy_(sizes, non_blocking=True)
-                keep = (outs, sizes, dtab, hsizes)
+                self.h_sizes[slot][:k].copy_(sizes[:k], non_blocking=True)
             else:
-                outs, table = [], (fsz.FszDField * len(reqs))()
+                table = (fsz.FszDField * k).from_address(self.h_table[slot].data_ptr())
                 cap_total = 0
                 for i, r in enumerate(reqs):
                     cap = _align16(4 * max(r.n, 4)) // 4
                     cap_total += cap
                     out = torch.empty(cap, dtype=torch.float32, device=self.device)
-                    outs.append(out)
                     src = r.data if r.data.data_ptr() % 16 == 0 else r.data.clone()
+                    keep.append((out, src))
                     table[i].in_, table[i].in_bytes = src.data_ptr(), src.numel()
                     table[i].out, table[i].out_capacity_elems = out.data_ptr(), cap
-                    outs.append(src)
-                dtab = torch.frombuffer(bytearray(bytes(table)), dtype=torch.uint8).pin_memory()
-                dtab = dtab.to(self.device, non_blocking=True)
-                code = fsz.fsz_decompress_batched(dtab.data_ptr(), len(reqs), cap_total,
+                nb = k * ctypes.sizeof(fsz.FszDField)
+                self.d_table[slot][:nb].copy_(self.h_table[slot][:nb], non_blocking=True)
+                code = fsz.fsz_decompress_batched(self.d_table[slot].data_ptr(), k, cap_total,
                                                   self.ws[slot].data_ptr(), self.ws_bytes,
                                                   st.cuda_stream)
-                keep = (outs, dtab)
             ev = torch.cuda.Event()
             ev.record(st)
         return {"event": ev, "code": code, "keep": keep, "kind": kind, "slot": slot}
@@ -138,19 +144,18 @@ class GpuBackend:
 
     def results(self, h, reqs):
         fsz = self.fsz
+        slot = h["slot"]
         per = (ctypes.c_uint32 * len(reqs))()
-        first = fsz.fsz_check_batched(self.ws[h["slot"]].data_ptr(), len(reqs), per,
-                                      self.streams[h["slot"]].cuda_stream)
+        first = fsz.fsz_check_batched(self.ws[slot].data_ptr(), len(reqs), per,
+                                      self.streams[slot].cuda_stream)
         out = []
         for i, r in enumerate(reqs):
             status = h["code"] if h["code"] else (int(per[i]) if first != fsz.ERR_CUDA else first)
             if h["kind"] == COMPRESS:
-                outs, sizes, dtab, hsizes = h["keep"]
-                nb = int(hsizes[i])
-                out.append((status, outs[i][:nb], nb))
+                nb = int(self.h_sizes[slot][i])
+                out.append((status, h["keep"][i][:nb], nb))
             else:
-                outs, dtab = h["keep"]
-                out.append((status, outs[2 * i][: r.n], 0))
+                out.append((status, h["keep"][i][0][: r.n], 0))
         return out
 
 

@@ -86,7 +86,7 @@ fsz_status check_compress(const float* d_in, fsz_dims dims, fsz_eb_mode mode, do
   d.ndim = dims.ndim;
   d.mode = uint32_t(mode);
   d.eb_req = eb;
-  d.nchunks = (T + kChunkTiles - 1) / kChunkTiles;
+  d.nchunks = (T + kCChunkTiles - 1) / kCChunkTiles;
   return FSZ_OK;
 }
 

@@ -1,18 +1,23 @@
 // FSZ single-pass compression kernel (Sec. 3.1 steps 1-5, Sec. 4).
 //
 // Persistent, warp-specialised CTAs (no CTA-wide barrier in the main loop; the roles
-// hand chunks to one another through mbarriers):
-//   producer warp  takes chunk tickets and stages each chunk of kChunkTiles tiles in
-//                  shared memory with a 1-D TMA bulk copy, kStages chunks ahead;
+// hand work to one another through mbarriers):
+//   producer warp  takes a ticket per chunk of kCChunkTiles tiles and stages the chunk
+//                  in shared memory, one half of kStageTiles tiles per 1-D TMA bulk copy;
 //   compute warps  (8) quantize, predict, evaluate the four variants, select and encode
-//                  one tile at a time from registers into a per-tile slot in shared
-//                  memory, and write the tile's rate header (steps 1-3 and 5; the tile is
-//                  read from HBM once);
-//   scanner warp   scans the chunk's tile sizes, publishes the chunk's aggregate flag,
-//                  looks back for the chunk's exclusive byte offset (step 4, Sec. 4.4) and
-//                  publishes the inclusive prefix;
-//   compute warps  copy each chunk's slots to their place in the stream kDefer chunks
-//                  later, by which time the scanner has resolved the chunk's offset.
+//                  one tile at a time from registers into the warp's own ring buffer in
+//                  shared memory, and write the tile's rate header (steps 1-3 and 5; the
+//                  tile is read from HBM once). The last warp through a chunk scans its
+//                  tile sizes and publishes the chunk's aggregate flag;
+//   resolver warp  looks back for the chunk's exclusive byte offset (step 4, Sec. 4.4)
+//                  and publishes the inclusive prefix;
+//   compute warps  copy their tiles of each resolved chunk from the ring to the stream,
+//                  whenever one has resolved (between stages and while waiting for input);
+//                  they wait for an offset only when their ring is full.
+// The ring decouples encoding from the device-wide scan: chunks finish out of ticket order
+// across the grid, and a chunk's offset is known only when every earlier chunk has
+// published its size, so the encoded bytes wait in shared memory meanwhile (about
+// kRingBytes / 250 B tiles per warp at the typical rate, at least one chunk at the worst).
 #include "fsz_internal.cuh"
 
 namespace fsz {
@@ -21,18 +26,27 @@ namespace {
 
 constexpr int kComputeWarps = 8;
 constexpr int kProducerWarp = kComputeWarps;
-constexpr int kScannerWarp = kComputeWarps + 1;
+constexpr int kResolverWarp = kComputeWarps + 1;
 constexpr int kThreads = (kComputeWarps + 2) * 32;
-constexpr int kStages = 2;            // TMA input stages
-constexpr int kSets = 3;              // slot sets of encoded tiles
-constexpr int kDefer = kSets - 1;     // chunk j is copied out while computing chunk j + kDefer
+constexpr int kStageTiles = 16;                    // tiles per TMA stage (half a chunk)
+constexpr int kStageElems = kStageTiles * kTile;
+constexpr int kStages = 2;                         // TMA input stages
+constexpr int kSets = 8;                           // chunks in flight per CTA
+constexpr int kRingBytes = 4096;                   // encoded-tile ring per compute warp
+#ifndef FSZ_C_LOOKBACK
+#define FSZ_C_LOOKBACK 4
+#endif
+constexpr int kLookbackPerLane = FSZ_C_LOOKBACK;   // lookback window: 32 x this flags
 constexpr uint32_t kNone = 0xffffffffu;
-constexpr int kSlot = kMaxTileBytes;
-static_assert(kChunkTiles <= 32, "one lane per tile in the chunk scan");
-static_assert(kSlot % 4 == 0, "slots hold 32-bit words");
+static_assert(kCChunkTiles == 2 * kStageTiles, "a chunk is two stages");
+static_assert(kCChunkTiles <= 32, "one lane per tile in the chunk scan");
+static_assert(kRingBytes >= kMaxTileBytes * (kCChunkTiles / kComputeWarps) + kMaxTileBytes,
+              "a ring holds a warp's worst-case share of one chunk, after any wrap");
+static_assert(kRingBytes <= 65536, "ring offsets are 16-bit");
+static_assert(kMaxTileBytes % 4 == 0, "tiles are 32-bit words");
 
-// A chunk's parameters, read once from the field record by the producer and handed to the
-// other warps through shared memory (keeps dependent global loads off the compute path).
+// A chunk's parameters, read once from the field record by the producer and kept in the
+// chunk's set until every compute warp has placed the chunk.
 constexpr uint32_t kInfoOk = 1u, kInfoLast = 2u, kInfoFirst = 4u, kInfoSkip = 8u;
 struct ChunkInfo {
   const float* in;       // the chunk's first element
@@ -45,24 +59,31 @@ struct ChunkInfo {
   uint32_t chunk;        // global ticket, or kNone
   uint32_t ntiles;
   uint32_t cnt;          // valid elements in the chunk
-  uint32_t bulk_elems;   // elements covered by the TMA copy
   float r;
   uint32_t flags;        // kInfo* bits
+  uint32_t pad;
+};
+
+struct StageInfo {
+  uint32_t seq;   // the CTA's chunk sequence number of the staged chunk
+  uint32_t half;  // which half of it
 };
 
 struct __align__(16) CompressSmem {
-  float in[kStages][kChunkElems];            // TMA stages
-  uint8_t slot[kSets][kChunkTiles][kSlot];   // encoded tiles awaiting their offset
-  uint64_t hdr[kComputeWarps];               // per-warp scratch: one tile's 8 header bytes
-  uint32_t tbytes[kSets][kChunkTiles];
-  uint32_t toff[kSets][kChunkTiles];
+  float in[kStages][kStageElems];                 // TMA stages
+  uint8_t ring[kComputeWarps][kRingBytes];        // encoded tiles awaiting their offset
+  ChunkInfo meta[kSets];
+  ChunkInfo pre[2];                               // producer's tickets taken ahead
   uint64_t set_excl[kSets];
-  uint32_t set_total[kSets];
-  ChunkInfo stage_info[kStages];             // producer -> compute warps
-  ChunkInfo pre[2];                          // producer's tickets taken ahead
-  ChunkInfo set_info[kSets];                 // compute warp 0 -> scanner
-  ChunkInfo warp_info[kComputeWarps][kSets]; // each compute warp's own copy, for its copy-out
-  uint64_t full[kStages], empty[kStages], computed[kSets], resolved[kSets];
+  uint64_t hdr[kComputeWarps];                    // per-warp scratch: one tile's header
+  uint32_t toff[kSets][kCChunkTiles];             // tile offsets inside the chunk
+  uint32_t ring_mark[kComputeWarps][kSets];       // ring head after the warp's share
+  uint32_t set_tot[kSets];
+  uint32_t done_cnt[kSets];
+  uint16_t tsize[kSets][kCChunkTiles];            // encoded tile sizes
+  uint16_t roff[kSets][kCChunkTiles];             // ring offsets of the tiles
+  StageInfo stage[kStages];
+  uint64_t full[kStages], empty[kStages], computed[kSets], resolved[kSets], setfree[kSets];
 };
 
 // Eq. 3: S_b = 0 for r_b = 0, else 4 + 4 r_b.
@@ -238,8 +259,10 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
       mbar_init(&S.empty[k], kComputeWarps);
     }
     for (int k = 0; k < kSets; ++k) {
-      mbar_init(&S.computed[k], kComputeWarps);
+      mbar_init(&S.computed[k], 1);
       mbar_init(&S.resolved[k], 1);
+      mbar_init(&S.setfree[k], kComputeWarps);
+      S.done_cnt[k] = 0;
     }
     fence_mbar_init();
   }
@@ -248,7 +271,8 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
   if (warp == kProducerWarp) {
     // ---------------------------------------------------------------- producer
     // Tickets are taken two chunks ahead, so the ticket atomic and the field-record loads
-    // overlap the wait for a free stage; a free stage is refilled at once.
+    // overlap the waits; a chunk's record goes to its set once the chunk kSets earlier has
+    // been placed by every compute warp, and each half goes out as soon as a stage frees.
     if (lane != 0) return;
     const bool single = a.ctrl->nfields == 1;
     auto fetch = [&](ChunkInfo& ci) {
@@ -258,11 +282,9 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
       FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
       const uint64_t first = fi->chunk_first;
       const uint64_t lc = c - first;
-      const uint64_t tile0 = lc * kChunkTiles;
+      const uint64_t tile0 = lc * kCChunkTiles;
       const uint64_t e0 = tile0 * kTile;
       const uint64_t T = fi->T;
-      const uint32_t cnt = uint32_t(min(fi->n - e0, uint64_t(kChunkElems)));
-      const bool ok = fi->s > 0.0f;  // a field without a step has nothing to load
       ci.in = fi->in + e0;
       ci.out = fi->out;
       ci.fi = fi;
@@ -270,157 +292,180 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
       ci.data_base = 64 + 8 * T;
       ci.cap = fi->cap;
       ci.chunk_first = first;
-      ci.ntiles = uint32_t(min(uint64_t(kChunkTiles), T - tile0));
-      ci.cnt = cnt;
-      ci.bulk_elems = ok ? ((cnt * 4) & ~15u) / 4 : 0u;
+      ci.ntiles = uint32_t(min(uint64_t(kCChunkTiles), T - tile0));
+      ci.cnt = uint32_t(min(fi->n - e0, uint64_t(kCChunkElems)));
       ci.r = fi->r;
-      ci.flags = (ok ? kInfoOk : 0u) | (lc + 1 == fi->nchunks ? kInfoLast : 0u) |
-                 (lc == 0 ? kInfoFirst : 0u) | (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
+      ci.flags = (fi->s > 0.0f ? kInfoOk : 0u) |  // a field without a step has nothing to load
+                 (lc + 1 == fi->nchunks ? kInfoLast : 0u) | (lc == 0 ? kInfoFirst : 0u) |
+                 (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
     };
     fetch(S.pre[0]);
     fetch(S.pre[1]);
-    for (uint32_t j = 0;; ++j) {
-      const int s = int(j % kStages);
-      if (j >= uint32_t(kStages) && !mbar_wait(&S.empty[s], ((j / kStages) - 1) & 1u, wait_ns)) {
+    uint32_t u = 0;  // stage uses so far
+    auto take_stage = [&](uint32_t seq, uint32_t h) -> int {
+      const int s = int(u % kStages);
+      if (u >= uint32_t(kStages) && !mbar_wait(&S.empty[s], ((u / kStages) - 1) & 1u, wait_ns)) {
+        set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return -1;
+      }
+      S.stage[s].seq = seq;
+      S.stage[s].half = h;
+      ++u;
+      return s;
+    };
+    for (uint32_t seq = 0;; ++seq) {
+      const int b = int(seq % kSets);
+      if (seq >= uint32_t(kSets) && !mbar_wait(&S.setfree[b], ((seq / kSets) - 1) & 1u, wait_ns)) {
         set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
         return;
       }
-      ChunkInfo& q = S.pre[j & 1];
-      S.stage_info[s] = q;
+      ChunkInfo& q = S.pre[seq & 1];
+      S.meta[b] = q;
       if (q.chunk >= total) {
-        S.stage_info[s].chunk = kNone;
-        mbar_arrive(&S.full[s]);
+        S.meta[b].chunk = kNone;
+        const int s = take_stage(seq, 0);
+        if (s >= 0) mbar_arrive(&S.full[s]);
         return;
       }
-      const uint32_t bulk = q.bulk_elems * 4;
-      fence_proxy_async();
-      mbar_arrive_expect_tx(&S.full[s], bulk);
-      if (bulk) tma_load_1d(S.in[s], q.in, bulk, &S.full[s]);
+      const uint32_t halves = q.ntiles > uint32_t(kStageTiles) ? 2u : 1u;
+      for (uint32_t h = 0; h < halves; ++h) {
+        const int s = take_stage(seq, h);
+        if (s < 0) return;
+        const uint32_t e_h = h * kStageElems;
+        const uint32_t valid = min(q.cnt - e_h, uint32_t(kStageElems));
+        const uint32_t bulk = (q.flags & kInfoOk) ? ((valid * 4) & ~15u) : 0u;
+        fence_proxy_async();
+        mbar_arrive_expect_tx(&S.full[s], bulk);
+        if (bulk) tma_load_1d(S.in[s], q.in + e_h, bulk, &S.full[s]);
+      }
       fetch(q);  // the ticket two chunks ahead
     }
   }
 
-  if (warp == kScannerWarp) {
-    // ---------------------------------------------------------------- scanner
-    // Chunk j's aggregate is published as soon as its tiles are encoded; chunk j's
-    // lookback waits until chunk j + 1 is encoded, so that the chunks ticketed next to
-    // chunk j on other SMs have published theirs by then.
-    uint32_t prev_c = kNone, prev_tot = 0, prev_flags = 0;
-    uint64_t prev_first = 0;
-    FieldInfo* prev_fi = nullptr;
-    int prev_b = 0;
-    auto resolve = [&](uint32_t c, uint64_t first, uint32_t flags, FieldInfo* fi, uint32_t tot, int b) {
+  if (warp == kResolverWarp) {
+    // ---------------------------------------------------------------- resolver
+    // Step 4 at device level, one chunk after another in this CTA's ticket order, as soon
+    // as the chunk's aggregate is out: the compute warps keep encoding meanwhile.
+    for (uint32_t seq = 0;; ++seq) {
+      const int b = int(seq % kSets);
+      if (!mbar_wait(&S.computed[b], (seq / kSets) & 1u, wait_ns)) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      const ChunkInfo& ci = S.meta[b];
+      const uint32_t c = ci.chunk;
+      if (c == kNone) return;
+      const uint32_t flags = ci.flags;
+      const uint32_t tot = S.set_tot[b];
       uint64_t excl = 0;
       if (!(flags & kInfoFirst)) {
         bool to = false;
-        excl = lookback(a.flags, int64_t(c), int64_t(first), globaltimer_ns() + a.timeout_ns, &to);
+        excl = lookback<kLookbackPerLane>(a.flags, int64_t(c), int64_t(ci.chunk_first),
+                                          globaltimer_ns() + a.timeout_ns, &to);
         if (lane == 0) {
-          if (to) set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
+          if (to) set_error(a.ctrl, ci.fi, FSZ_ERR_TIMEOUT);
           if (!(flags & kInfoSkip)) st_flag(a.flags + c, kFlagIncl | (excl + tot));
         }
       }
       __syncwarp();
       if (lane == 0) {
         S.set_excl[b] = excl;
-        S.set_total[b] = tot;
         mbar_arrive(&S.resolved[b]);
       }
-    };
-    for (uint32_t j = 0;; ++j) {
-      const int b = int(j % kSets);
-      if (!mbar_wait(&S.computed[b], (j / kSets) & 1u, wait_ns)) {
-        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-        return;
-      }
-      const ChunkInfo& ci = S.set_info[b];
-      const uint32_t c = ci.chunk;
-      if (c == kNone) break;
-      const uint32_t flags = ci.flags;
-      const int ntiles = int(ci.ntiles);
-      // Thread and warp levels of the scan over the chunk's tiles; the chunk's aggregate.
-      const uint32_t mine = ((flags & kInfoOk) && lane < ntiles) ? S.tbytes[b][lane] : 0u;
-      uint32_t inc = mine;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += x;
-      }
-      if (lane < kChunkTiles) S.toff[b][lane] = inc - mine;
-      const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-      if (lane == 0 && !(flags & kInfoSkip))
-        st_flag(a.flags + c, ((flags & kInfoFirst) ? kFlagIncl : kFlagAgg) | tot);
-      // Device level for the previous chunk.
-      if (prev_c != kNone) resolve(prev_c, prev_first, prev_flags, prev_fi, prev_tot, prev_b);
-      prev_c = c;
-      prev_first = ci.chunk_first;
-      prev_flags = flags;
-      prev_fi = ci.fi;
-      prev_tot = tot;
-      prev_b = b;
     }
-    if (prev_c != kNone) resolve(prev_c, prev_first, prev_flags, prev_fi, prev_tot, prev_b);
-    return;
   }
 
   // ------------------------------------------------------------------ compute warps
-  // Copies this warp's tiles of chunk k (slot set k % kSets) into the stream.
-  auto copy_out = [&](uint32_t k) -> bool {
-    const int b = int(k % kSets);
-    if (!mbar_wait(&S.resolved[b], (k / kSets) & 1u, wait_ns)) return false;
-    const ChunkInfo& ci = S.warp_info[warp][b];
-    if ((ci.flags & (kInfoOk | kInfoSkip)) != kInfoOk) return true;
-    const uint64_t excl = S.set_excl[b];
-    const uint32_t tot = S.set_total[b];
-    if (ci.data_base + excl + tot > ci.cap) {
-      if (lane == 0) set_error(a.ctrl, ci.fi, FSZ_ERR_CAPACITY);
-    } else {
-      uint8_t* base = ci.out + ci.data_base + excl;
-      for (int tl = warp; tl < int(ci.ntiles); tl += kComputeWarps) {
-        const uint32_t nw = S.tbytes[b][tl] >> 2;
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(S.slot[b][tl]);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][tl]);
-        for (uint32_t q = lane; q < nw; q += 32) dst[q] = src[q];
+  uint8_t* const ring = S.ring[warp];
+  uint32_t head = 0, tail = 0;  // ring byte counters (warp-uniform)
+  uint32_t placed = 0;          // this CTA's chunks placed by this warp so far
+  uint32_t done = 0;            // ... encoded by this warp so far
+
+  // Copies this warp's tiles of chunk `placed` (resolved) into the stream and frees them.
+  auto place = [&]() {
+    const int b = int(placed % kSets);
+    const ChunkInfo& ci = S.meta[b];
+    if ((ci.flags & (kInfoOk | kInfoSkip)) == kInfoOk) {
+      const uint64_t excl = S.set_excl[b];
+      const uint32_t tot = S.set_tot[b];
+      if (ci.data_base + excl + tot > ci.cap) {
+        if (lane == 0) set_error(a.ctrl, ci.fi, FSZ_ERR_CAPACITY);
+      } else {
+        uint8_t* base = ci.out + ci.data_base + excl;
+        for (int tl = warp; tl < int(ci.ntiles); tl += kComputeWarps) {
+          const uint32_t nw = uint32_t(S.tsize[b][tl]) >> 2;
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(ring + S.roff[b][tl]);
+          uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][tl]);
+          for (uint32_t q = lane; q < nw; q += 32) dst[q] = src[q];
+        }
+        if (warp == 0 && lane == 0 && (ci.flags & kInfoLast)) write_preamble(ci.fi, excl + tot);
       }
-      if (warp == 0 && lane == 0 && (ci.flags & kInfoLast)) write_preamble(ci.fi, excl + tot);
     }
+    tail = S.ring_mark[warp][b];
+    ++placed;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.setfree[b]);
+  };
+  // Places every chunk that has resolved, without waiting.
+  auto place_ready = [&]() {
+    while (placed < done && mbar_test(&S.resolved[placed % kSets], (placed / kSets) & 1u)) place();
+  };
+  // Places the oldest chunk, waiting for its offset.
+  auto place_oldest = [&]() -> bool {
+    if (!mbar_wait(&S.resolved[placed % kSets], (placed / kSets) & 1u, wait_ns)) return false;
+    place();
     return true;
   };
 
-  uint32_t j = 0;
-  for (;; ++j) {
-    const int s = int(j % kStages), b = int(j % kSets);
-    if (!mbar_wait(&S.full[s], (j / kStages) & 1u, wait_ns)) {
-      if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-      return;
+  bool ok_run = true;
+  for (uint32_t u = 0;; ++u) {
+    const int s = int(u % kStages);
+    const uint32_t par = (u / kStages) & 1u;
+    // Wait for the stage, placing resolved chunks meanwhile (the producer may be waiting
+    // for this warp to free a set).
+    {
+      const uint64_t deadline = globaltimer_ns() + wait_ns;
+      bool got = false;
+      while (!got) {
+        if (placed < done) {
+          if (mbar_test(&S.resolved[placed % kSets], (placed / kSets) & 1u)) {
+            place();
+            continue;
+          }
+          got = mbar_try_wait_for(&S.full[s], par, 2000u);
+        } else {
+          got = mbar_try_wait_sleep(&S.full[s], par);
+        }
+        if (!got && globaltimer_ns() > deadline) break;
+      }
+      if (!got) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        ok_run = false;
+        break;
+      }
     }
-    const ChunkInfo& ci = S.stage_info[s];
-    // Keep the chunk's parameters past the stage's reuse: this warp's copy, and warp 0's
-    // copy for the scanner (16 lanes copy 4 bytes each).
-    static_assert(sizeof(ChunkInfo) % 4 == 0 && sizeof(ChunkInfo) <= 128, "ChunkInfo copy");
-    if (lane < int(sizeof(ChunkInfo) / 4)) {
-      const uint32_t w = reinterpret_cast<const uint32_t*>(&ci)[lane];
-      reinterpret_cast<uint32_t*>(&S.warp_info[warp][b])[lane] = w;
-      if (warp == 0) reinterpret_cast<uint32_t*>(&S.set_info[b])[lane] = w;
-    }
-    if (warp == 0) __threadfence_block();  // all lanes' copies before lane 0's arrival
+    const uint32_t seq = S.stage[s].seq, h = S.stage[s].half;
+    const int b = int(seq % kSets);
+    const ChunkInfo& ci = S.meta[b];
     const uint32_t c = ci.chunk;
-    if (c == kNone) {
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.computed[b]);  // tells the scanner to stop
-      break;
-    }
     const uint32_t flags = ci.flags;
-    if (flags & kInfoOk) {
+    const int ntiles = int(ci.ntiles);
+    const bool end = (c == kNone);
+    const bool last_half = end || (h + 1 == (ntiles > kStageTiles ? 2u : 1u));
+    if (!end && (flags & kInfoOk)) {
       const float r = ci.r;
-      const int ntiles = int(ci.ntiles);
-      const uint32_t cnt = ci.cnt, bulk_elems = ci.bulk_elems;
-      const float* gin = ci.in;
+      const uint32_t e_h = h * kStageElems;
+      const uint32_t cnt = min(ci.cnt - e_h, uint32_t(kStageElems));
+      const uint32_t bulk_elems = ((cnt * 4) & ~15u) / 4;
+      const float* gin = ci.in + e_h;
       uint64_t* hdr_out = reinterpret_cast<uint64_t*>(ci.out + 64) + ci.tile0;
-      for (int tl = warp; tl < ntiles; tl += kComputeWarps) {
-        float* tile = S.in[s] + tl * kTile;
+      const int t_end = min(ntiles, int(h + 1) * kStageTiles);
+      for (int tl = int(h) * kStageTiles + warp; tl < t_end; tl += kComputeWarps) {
+        const int ts = tl - int(h) * kStageTiles;  // tile within the stage
+        float* tile = S.in[s] + ts * kTile;
         // Ragged end of a field: this lane's elements past the last 16-byte boundary of
         // the bulk copy by plain loads; padding elements are zeros (they quantize to 0).
-        const uint32_t k0 = uint32_t(tl) * kTile + 8u * uint32_t(lane);
+        const uint32_t k0 = uint32_t(ts) * kTile + 8u * uint32_t(lane);
         if (k0 + 8 > bulk_elems) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -428,31 +473,80 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
             if (k >= bulk_elems) tile[8 * lane + i] = k < cnt ? gin[k] : 0.0f;
           }
         }
-        const uint32_t nb = compress_tile(tile, S.slot[b][tl],
-                                          reinterpret_cast<uint8_t*>(&S.hdr[warp]), r, lane);
+        // Room for a worst-case tile, contiguous in the ring (a tile never wraps). The
+        // counters only grow: a chunk this warp has no tile in still holds a mark.
+        uint32_t pos = head % kRingBytes;
+        uint32_t skip = pos + kMaxTileBytes > kRingBytes ? kRingBytes - pos : 0u;
+        while (kRingBytes - (head - tail) < skip + kMaxTileBytes) {
+          if (placed == done || !place_oldest()) {  // cannot happen with an empty ring
+            if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+            ok_run = false;
+            break;
+          }
+          pos = head % kRingBytes;
+          skip = pos + kMaxTileBytes > kRingBytes ? kRingBytes - pos : 0u;
+        }
+        if (!ok_run) break;
+        head += skip;
+        pos = head % kRingBytes;
+        const uint32_t nb = compress_tile(tile, ring + pos, reinterpret_cast<uint8_t*>(&S.hdr[warp]), r, lane);
         __syncwarp();
         if (lane == 0) {
-          S.tbytes[b][tl] = nb;
+          S.tsize[b][tl] = uint16_t(nb);
+          S.roff[b][tl] = uint16_t(pos);
           hdr_out[tl] = S.hdr[warp];
         }
+        head += nb;
         __syncwarp();
       }
+      if (!ok_run) break;
     }
     __syncwarp();
-    if (lane == 0) {
-      mbar_arrive(&S.empty[s]);     // done reading the stage
-      mbar_arrive(&S.computed[b]);  // tile sizes ready for the scanner
+    if (!end && lane == 0) mbar_arrive(&S.empty[s]);  // done reading the stage
+    if (last_half) {
+      // This warp is through the chunk: the last warp to get here scans the chunk's tile
+      // sizes and publishes its aggregate (step 4, thread and warp levels).
+      uint32_t last = 0;
+      S.ring_mark[warp][b] = head;  // every lane (the same value): read by every lane
+      if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&S.done_cnt[b], 1u) == uint32_t(kComputeWarps - 1) ? 1u : 0u;
+        __threadfence_block();
+      }
+      last = __shfl_sync(0xffffffffu, last, 0);
+      __syncwarp();
+      if (last) {
+        if (!end) {
+          const uint32_t mine = ((flags & kInfoOk) && lane < ntiles) ? uint32_t(S.tsize[b][lane]) : 0u;
+          uint32_t inc = mine;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += x;
+          }
+          S.toff[b][lane] = inc - mine;
+          const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+          if (lane == 0) {
+            S.set_tot[b] = tot;
+            if (!(flags & kInfoSkip)) st_flag(a.flags + c, ((flags & kInfoFirst) ? kFlagIncl : kFlagAgg) | tot);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          S.done_cnt[b] = 0;
+          mbar_arrive(&S.computed[b]);
+        }
+      }
+      if (end) break;
+      ++done;
     }
-    if (j >= uint32_t(kDefer) && !copy_out(j - kDefer)) {
-      if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-      return;
-    }
+    place_ready();
   }
-  // Chunks computed but not yet placed.
-  for (uint32_t k = j >= uint32_t(kDefer) ? j - kDefer : 0; k < j; ++k) {
-    if (!copy_out(k)) {
+  // Chunks encoded but not yet placed.
+  while (ok_run && placed < done) {
+    if (!place_oldest()) {
       if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-      return;
+      break;
     }
   }
 }

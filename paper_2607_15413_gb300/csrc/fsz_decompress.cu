@@ -22,16 +22,17 @@ constexpr int kHeaderWarp = kDecodeWarps;
 constexpr int kLoaderWarp = kDecodeWarps + 1;
 constexpr int kThreads = (kDecodeWarps + 2) * 32;
 constexpr int kStages = 3;
-constexpr int kPayloadBytes = kChunkTiles * kMaxDecTileBytes + 32;
-static_assert(kChunkTiles <= 32, "one lane per tile in the chunk scan");
+constexpr int kPayloadBytes = kDChunkTiles * kMaxDecTileBytes + 32;
+static_assert(kDChunkTiles <= 32, "one lane per tile in the chunk scan");
 static_assert(kPayloadBytes % 16 == 0, "stage size");
 constexpr uint32_t kNoneChunk = 0xffffffffu;
+constexpr int kLookbackPerLane = 4;  // 128-flag lookback window
 
 // A chunk's header and parameters, handed from the header warp to the loader and the
 // decode warps through shared memory (keeps dependent global loads off the decode path).
 struct StageInfo {
-  uint64_t hdr[kChunkTiles];
-  uint32_t toff[kChunkTiles];
+  uint64_t hdr[kDChunkTiles];
+  uint32_t toff[kDChunkTiles];
   FieldInfo* fi;
   float* dout;     // the chunk's first output element
   uint32_t chunk;  // ticket held by the stage
@@ -186,11 +187,11 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
       }
       FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
       const uint64_t lc = c - fi->chunk_first;
-      const uint64_t tile0 = lc * kChunkTiles;
-      const int ntiles = int(min(uint64_t(kChunkTiles), fi->T - tile0));
+      const uint64_t tile0 = lc * kDChunkTiles;
+      const int ntiles = int(min(uint64_t(kDChunkTiles), fi->T - tile0));
       uint64_t hb = 0;
       if (lane < ntiles) hb = __ldg(reinterpret_cast<const unsigned long long*>(fi->sin + 64) + tile0 + lane);
-      if (lane < kChunkTiles) q.hdr[lane] = hb;
+      if (lane < kDChunkTiles) q.hdr[lane] = hb;
       const bool bad_hdr = __any_sync(FULL, lane < ntiles && header_reserved_bits_set(hb));
       const uint32_t mine = lane < ntiles ? tile_bytes_from_header(hb) : 0u;
       uint32_t inc = mine;
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
         const uint32_t y = __shfl_up_sync(FULL, inc, o);
         if (lane >= o) inc += y;
       }
-      if (lane < kChunkTiles) q.toff[lane] = inc - mine;
+      if (lane < kDChunkTiles) q.toff[lane] = inc - mine;
       const uint32_t tot = __shfl_sync(FULL, inc, 31);
       if (lane == 0) {
         q.chunk = c;
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
         q.fi = fi;
         q.dout = fi->dout + tile0 * kTile;
         q.ntiles = uint32_t(ntiles);
-        q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kChunkElems)));
+        q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kDChunkElems)));
         q.step = fi->s;
         if (uint64_t(c) != a.skip_chunk) st_flag(a.flags + c, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
       }
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
       uint64_t excl = 0;
       if (lc != 0) {
         bool to = false;
-        excl = lookback(a.flags, int64_t(c), int64_t(fi->chunk_first), globaltimer_ns() + a.timeout_ns,
+        excl = lookback<kLookbackPerLane>(a.flags, int64_t(c), int64_t(fi->chunk_first), globaltimer_ns() + a.timeout_ns,
                         &to);
         if (lane == 0) {
           if (to) set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);

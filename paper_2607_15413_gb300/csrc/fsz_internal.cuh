@@ -1,11 +1,11 @@
 // Internal definitions shared by the FSZ CUDA kernels (sm_103a).
 //
 // Work decomposition (GB300 design, not the paper's): a persistent CTA takes chunks of
-// kChunkTiles tiles by an atomic ticket, stages each chunk in shared memory with 1-D
-// TMA bulk copies (double-buffered, mbarrier-tracked) and gives each warp one 256-element
-// tile at a time. Lane j of the warp owns the 8 consecutive elements 8j..8j+7, so the
-// 4 lanes 4g..4g+3 hold block g (Sec. 3.1: a tile is 8 blocks of 32 elements). Residual
-// chains stay in registers; a shuffle carries the state across lane and block boundaries.
+// tiles by an atomic ticket, stages them in shared memory with 1-D TMA bulk copies
+// (mbarrier-tracked) and gives each warp one 256-element tile at a time. Lane j of the
+// warp owns the 8 consecutive elements 8j..8j+7, so the 4 lanes 4g..4g+3 hold block g
+// (Sec. 3.1: a tile is 8 blocks of 32 elements). Residual chains stay in registers; a
+// shuffle carries the state across lane and block boundaries.
 #pragma once
 
 #include <cstdint>
@@ -20,11 +20,15 @@ constexpr int kMaxTileBytes = 708;    // 8 * (4 + 4 * 21) + 4, Eq. 3 with rate <
 constexpr int kMaxDecTileBytes = 1028;  // any header-valid tile: 8 * (4 + 4 * 31) + 4
 constexpr uint32_t kQmax = 174761;    // largest Q with (3Q + 4) 2^-23 <= 2^-4
 constexpr int kMinChunkTiles = 16;    // smallest chunk any kernel uses (workspace sizing)
-#ifndef FSZ_CHUNK_TILES
-#define FSZ_CHUNK_TILES 16
-#endif
-constexpr int kChunkTiles = FSZ_CHUNK_TILES;  // tiles per work item of every kernel
-constexpr int kChunkElems = kChunkTiles * kTile;
+// Tiles per work item (one ticket, one lookback flag). Compression (and its value-range
+// pass, which shares the chunk -> field table) uses 32-tile chunks: fewer device-wide
+// scan links per byte. Decompression stages a chunk's whole payload at once, so its
+// chunks stay at 16 tiles.
+constexpr int kCChunkTiles = 32;
+constexpr int kCChunkElems = kCChunkTiles * kTile;
+constexpr int kDChunkTiles = 16;
+constexpr int kDChunkElems = kDChunkTiles * kTile;
+static_assert(kCChunkTiles >= kMinChunkTiles && kDChunkTiles >= kMinChunkTiles, "workspace sizing");
 constexpr uint64_t kMaxElems = uint64_t(1) << 40;
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;
 
@@ -188,6 +192,32 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
   return ok != 0;
 }
 
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// try_wait that may suspend the thread for up to `hint_ns` while the phase is incomplete.
+__device__ __forceinline__ bool mbar_try_wait_for(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
 // Waits for the phase of `bar` with the given parity; false if `timeout_ns` ran out first.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t timeout_ns) {
   if (mbar_try_wait_sleep(bar, parity)) return true;
@@ -261,24 +291,27 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 
 // Exclusive prefix of the chunks before `gchunk` within its field (Sec. 4.4, device
 // level: decoupled lookback over the 3-state flags). Called by one whole warp. A window
-// holds the 32 * kLookbackPerLane nearest predecessors not yet summed (128 by default:
-// wider windows measured slower, because more of the flags they cover belong to chunks
-// still queued behind other CTAs' prefetched tickets) (lane L holds
-// distances kLookbackPerLane * L + k, nearest first). The warp waits only for flags that
-// are still unpublished AND nearer than the nearest inclusive prefix; then it sums every
-// flag up to that prefix, or the whole window and moves on. Every spin is bounded by
-// `deadline`; a wait that runs out reads as a zero inclusive prefix and sets *timed_out
-// (the caller records FSZ_ERR_TIMEOUT and still publishes, so no successor waits forever).
-#ifndef FSZ_LOOKBACK_PER_LANE
-#define FSZ_LOOKBACK_PER_LANE 4
-#endif
-constexpr int kLookbackPerLane = FSZ_LOOKBACK_PER_LANE;
-
+// holds the 32 * K nearest predecessors not yet summed, interleaved so that each load
+// instruction of the warp reads 32 consecutive flags (lane L, slot k holds distance
+// 32 k + L, nearest first). The warp waits only for flags that are still unpublished AND
+// nearer than the nearest inclusive prefix; then it sums every flag up to that prefix, or
+// the whole window and moves on.
+//
+// A lookback costs about one L2 round trip per window, and the nearest inclusive prefix
+// trails a chunk by the chunks that finish during about one lookback, so the window must
+// cover what the grid finishes in one round trip. Upgrading other chunks' aggregate flags
+// to inclusive ones during a lookback was measured several times slower (store contention
+// on the flag lines) and is not done.
+//
+// Every spin is bounded by `deadline`; a wait that runs out reads as a zero inclusive
+// prefix and sets *timed_out (the caller records FSZ_ERR_TIMEOUT and still publishes, so
+// no successor waits forever).
+template <int K>
 __device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchunk, int64_t first,
                                              uint64_t deadline, bool* timed_out) {
   constexpr uint32_t FULL = 0xffffffffu;
   constexpr uint32_t kNoIncl = 1u << 20, kNoWait = 1u << 21;  // beyond any window distance
-  static_assert(kLookbackPerLane <= 32, "per-lane state masks are 32 bits");
+  static_assert(K >= 1 && K <= 32, "per-lane state masks are 32 bits");
   const int lane = threadIdx.x & 31;
   uint64_t excl = 0;
   bool to = false;
@@ -287,7 +320,7 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchu
     // Aggregates are a chunk's byte count (< 2^16), so a slot keeps its value's low 32 bits
     // and the lane keeps, as bit masks, which slots are unpublished or inclusive; the full
     // value of the lane's nearest inclusive prefix is kept aside.
-    uint32_t lo[kLookbackPerLane];
+    uint32_t lo[K];
     uint32_t wait_mask = 0, incl_mask = 0;
     uint64_t incl_val = 0;
     auto take = [&](int k, uint64_t f) {
@@ -301,43 +334,41 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchu
       }
     };
 #pragma unroll
-    for (int k = 0; k < kLookbackPerLane; ++k) {
-      const int64_t idx = pos - (kLookbackPerLane * lane + k);
+    for (int k = 0; k < K; ++k) {
+      const int64_t idx = pos - (32 * k + lane);
       take(k, idx >= first ? ld_flag(flags + idx) : kFlagIncl);  // before the field: 0
     }
     uint32_t d_incl;
     for (uint32_t spins = 0;; ++spins) {
-      const uint32_t my_incl = incl_mask ? uint32_t(kLookbackPerLane * lane + __ffs(incl_mask) - 1) : kNoIncl;
-      const uint32_t my_wait = wait_mask ? uint32_t(kLookbackPerLane * lane + __ffs(wait_mask) - 1) : kNoWait;
+      const uint32_t my_incl = incl_mask ? uint32_t(32 * (__ffs(incl_mask) - 1) + lane) : kNoIncl;
+      const uint32_t my_wait = wait_mask ? uint32_t(32 * (__ffs(wait_mask) - 1) + lane) : kNoWait;
       d_incl = __reduce_min_sync(FULL, my_incl);
       const uint32_t d_wait = __reduce_min_sync(FULL, my_wait);
       if (d_wait > d_incl) break;  // everything up to the nearest inclusive prefix is in
       if ((spins & 15u) == 15u && globaltimer_ns() > deadline) {
         to = true;  // give up: unpublished flags read as a zero inclusive prefix
 #pragma unroll
-        for (int k = 0; k < kLookbackPerLane; ++k)
+        for (int k = 0; k < K; ++k)
           if (wait_mask & (1u << k)) take(k, kFlagIncl);
         continue;
       }
       __nanosleep(64);
 #pragma unroll
-      for (int k = 0; k < kLookbackPerLane; ++k) {
-        const uint32_t d = uint32_t(kLookbackPerLane * lane + k);
+      for (int k = 0; k < K; ++k) {
+        const uint32_t d = uint32_t(32 * k + lane);
         if ((wait_mask & (1u << k)) && d < d_incl) take(k, ld_flag(flags + (pos - int64_t(d))));
       }
     }
     // Sum the aggregates nearer than the nearest inclusive prefix, then that prefix.
     uint32_t agg = 0;
 #pragma unroll
-    for (int k = 0; k < kLookbackPerLane; ++k)
-      if (uint32_t(kLookbackPerLane * lane + k) < d_incl) agg += lo[k];
+    for (int k = 0; k < K; ++k)
+      if (uint32_t(32 * k + lane) < d_incl) agg += lo[k];
     uint64_t mine = agg;
-    if (d_incl != kNoIncl && uint32_t(kLookbackPerLane * lane) <= d_incl &&
-        d_incl < uint32_t(kLookbackPerLane * (lane + 1)))
-      mine += incl_val;
+    if (d_incl != kNoIncl && uint32_t(lane) == (d_incl & 31u)) mine += incl_val;
     excl += warp_sum_u64(mine);
     if (d_incl != kNoIncl) break;
-    pos -= 32 * kLookbackPerLane;
+    pos -= 32 * K;
   }
   *timed_out = __any_sync(FULL, to);
   return excl;

@@ -93,7 +93,7 @@ extern "C" fsz_status fsz_compress_noalloc(const float* d_in, fsz_dims dims, fsz
   desc.ndim = dims.ndim;
   desc.mode = uint32_t(mode);
   desc.eb_req = eb;
-  desc.nchunks = (T + kChunkTiles - 1) / kChunkTiles;
+  desc.nchunks = (T + kCChunkTiles - 1) / kCChunkTiles;
 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   // The array keeps the previous call's contents: clear the part this call uses.

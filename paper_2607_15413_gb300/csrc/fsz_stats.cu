@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(kStatsThreads) fsz_stats_kernel(KernelArgs a) 
       cur_f = f;
     }
     const FieldInfo* fi = a.fields + f;
-    const uint64_t e0 = (g - fi->chunk_first) * uint64_t(kChunkElems);
-    const uint64_t cnt = min(fi->n - e0, uint64_t(kChunkElems));
+    const uint64_t e0 = (g - fi->chunk_first) * uint64_t(kCChunkElems);
+    const uint64_t cnt = min(fi->n - e0, uint64_t(kCChunkElems));
     const float* p = fi->in + e0;
     const float4* p4 = reinterpret_cast<const float4*>(p);
     auto take4 = [&](float4 v) {
@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(kStatsThreads) fsz_stats_kernel(KernelArgs a) 
       uint32_t m1 = max(__float_as_uint(v.z) & 0x7fffffffu, __float_as_uint(v.w) & 0x7fffffffu);
       mabs = max(mabs, max(m0, m1));
     };
-    if (cnt == uint64_t(kChunkElems)) {
-      constexpr int kPer = kChunkElems / 4 / kStatsThreads;
+    if (cnt == uint64_t(kCChunkElems)) {
+      constexpr int kPer = kCChunkElems / 4 / kStatsThreads;
       float4 v[kPer];
 #pragma unroll
       for (int u = 0; u < kPer; ++u) v[u] = __ldcs(p4 + threadIdx.x + u * kStatsThreads);
@@ -182,7 +182,7 @@ __device__ uint32_t plan_cfield(FieldInfo* fi, const fsz_cfield& d) {
   fi->n = n;
   fi->T = T;
   if (d.out_capacity < 64 + 8 * T) return FSZ_ERR_CAPACITY;
-  fi->nchunks = (T + kChunkTiles - 1) / kChunkTiles;
+  fi->nchunks = (T + kCChunkTiles - 1) / kCChunkTiles;
   return FSZ_OK;
 }
 
@@ -238,7 +238,7 @@ __device__ uint32_t plan_dfield(FieldInfo* fi, const uint8_t* in, uint64_t in_by
   fi->s = sv;
   fi->data_bytes = db;
   if (n > cap_elems) return FSZ_ERR_CAPACITY;
-  fi->nchunks = (T + kChunkTiles - 1) / kChunkTiles;
+  fi->nchunks = (T + kDChunkTiles - 1) / kDChunkTiles;
   return FSZ_OK;
 }
 

@@ -37,6 +37,10 @@ constexpr int kRingBytes = 4096;                   // encoded-tile ring per comp
 #define FSZ_C_LOOKBACK 4
 #endif
 constexpr int kLookbackPerLane = FSZ_C_LOOKBACK;   // lookback window: 32 x this flags
+#ifndef FSZ_TICKET_AHEAD
+#define FSZ_TICKET_AHEAD 2
+#endif
+constexpr int kTicketAhead = FSZ_TICKET_AHEAD;     // chunk tickets taken ahead of use
 constexpr uint32_t kNone = 0xffffffffu;
 static_assert(kCChunkTiles == 2 * kStageTiles, "a chunk is two stages");
 static_assert(kCChunkTiles <= 32, "one lane per tile in the chunk scan");
@@ -73,15 +77,13 @@ struct __align__(16) CompressSmem {
   float in[kStages][kStageElems];                 // TMA stages
   uint8_t ring[kComputeWarps][kRingBytes];        // encoded tiles awaiting their offset
   ChunkInfo meta[kSets];
-  ChunkInfo pre[2];                               // producer's tickets taken ahead
+  ChunkInfo pre[kTicketAhead > 0 ? kTicketAhead : 1];  // producer's tickets taken ahead
   uint64_t set_excl[kSets];
-  uint64_t hdr[kComputeWarps];                    // per-warp scratch: one tile's header
   uint32_t toff[kSets][kCChunkTiles];             // tile offsets inside the chunk
   uint32_t ring_mark[kComputeWarps][kSets];       // ring head after the warp's share
   uint32_t set_tot[kSets];
   uint32_t done_cnt[kSets];
-  uint16_t tsize[kSets][kCChunkTiles];            // encoded tile sizes
-  uint16_t roff[kSets][kCChunkTiles];             // ring offsets of the tiles
+  uint32_t tinfo[kSets][kCChunkTiles];            // ring offset << 16 | encoded size
   StageInfo stage[kStages];
   uint64_t full[kStages], empty[kStages], computed[kSets], resolved[kSets], setfree[kSets];
 };
@@ -94,7 +96,8 @@ __device__ __forceinline__ uint32_t sign_mag(int l) { return (uabs32(l) << 1) | 
 
 // Compresses the 256-element tile at `tile` (shared memory) with one warp. Lane j owns
 // elements 8j..8j+7; the 4 lanes 4g..4g+3 own block g. Writes the tile's 8 rate-header
-// bytes to hdr and its encoded bytes to slot; returns the byte count (warp-uniform).
+// bytes to hdr (global) and its encoded bytes to slot; returns the byte count
+// (warp-uniform).
 __device__ __forceinline__ uint32_t compress_tile(const float* __restrict__ tile,
                                                   uint8_t* __restrict__ slot,
                                                   uint8_t* __restrict__ hdr, const float r,
@@ -164,18 +167,25 @@ __device__ __forceinline__ uint32_t compress_tile(const float* __restrict__ tile
   const int R1c = 32 - __clz(int(rest1 | x1 | x2 | c10));
   const int R2c = 32 - __clz(int(rest2 | y1 | y2 | c10 | c21));
 
-  // Tile costs C = sum of S_b (Eq. 3), plus 4 bytes for mu when centred (step 2).
-  uint32_t pk = block_cost(R1) | (block_cost(R2) << 16);
-  pk += __shfl_xor_sync(FULL, pk, 4);
-  pk += __shfl_xor_sync(FULL, pk, 8);
-  pk += __shfl_xor_sync(FULL, pk, 16);
-  const int C1 = int(pk & 0xffffu), C2 = int(pk >> 16);
+  // Block costs S_b (Eq. 3) of LZ1 and LZ2 as 16-bit halves. An inclusive scan over the
+  // 8 groups gives every block's end offset for both variants; lane 31 holds the tile
+  // costs C = sum of S_b.
+  const uint32_t pk = block_cost(R1) | (block_cost(R2) << 16);
+  uint32_t pinc = pk, tmp;
+  tmp = __shfl_up_sync(FULL, pinc, 4); if (lane >= 4) pinc += tmp;
+  tmp = __shfl_up_sync(FULL, pinc, 8); if (lane >= 8) pinc += tmp;
+  tmp = __shfl_up_sync(FULL, pinc, 16); if (lane >= 16) pinc += tmp;
+  const uint32_t ptot = __shfl_sync(FULL, pinc, 31);
+  const int C1 = int(ptot & 0xffffu), C2 = int(ptot >> 16);
+  // Centring changes block 0 only: its cost deltas and rates, from lane 0.
   uint32_t bc = (block_cost(R1c) - block_cost(R1) + 1024u) |
                 ((block_cost(R2c) - block_cost(R2) + 1024u) << 11) | (uint32_t(R1c) << 22) |
                 (uint32_t(R2c) << 27);
   bc = __shfl_sync(FULL, bc, 0);
-  const int C3 = 4 + C1 + int(bc & 0x7ffu) - 1024;
-  const int C4 = 4 + C2 + int((bc >> 11) & 0x7ffu) - 1024;
+  const int dC1 = int(bc & 0x7ffu) - 1024, dC2 = int((bc >> 11) & 0x7ffu) - 1024;
+  // Variants 3 and 4 pay 4 bytes for mu (step 2).
+  const int C3 = 4 + C1 + dC1;
+  const int C4 = 4 + C2 + dC2;
   const int R1c0 = int((bc >> 22) & 31u), R2c0 = int(bc >> 27);
 
   // Step 3, adaptive select: first strict minimum in the order LZ1, LZ2, LZ1c, LZ2c.
@@ -205,19 +215,17 @@ __device__ __forceinline__ uint32_t compress_tile(const float* __restrict__ tile
 #pragma unroll
     for (int i = 0; i < 8; ++i) vv[i] = sign_mag(l1[i]);
   }
-  if (centred && lane == 0) {
-    vv[0] = sign_mag(q0 - mu);
-    if (second) vv[1] = sign_mag(l2[1] + mu);
-  }
+  const bool fix = centred && lane == 0;
+  vv[0] = fix ? sign_mag(q0 - mu) : vv[0];
+  vv[1] = (fix && second) ? sign_mag(l2[1] + mu) : vv[1];
 
-  // Byte offset of block g inside the tile's data (after mu when centred).
-  const int Sg = int(block_cost(Rg));
-  int inc = Sg, tmp;
-  tmp = __shfl_up_sync(FULL, inc, 4); if (lane >= 4) inc += tmp;
-  tmp = __shfl_up_sync(FULL, inc, 8); if (lane >= 8) inc += tmp;
-  tmp = __shfl_up_sync(FULL, inc, 16); if (lane >= 16) inc += tmp;
-  uint8_t* blk = slot + (centred ? 4 : 0) + (inc - Sg);
-  if (centred && lane == 0) *reinterpret_cast<float*>(slot) = __int2float_rn(mu);
+  // Byte offset of block g inside the tile's data: the variant's exclusive prefix; when
+  // centred, mu's 4 bytes come first and block 0's cost changes by its delta.
+  const uint32_t pexc = pinc - pk;
+  int off = int(second ? (pexc >> 16) : (pexc & 0xffffu));
+  if (centred) off += 4 + (g > 0 ? (second ? dC2 : dC1) : 0);
+  uint8_t* blk = slot + off;
+  if (fix) *reinterpret_cast<float*>(slot) = __int2float_rn(mu);
 
   const int Rmax = int(__reduce_max_sync(FULL, uint32_t(Rg)));
   if (Rmax > 0) {
@@ -299,8 +307,7 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
                  (lc + 1 == fi->nchunks ? kInfoLast : 0u) | (lc == 0 ? kInfoFirst : 0u) |
                  (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
     };
-    fetch(S.pre[0]);
-    fetch(S.pre[1]);
+    for (int k = 0; k < kTicketAhead; ++k) fetch(S.pre[k]);
     uint32_t u = 0;  // stage uses so far
     auto take_stage = [&](uint32_t seq, uint32_t h) -> int {
       const int s = int(u % kStages);
@@ -319,7 +326,8 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
         set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
         return;
       }
-      ChunkInfo& q = S.pre[seq & 1];
+      ChunkInfo& q = S.pre[kTicketAhead ? seq % kTicketAhead : 0];
+      if (kTicketAhead == 0) fetch(q);
       S.meta[b] = q;
       if (q.chunk >= total) {
         S.meta[b].chunk = kNone;
@@ -338,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
         mbar_arrive_expect_tx(&S.full[s], bulk);
         if (bulk) tma_load_1d(S.in[s], q.in + e_h, bulk, &S.full[s]);
       }
-      fetch(q);  // the ticket two chunks ahead
+      if (kTicketAhead > 0) fetch(q);  // the ticket kTicketAhead chunks ahead
     }
   }
 
@@ -393,8 +401,9 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
       } else {
         uint8_t* base = ci.out + ci.data_base + excl;
         for (int tl = warp; tl < int(ci.ntiles); tl += kComputeWarps) {
-          const uint32_t nw = uint32_t(S.tsize[b][tl]) >> 2;
-          const uint32_t* src = reinterpret_cast<const uint32_t*>(ring + S.roff[b][tl]);
+          const uint32_t ti = S.tinfo[b][tl];
+          const uint32_t nw = (ti & 0xffffu) >> 2;
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(ring + (ti >> 16));
           uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][tl]);
           for (uint32_t q = lane; q < nw; q += 32) dst[q] = src[q];
         }
@@ -458,15 +467,16 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
       const uint32_t cnt = min(ci.cnt - e_h, uint32_t(kStageElems));
       const uint32_t bulk_elems = ((cnt * 4) & ~15u) / 4;
       const float* gin = ci.in + e_h;
-      uint64_t* hdr_out = reinterpret_cast<uint64_t*>(ci.out + 64) + ci.tile0;
+      uint8_t* hdr_out = ci.out + 64 + 8 * ci.tile0;
       const int t_end = min(ntiles, int(h + 1) * kStageTiles);
+      const bool ragged = cnt < uint32_t(kStageElems);
       for (int tl = int(h) * kStageTiles + warp; tl < t_end; tl += kComputeWarps) {
         const int ts = tl - int(h) * kStageTiles;  // tile within the stage
         float* tile = S.in[s] + ts * kTile;
         // Ragged end of a field: this lane's elements past the last 16-byte boundary of
         // the bulk copy by plain loads; padding elements are zeros (they quantize to 0).
         const uint32_t k0 = uint32_t(ts) * kTile + 8u * uint32_t(lane);
-        if (k0 + 8 > bulk_elems) {
+        if (ragged && k0 + 8 > bulk_elems) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const uint32_t k = k0 + uint32_t(i);
@@ -489,15 +499,9 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
         if (!ok_run) break;
         head += skip;
         pos = head % kRingBytes;
-        const uint32_t nb = compress_tile(tile, ring + pos, reinterpret_cast<uint8_t*>(&S.hdr[warp]), r, lane);
-        __syncwarp();
-        if (lane == 0) {
-          S.tsize[b][tl] = uint16_t(nb);
-          S.roff[b][tl] = uint16_t(pos);
-          hdr_out[tl] = S.hdr[warp];
-        }
+        const uint32_t nb = compress_tile(tile, ring + pos, hdr_out + 8 * tl, r, lane);
+        if (lane == 0) S.tinfo[b][tl] = (pos << 16) | nb;
         head += nb;
-        __syncwarp();
       }
       if (!ok_run) break;
     }
@@ -517,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
       __syncwarp();
       if (last) {
         if (!end) {
-          const uint32_t mine = ((flags & kInfoOk) && lane < ntiles) ? uint32_t(S.tsize[b][lane]) : 0u;
+          const uint32_t mine = ((flags & kInfoOk) && lane < ntiles) ? (S.tinfo[b][lane] & 0xffffu) : 0u;
           uint32_t inc = mine;
 #pragma unroll
           for (int o = 1; o < 32; o <<= 1) {

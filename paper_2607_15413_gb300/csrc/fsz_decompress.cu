@@ -1,12 +1,15 @@
 // FSZ decompression kernel (Sec. 3.1 "Decompression", steps d1-d5).
 //
 // Persistent, warp-specialised CTAs; the roles hand chunks to one another through
-// mbarriers, kStages chunks deep:
+// mbarriers:
 //   header warp   takes a ticket, d1 reads the chunk's rate header, d2 derives the tile
-//                 sizes and scans them, and publishes the chunk's aggregate flag at once;
-//   loader warp   d3 looks back for the chunk's byte offset (decoupled lookback), publishes
-//                 the inclusive prefix and loads the chunk's payload into shared memory
-//                 with a 1-D TMA bulk copy;
+//                 sizes and scans them, publishes the chunk's aggregate flag at once and
+//                 leaves the chunk's record (headers, offsets, field parameters) in a ring
+//                 of kRecs records, running ahead of decoding;
+//   loader warp   d3 looks back for the chunk's byte offset (decoupled lookback) as soon
+//                 as the record is in, publishes the inclusive prefix, then waits for a
+//                 free payload stage and loads the chunk's payload into it with a 1-D TMA
+//                 bulk copy (the lookback thus overlaps the decoding of earlier chunks);
 //   decode warps  (8) d4 bit-unshuffle one tile at a time (lane j owns elements 8j..8j+7),
 //                 d5 invert the prediction as warp-wide prefix sums (once for LZ1, twice
 //                 for LZ2), add mu, d' = fl(float(q) s), and store the tile with a 1-D TMA
@@ -21,36 +24,44 @@ constexpr int kDecodeWarps = 8;
 constexpr int kHeaderWarp = kDecodeWarps;
 constexpr int kLoaderWarp = kDecodeWarps + 1;
 constexpr int kThreads = (kDecodeWarps + 2) * 32;
-constexpr int kStages = 3;
+constexpr int kStages = 3;   // payload stages
+constexpr int kRecs = 6;     // chunk records in flight (fetched .. decoded)
 constexpr int kPayloadBytes = kDChunkTiles * kMaxDecTileBytes + 32;
 static_assert(kDChunkTiles <= 32, "one lane per tile in the chunk scan");
 static_assert(kPayloadBytes % 16 == 0, "stage size");
 constexpr uint32_t kNoneChunk = 0xffffffffu;
 constexpr int kLookbackPerLane = 4;  // 128-flag lookback window
 
-// A chunk's header and parameters, handed from the header warp to the loader and the
-// decode warps through shared memory (keeps dependent global loads off the decode path).
-struct StageInfo {
+// A chunk's header and parameters, from the header warp to the loader and the decode
+// warps through shared memory (keeps dependent global loads off the decode path).
+struct ChunkRec {
   uint64_t hdr[kDChunkTiles];
+  uint64_t boff[kDChunkTiles];  // block word offsets of each tile (block_word_offsets)
   uint32_t toff[kDChunkTiles];
   FieldInfo* fi;
-  float* dout;     // the chunk's first output element
-  uint32_t chunk;  // ticket held by the stage
-  uint32_t tot;    // payload bytes of the chunk
-  uint32_t bad;    // reserved header bits seen
-  uint32_t valid;  // payload loaded and decodable
-  uint32_t shift;  // payload start inside the stage
+  float* dout;           // the chunk's first output element
+  const uint8_t* sin;    // the field's stream
+  uint64_t in_bytes;     // its size
+  uint64_t data_bytes;   // tile data bytes the preamble declares
+  uint64_t data_base;    // 64 + 8T: start of the tile data
+  uint64_t excl;         // byte offset of the chunk's payload in the tile data
+  uint32_t chunk;        // ticket, or kNoneChunk
+  uint32_t lc;           // chunk index inside the field
+  uint32_t last;         // the field's last chunk
+  uint32_t tot;          // payload bytes of the chunk
+  uint32_t bad;          // reserved header bits seen
+  uint32_t valid;        // payload loaded and decodable
+  uint32_t shift;        // payload start inside the stage
   uint32_t ntiles;
-  uint32_t cnt;    // valid elements of the chunk
+  uint32_t cnt;          // valid elements of the chunk
   float step;
 };
 
 struct __align__(16) DecompressSmem {
   uint8_t payload[kStages][kPayloadBytes];
   float out[kDecodeWarps][2][kTile];  // per-warp double buffer for the TMA stores
-  StageInfo st[kStages];
-  StageInfo pre[2];                   // the header warp's tickets taken ahead
-  uint64_t hready[kStages], full[kStages], empty[kStages];
+  ChunkRec rec[kRecs];
+  uint64_t fetched[kRecs], recfree[kRecs], full[kStages], empty[kStages];
 };
 
 // Bytes of a tile from its 8 header bytes: sum of S_b (Eq. 3) + 4 for a centred tile.
@@ -62,12 +73,21 @@ __device__ __forceinline__ uint32_t tile_bytes_from_header(uint64_t h) {
   return 4u * words + ((h & 0x40u) ? 4u : 0u);
 }
 
+// Word offsets of the 8 blocks inside the tile's data (after mu), one per byte: the
+// exclusive byte-wise prefix sum of the blocks' word counts (rate + 1, or 0; <= 224).
+__device__ __forceinline__ uint64_t block_word_offsets(uint64_t h) {
+  const uint64_t R = h & 0x1F1F1F1F1F1F1F1FULL;
+  const uint64_t W = R + (((R + 0x7F7F7F7F7F7F7F7FULL) & 0x8080808080808080ULL) >> 7);
+  return (W * 0x0101010101010101ULL) << 8;
+}
+
 __device__ __forceinline__ bool header_reserved_bits_set(uint64_t h) {
   return (h & 0x20u) || (h & 0xE0E0E0E0E0E0E000ULL);
 }
 
 // Decodes one tile with one warp; returns false if the tile's mean slot is malformed.
-__device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint8_t* __restrict__ tp,
+__device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t boff,
+                                                const uint8_t* __restrict__ tp,
                                                 float* __restrict__ out, const float s,
                                                 const int lane) {
   constexpr uint32_t FULL = 0xffffffffu;
@@ -75,10 +95,7 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint8_t*
   const bool second = (h & 0x80u) != 0, centred = (h & 0x40u) != 0;
   const int Rg = int((h >> (8 * g)) & 31u);
   // d2: words per block (rate + 1, or 0) and block offsets by a byte-wise prefix sum.
-  const uint64_t R = h & 0x1F1F1F1F1F1F1F1FULL;
-  const uint64_t W = R + (((R + 0x7F7F7F7F7F7F7F7FULL) & 0x8080808080808080ULL) >> 7);
-  const uint64_t P = W * 0x0101010101010101ULL;
-  const int offw = g ? int((P >> (8 * (g - 1))) & 0xFFu) : 0;
+  const int offw = int((boff >> (8 * g)) & 0xFFu);
   const uint8_t* blk = tp + (centred ? 4 : 0) + 4 * offw;
 
   bool good = true;
@@ -163,8 +180,11 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
   const uint64_t wait_ns = 4 * a.timeout_ns;
 
   if (tid == 0) {
+    for (int k = 0; k < kRecs; ++k) {
+      mbar_init(&S.fetched[k], 1);
+      mbar_init(&S.recfree[k], kDecodeWarps);
+    }
     for (int k = 0; k < kStages; ++k) {
-      mbar_init(&S.hready[k], 1);
       mbar_init(&S.full[k], 1);
       mbar_init(&S.empty[k], kDecodeWarps);
     }
@@ -174,24 +194,37 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
 
   if (warp == kHeaderWarp) {
     // ---------------------------------------------------------------- header warp
-    // Tickets are taken two chunks ahead: d1-d2 and the chunk's aggregate flag happen at
-    // once, so successors find the aggregate early; a freed stage is refilled from there.
     const bool single = a.ctrl->nfields == 1;
-    auto fetch = [&](StageInfo& q) {
+    for (uint32_t seq = 0;; ++seq) {
+      const int r = int(seq % kRecs);
+      if (seq >= uint32_t(kRecs) && !mbar_wait(&S.recfree[r], ((seq / kRecs) - 1) & 1u, wait_ns)) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      ChunkRec& q = S.rec[r];
       uint32_t c = 0;
       if (lane == 0) c = atomicAdd(&a.ctrl->ticket, 1u);
       c = __shfl_sync(FULL, c, 0);
       if (c >= total) {
-        if (lane == 0) q.chunk = kNoneChunk;
+        if (lane == 0) {
+          q.chunk = kNoneChunk;
+          mbar_arrive(&S.fetched[r]);
+        }
         return;
       }
       FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
-      const uint64_t lc = c - fi->chunk_first;
+      const uint64_t first = fi->chunk_first;
+      const uint64_t lc = c - first;
+      const uint64_t T = fi->T;
       const uint64_t tile0 = lc * kDChunkTiles;
-      const int ntiles = int(min(uint64_t(kDChunkTiles), fi->T - tile0));
+      const int ntiles = int(min(uint64_t(kDChunkTiles), T - tile0));
+      const uint8_t* sin = fi->sin;
       uint64_t hb = 0;
-      if (lane < ntiles) hb = __ldg(reinterpret_cast<const unsigned long long*>(fi->sin + 64) + tile0 + lane);
-      if (lane < kDChunkTiles) q.hdr[lane] = hb;
+      if (lane < ntiles) hb = __ldg(reinterpret_cast<const unsigned long long*>(sin + 64) + tile0 + lane);
+      if (lane < kDChunkTiles) {
+        q.hdr[lane] = hb;
+        q.boff[lane] = block_word_offsets(hb);
+      }
       const bool bad_hdr = __any_sync(FULL, lane < ntiles && header_reserved_bits_set(hb));
       const uint32_t mine = lane < ntiles ? tile_bytes_from_header(hb) : 0u;
       uint32_t inc = mine;
@@ -203,87 +236,75 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
       if (lane < kDChunkTiles) q.toff[lane] = inc - mine;
       const uint32_t tot = __shfl_sync(FULL, inc, 31);
       if (lane == 0) {
+        if (uint64_t(c) != a.skip_chunk) st_flag(a.flags + c, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
         q.chunk = c;
+        q.lc = uint32_t(lc);
+        q.last = (lc + 1 == fi->nchunks) ? 1u : 0u;
         q.tot = tot;
         q.bad = bad_hdr ? 1u : 0u;
         q.fi = fi;
+        q.sin = sin;
+        q.in_bytes = fi->in_bytes;
+        q.data_bytes = fi->data_bytes;
+        q.data_base = 64 + 8 * T;
         q.dout = fi->dout + tile0 * kTile;
         q.ntiles = uint32_t(ntiles);
         q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kDChunkElems)));
         q.step = fi->s;
-        if (uint64_t(c) != a.skip_chunk) st_flag(a.flags + c, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
       }
-    };
-    fetch(S.pre[0]);
-    fetch(S.pre[1]);
-    __syncwarp();
-    for (uint32_t j = 0;; ++j) {
-      const int p = int(j % kStages);
-      if (j >= uint32_t(kStages) && !mbar_wait(&S.empty[p], ((j / kStages) - 1) & 1u, wait_ns)) {
-        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-        return;
-      }
-      StageInfo& q = S.pre[j & 1];
-      StageInfo& st = S.st[p];
-      // hand the prefetched chunk to the loader (32 lanes copy the record)
-      constexpr int kWords = int(sizeof(StageInfo) / 4);
-      static_assert(sizeof(StageInfo) % 4 == 0, "StageInfo copy");
-      for (int w = lane; w < kWords; w += 32)
-        reinterpret_cast<uint32_t*>(&st)[w] = reinterpret_cast<const uint32_t*>(&q)[w];
-      __threadfence_block();
       __syncwarp();
-      const bool none = st.chunk == kNoneChunk;
-      if (lane == 0) mbar_arrive(&S.hready[p]);
-      if (none) return;
-      fetch(q);  // the ticket two chunks ahead
-      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.fetched[r]);
     }
   }
 
   if (warp == kLoaderWarp) {
     // ---------------------------------------------------------------- loader warp
-    for (uint32_t j = 0;; ++j) {
-      const int p = int(j % kStages);
-      if (!mbar_wait(&S.hready[p], (j / kStages) & 1u, wait_ns)) {
+    for (uint32_t seq = 0;; ++seq) {
+      const int r = int(seq % kRecs), p = int(seq % kStages);
+      if (!mbar_wait(&S.fetched[r], (seq / kRecs) & 1u, wait_ns)) {
         if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
         return;
       }
-      StageInfo& st = S.st[p];
-      const uint32_t c = st.chunk;
-      if (c == kNoneChunk) {
-        if (lane == 0) mbar_arrive(&S.full[p]);
-        return;
-      }
-      FieldInfo* fi = st.fi;
-      const uint64_t lc = c - fi->chunk_first;
-      const uint32_t tot = st.tot;
-      const bool skip = (uint64_t(c) == a.skip_chunk);
+      ChunkRec& q = S.rec[r];
+      const uint32_t c = q.chunk;
+      const bool none = c == kNoneChunk;
+      FieldInfo* fi = q.fi;
+      const uint32_t tot = q.tot;
+      const bool skip = !none && uint64_t(c) == a.skip_chunk;
       uint64_t excl = 0;
-      if (lc != 0) {
+      if (!none && q.lc != 0) {
         bool to = false;
-        excl = lookback<kLookbackPerLane>(a.flags, int64_t(c), int64_t(fi->chunk_first), globaltimer_ns() + a.timeout_ns,
-                        &to);
+        excl = lookback<kLookbackPerLane>(a.flags, int64_t(c), int64_t(c) - int64_t(q.lc),
+                                          globaltimer_ns() + a.timeout_ns, &to);
         if (lane == 0) {
           if (to) set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
           if (!skip) st_flag(a.flags + c, kFlagIncl | (excl + tot));
         }
       }
-      const uint64_t data_base = 64 + 8 * fi->T;
-      bool valid = st.bad == 0 && !skip;
-      if (data_base + excl + tot > fi->in_bytes) valid = false;
-      if (lc + 1 == fi->nchunks && excl + tot != fi->data_bytes) valid = false;
-      const uint64_t src = reinterpret_cast<uint64_t>(fi->sin) + data_base + excl;
+      // The payload stage frees once the decode warps are through chunk seq - kStages.
+      if (seq >= uint32_t(kStages) && !mbar_wait(&S.empty[p], ((seq / kStages) - 1) & 1u, wait_ns)) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      if (none) {
+        if (lane == 0) mbar_arrive(&S.full[p]);
+        return;
+      }
+      bool valid = q.bad == 0 && !skip;
+      if (q.data_base + excl + tot > q.in_bytes) valid = false;
+      if (q.last && excl + tot != q.data_bytes) valid = false;
+      const uint64_t base = reinterpret_cast<uint64_t>(q.sin);
+      const uint64_t src = base + q.data_base + excl;
       const uint64_t a0 = src & ~uint64_t(15);
       // Round the copy's end up to 16 bytes while that stays inside the stream buffer;
       // otherwise the last few bytes come by plain loads.
       const uint64_t end_up = (src + tot + 15) & ~uint64_t(15);
-      const uint64_t a1 = end_up <= reinterpret_cast<uint64_t>(fi->sin) + fi->in_bytes
-                              ? end_up : ((src + tot) & ~uint64_t(15));
+      const uint64_t a1 = end_up <= base + q.in_bytes ? end_up : ((src + tot) & ~uint64_t(15));
       const uint32_t bulk = (valid && a1 > a0) ? uint32_t(a1 - a0) : 0u;
       if (lane == 0) {
         if (!valid && !skip) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
-        st.shift = uint32_t(src - a0);
-        st.valid = valid ? 1u : 0u;
+        q.shift = uint32_t(src - a0);
+        q.valid = valid ? 1u : 0u;
         if (bulk) {
           fence_proxy_async();
           mbar_expect_tx(&S.full[p], bulk);
@@ -306,13 +327,13 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
   // ------------------------------------------------------------------ decode warps
   uint32_t nstore = 0;
   bool good = true;
-  for (uint32_t j = 0;; ++j) {
-    const int p = int(j % kStages);
-    if (!mbar_wait(&S.full[p], (j / kStages) & 1u, wait_ns)) {
+  for (uint32_t seq = 0;; ++seq) {
+    const int r = int(seq % kRecs), p = int(seq % kStages);
+    if (!mbar_wait(&S.full[p], (seq / kStages) & 1u, wait_ns)) {
       if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
       break;
     }
-    const StageInfo& st = S.st[p];
+    const ChunkRec& st = S.rec[r];
     const uint32_t c = st.chunk;
     if (c == kNoneChunk) break;
     FieldInfo* fi = st.fi;
@@ -326,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
         float* buf = S.out[warp][nstore & 1u];
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         __syncwarp();
-        good &= decompress_tile(st.hdr[tl], pay + st.toff[tl], buf, step, lane);
+        good &= decompress_tile(st.hdr[tl], st.boff[tl], pay + st.toff[tl], buf, step, lane);
         fence_proxy_async();
         __syncwarp();
         const uint32_t k0 = uint32_t(tl) * kTile;
@@ -343,7 +364,10 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs 
     if (!good && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
     good = true;
     __syncwarp();
-    if (lane == 0) mbar_arrive(&S.empty[p]);
+    if (lane == 0) {
+      mbar_arrive(&S.empty[p]);
+      mbar_arrive(&S.recfree[r]);
+    }
   }
   if (lane == 0) tma_store_wait_all();
 }

@@ -121,6 +121,13 @@ def barrier(world: int):
         dist.barrier()
 
 
+def job_throughput(world: int, bytes_per_rank: float, ms_local: float) -> tuple[float, float]:
+    """Whole-job GB/s: every rank processes `bytes_per_rank` per step (weak scaling) and the
+    job takes as long as its slowest rank. Returns (GB/s, max ms over ranks)."""
+    ms = all_max(ms_local, world)
+    return world * bytes_per_rank / (ms * 1e-3) / 1e9, ms
+
+
 CPU_SAMPLE_SHAPE = (384, 512, 512)  # 3 x 2^25 elements per field: about 10-30 s of oracle work
 
 
@@ -504,9 +511,8 @@ def main():
             comp_ms[j].append(ev[j][0].elapsed_time(ev[j][2]))
             dec_ms[j].append(evd[j][0].elapsed_time(evd[j][1]))
     total_ms = t_start.elapsed_time(t_end)
-    ms_step = all_max(total_ms / args.steps, world)
     bytes_step = 2 * len(jobs) * 4 * n
-    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+    value, ms_step = job_throughput(world, bytes_step, total_ms / args.steps)
 
     # e2e: the same calls with pinned host buffers
     e2e = None
@@ -557,8 +563,8 @@ def main():
         for _ in range(ksteps):
             h2d, d2h = e2e_step()
         torch.cuda.synchronize(dev)
-        e2e_ms = all_max((time.perf_counter() - t0) * 1e3 / ksteps, world)
-        e2e = {"value": world * bytes_step / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+        e2e_gbs, e2e_ms = job_throughput(world, bytes_step, (time.perf_counter() - t0) * 1e3 / ksteps)
+        e2e = {"value": e2e_gbs, "unit": "GB/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
         del hin, hstream, din
 
@@ -590,7 +596,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "peak_kind": peak_kind,
                 "frac_of_nominal_8tbs": achieved / NOMINAL_HBM_GBS, "traffic": traffic,
-                "traffic_note": "dram read+write bytes of one captured launch (512^3 GRF, REL 1e-3; "
+                "traffic_note": "mean dram read+write bytes per launch over the 6 jobs of one step (one ncu capture; "
                                 "profiles/traffic.json), null once the kernel source changed",
                 "algorithmic_bytes_per_launch": algo / (args.steps * len(jobs))}
 

@@ -47,6 +47,23 @@ class FszDField(ctypes.Structure):
                 ("out_capacity_elems", ctypes.c_uint64)]
 
 
+# numpy views of the same layouts, for filling many descriptors at once
+def _np_dtypes():
+    import numpy as np
+    cf = np.dtype({"names": ["in_", "ndim", "dreserved", "d0", "d1", "d2", "mode", "reserved", "eb",
+                             "out", "out_capacity", "out_bytes"],
+                   "formats": ["<u8", "<u4", "<u4", "<u8", "<u8", "<u8", "<u4", "<u4", "<f8", "<u8",
+                               "<u8", "<u8"],
+                   "offsets": [0, 8, 12, 16, 24, 32, 40, 44, 48, 56, 64, 72], "itemsize": 80})
+    df = np.dtype({"names": ["in_", "in_bytes", "out", "out_capacity_elems"],
+                   "formats": ["<u8", "<u8", "<u8", "<u8"], "offsets": [0, 8, 16, 24], "itemsize": 32})
+    assert cf.itemsize == ctypes.sizeof(FszCField) and df.itemsize == ctypes.sizeof(FszDField)
+    return cf, df
+
+
+CFIELD_NP, DFIELD_NP = _np_dtypes()
+
+
 class FszError(RuntimeError):
     def __init__(self, status: int, where: str):
         super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")

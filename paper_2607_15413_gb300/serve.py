@@ -93,48 +93,57 @@ class GpuBackend:
         return _align16(4 * max(req.n, 4))
 
     def launch(self, slot: int, kind: str, reqs):
+        """One batched call for `reqs` on stream slot `slot`. Outputs are views of one
+        arena per batch; the descriptor table is filled column-wise in pinned memory."""
+        import numpy as np
         torch, fsz = self.torch, self.fsz
         st = self.streams[slot]
         k = len(reqs)
         with torch.cuda.stream(st):
-            keep = []
             if kind == COMPRESS:
-                table = (fsz.FszCField * k).from_address(self.h_table[slot].data_ptr())
-                sizes = self.d_sizes[slot]
-                n_total = 0
-                for i, r in enumerate(reqs):
-                    n = r.data.numel()
-                    n_total += n
-                    cap = _align16(fsz.fsz_compress_bound(n))
-                    out = torch.empty(cap, dtype=torch.uint8, device=self.device)
-                    keep.append(out)
-                    table[i].in_ = r.data.data_ptr() if n else 0
-                    table[i].dims = fsz.make_dims(r.shape)
-                    table[i].mode, table[i].reserved, table[i].eb = int(r.mode), 0, float(r.eb)
-                    table[i].out, table[i].out_capacity = out.data_ptr(), cap
-                    table[i].out_bytes = sizes.data_ptr() + 8 * i
-                nb = k * ctypes.sizeof(fsz.FszCField)
+                caps = np.fromiter((r.cost - 16 for r in reqs), dtype=np.uint64, count=k)
+                offs = np.zeros(k, dtype=np.uint64)
+                np.cumsum(caps[:-1], out=offs[1:])
+                arena = torch.empty(int(caps.sum()), dtype=torch.uint8, device=self.device)
+                tab = self.h_table[slot].numpy()[: k * fsz.CFIELD_NP.itemsize].view(fsz.CFIELD_NP)
+                tab["in_"] = [r.data.data_ptr() if r.data.numel() else 0 for r in reqs]
+                dims = [tuple(int(x) for x in r.shape) + (0, 0, 0) for r in reqs]
+                tab["ndim"] = [len(r.shape) for r in reqs]
+                tab["dreserved"] = 0
+                tab["d0"] = [d[0] for d in dims]
+                tab["d1"] = [d[1] for d in dims]
+                tab["d2"] = [d[2] for d in dims]
+                tab["mode"] = [int(r.mode) for r in reqs]
+                tab["reserved"] = 0
+                tab["eb"] = [float(r.eb) for r in reqs]
+                tab["out"] = np.uint64(arena.data_ptr()) + offs
+                tab["out_capacity"] = caps
+                tab["out_bytes"] = np.uint64(self.d_sizes[slot].data_ptr()) + 8 * np.arange(k, dtype=np.uint64)
+                n_total = sum(r.data.numel() for r in reqs)
+                nb = k * fsz.CFIELD_NP.itemsize
                 self.d_table[slot][:nb].copy_(self.h_table[slot][:nb], non_blocking=True)
                 code = fsz.fsz_compress_batched(self.d_table[slot].data_ptr(), k, n_total,
                                                 self.ws[slot].data_ptr(), self.ws_bytes,
                                                 st.cuda_stream)
-                self.h_sizes[slot][:k].copy_(sizes[:k], non_blocking=True)
+                self.h_sizes[slot][:k].copy_(self.d_sizes[slot][:k], non_blocking=True)
+                keep = (arena, offs.tolist())
             else:
-                table = (fsz.FszDField * k).from_address(self.h_table[slot].data_ptr())
-                cap_total = 0
-                for i, r in enumerate(reqs):
-                    cap = _align16(4 * max(r.n, 4)) // 4
-                    cap_total += cap
-                    out = torch.empty(cap, dtype=torch.float32, device=self.device)
-                    src = r.data if r.data.data_ptr() % 16 == 0 else r.data.clone()
-                    keep.append((out, src))
-                    table[i].in_, table[i].in_bytes = src.data_ptr(), src.numel()
-                    table[i].out, table[i].out_capacity_elems = out.data_ptr(), cap
-                nb = k * ctypes.sizeof(fsz.FszDField)
+                caps = np.fromiter((_align16(4 * max(r.n, 4)) // 4 for r in reqs), dtype=np.uint64, count=k)
+                offs = np.zeros(k, dtype=np.uint64)
+                np.cumsum(caps[:-1], out=offs[1:])
+                arena = torch.empty(int(caps.sum()), dtype=torch.float32, device=self.device)
+                srcs = [r.data if r.data.data_ptr() % 16 == 0 else r.data.clone() for r in reqs]
+                tab = self.h_table[slot].numpy()[: k * fsz.DFIELD_NP.itemsize].view(fsz.DFIELD_NP)
+                tab["in_"] = [x.data_ptr() for x in srcs]
+                tab["in_bytes"] = [x.numel() for x in srcs]
+                tab["out"] = np.uint64(arena.data_ptr()) + 4 * offs
+                tab["out_capacity_elems"] = caps
+                nb = k * fsz.DFIELD_NP.itemsize
                 self.d_table[slot][:nb].copy_(self.h_table[slot][:nb], non_blocking=True)
-                code = fsz.fsz_decompress_batched(self.d_table[slot].data_ptr(), k, cap_total,
+                code = fsz.fsz_decompress_batched(self.d_table[slot].data_ptr(), k, int(caps.sum()),
                                                   self.ws[slot].data_ptr(), self.ws_bytes,
                                                   st.cuda_stream)
+                keep = (arena, offs.tolist(), srcs)
             ev = torch.cuda.Event()
             ev.record(st)
         return {"event": ev, "code": code, "keep": keep, "kind": kind, "slot": slot}
@@ -148,14 +157,18 @@ class GpuBackend:
         per = (ctypes.c_uint32 * len(reqs))()
         first = fsz.fsz_check_batched(self.ws[slot].data_ptr(), len(reqs), per,
                                       self.streams[slot].cuda_stream)
+        arena, offs = h["keep"][0], h["keep"][1]
         out = []
+        if h["kind"] == COMPRESS:
+            sizes = self.h_sizes[slot][: len(reqs)].tolist()
         for i, r in enumerate(reqs):
             status = h["code"] if h["code"] else (int(per[i]) if first != fsz.ERR_CUDA else first)
+            o = int(offs[i])
             if h["kind"] == COMPRESS:
-                nb = int(self.h_sizes[slot][i])
-                out.append((status, h["keep"][i][:nb], nb))
+                nb = int(sizes[i])
+                out.append((status, arena[o: o + nb], nb))
             else:
-                out.append((status, h["keep"][i][0][: r.n], 0))
+                out.append((status, arena[o: o + r.n], 0))
         return out
 
 

@@ -270,17 +270,19 @@ def run_batched(fsz, inputs, dev, reps: int = 3):
     return out
 
 
-def run_serving(fsz, inputs, dev, nreq: int = 200, seed: int = 4):
-    """Serving workload (bounded): requests of log-uniform 16 KiB-256 MiB cut from a
-    device-resident pool of the batched mix's classes, 60 % compress / 40 % decompress of
-    an earlier result, REL from {1e-2,1e-3,1e-4}, 40 GB admission budget. First the closed
-    loop (all requests at once: the peak), then Poisson arrivals at 25/50/75/100 % of that
-    peak; p50/p99 latency from host arrival to completion, sustained GB/s."""
+def run_serving(fsz, inputs, dev, nreq: int = 20000, seed: int = 4):
+    """Serving workload: requests of log-uniform 16 KiB-256 MiB cut from a device-resident
+    pool of the batched mix's classes, 60 % compress / 40 % decompress of an earlier result
+    (the 64 newest streams), REL from {1e-2,1e-3,1e-4}, 40 GB admission budget, 4 stream
+    slots, batches of up to 32. First the closed loop (all requests at once: the peak),
+    then Poisson arrivals at 25/50/75/100 % of that peak; p50/p99 latency from the
+    scheduled arrival to completion, sustained GB/s. The baseline is the closed loop's first
+    2000 requests issued as one library call each (fsz_compress / fsz_decompress) on one
+    stream."""
     import math
     import random
     import threading
 
-    import numpy as np
     import torch
 
     from paper_2607_15413_gb300 import serve
@@ -292,103 +294,124 @@ def run_serving(fsz, inputs, dev, nreq: int = 200, seed: int = 4):
     del g
     torch.cuda.empty_cache()
     rng = random.Random(seed)
+    lock = threading.Lock()
+    lru = []  # (stream tensor, element count) of the newest successful compressions
 
-    def make_requests():
+    def make_requests(count):
         out = []
-        for _ in range(nreq):
+        for _ in range(count):
             src = pool[rng.randrange(3)]
             n = int(math.exp(rng.uniform(math.log(4096), math.log(64 << 20))))
             n = max(4, min(n, src.numel()) // 4 * 4)
             off = rng.randrange(0, (src.numel() - n) // 4 + 1) * 4
-            out.append((src[off:off + n], rng.choice([1e-2, 1e-3, 1e-4]),
-                        rng.random() < 0.4))
+            out.append((src[off:off + n], rng.choice([1e-2, 1e-3, 1e-4]), rng.random() < 0.4))
         return out
 
     backend = serve.GpuBackend(n_slots=4, max_batch=32, max_elems=10 << 30, device=dev)
 
-    def run(reqs, rate=None):
-        """rate None: closed loop; else Poisson arrivals at `rate` requests/s."""
+    def run(reqs, rate=None, record=None):
+        """rate None: closed loop; else Poisson arrivals at `rate` requests/s. Results are
+        reduced to their status and latency as they complete (outputs are dropped, except
+        the newest compressions kept for later decompress requests)."""
         srv = serve.Server(backend, budget_bytes=40 << 30, n_slots=4, max_batch=32)
-        done_streams = []          # compressed results still resident (for decompress requests)
-        lock = threading.Lock()
-        futs, nbytes = [], 0
+        lat, refused = [], [0]
+        remaining = [len(reqs)]
+        all_done = threading.Event()
+
+        def on_done(f, kind, n):
+            r = f.result()
+            with lock:
+                if r.status == 0:
+                    lat.append(r.latency_s * 1e3)
+                    if kind == serve.COMPRESS:
+                        # a view into its batch's output arena: the 64 newest results come
+                        # from the last few batches, so only their arenas stay resident
+                        lru.append((r.output, n))
+                        if len(lru) > 64:
+                            lru.pop(0)
+                else:
+                    refused[0] += 1
+                remaining[0] -= 1
+                if remaining[0] == 0:
+                    all_done.set()
+
+        nbytes = 0
         t0 = time.perf_counter()
         t_arr = t0
         for x, rel, want_dec in reqs:
             if rate is not None:
                 t_arr += rng.expovariate(rate)
                 delay = t_arr - time.perf_counter()
-                if delay > 0:
+                if delay > 1e-4:
                     time.sleep(delay)
             with lock:
-                prev = done_streams[rng.randrange(len(done_streams))] if (want_dec and done_streams) else None
+                prev = lru[rng.randrange(len(lru))] if (want_dec and lru) else None
+            arrival = t_arr if rate is not None else 0.0
             if prev is not None:
-                req = serve.Request(kind=serve.DECOMPRESS, data=prev[0], n=prev[1],
-                                    arrival=t_arr if rate is not None else 0.0)
+                req = serve.Request(kind=serve.DECOMPRESS, data=prev[0], n=prev[1], arrival=arrival)
+                n = prev[1]
             else:
-                req = serve.Request(kind=serve.COMPRESS, data=x, shape=(x.numel(),), eb=rel, mode=1,
-                                    arrival=t_arr if rate is not None else 0.0)
-
-                def keep(f, n=x.numel()):
-                    r = f.result()
-                    if r.status == 0:
-                        with lock:
-                            done_streams.append((r.output, n))
-                            if len(done_streams) > 64:
-                                done_streams.pop(0)      # LRU: oldest result evicted
-                futs_cb.append((req, keep))
-            nbytes += 4 * (req.n if req.kind == serve.DECOMPRESS else x.numel())
-            f = srv.submit(req)
-            if req.kind == serve.COMPRESS:
-                f.add_done_callback(futs_cb[-1][1])
-            futs.append(f)
-        res = [f.result(timeout=300) for f in futs]
+                n = x.numel()
+                req = serve.Request(kind=serve.COMPRESS, data=x, shape=(n,), eb=rel, mode=1,
+                                    arrival=arrival)
+            if record is not None and len(record) < record_cap:
+                record.append((req.kind, req.data, n, rel))
+            nbytes += 4 * n
+            srv.submit(req).add_done_callback(lambda f, k=req.kind, n=n: on_done(f, k, n))
+        all_done.wait(600)
         wall = time.perf_counter() - t0
         srv.close()
-        lat = [r.latency_s * 1e3 for r in res if r.status == 0]
         return {"gbs": nbytes / wall / 1e9, "p50_ms": serve.percentile(lat, 50),
-                "p99_ms": serve.percentile(lat, 99), "requests": len(res),
-                "refused": sum(1 for r in res if r.status != 0), "bytes": nbytes,
+                "p99_ms": serve.percentile(lat, 99), "requests": len(reqs),
+                "refused": refused[0], "bytes": nbytes, "wall_s": wall,
                 "batches": srv.stats["batches"], "max_inflight": srv.stats["max_inflight"],
                 "admitted_while_busy": srv.stats["admitted_while_busy"]}
 
-    futs_cb = []
-    reqs = make_requests()
-    run(reqs[: nreq // 4])                       # warm-up
-    closed = run(reqs)
-    # one call per request, same requests, one stream (the per-request baseline)
+    run(make_requests(max(64, nreq // 10)))      # warm-up; fills the stream LRU
+    record, record_cap = [], min(nreq, 2000)
+    closed = run(make_requests(nreq), record=record)
+    # the closed loop's requests, one library call each, one stream (the per-request baseline)
     L = fsz.lib()
     sp = torch.cuda.current_stream(dev).cuda_stream
-    nmax = max(x.numel() for x, _, _ in reqs)
+    nmax = max(n for _, _, n, _ in record)
     ws_b = fsz.fsz_workspace_bytes(nmax)
     ws = torch.empty(ws_b, dtype=torch.uint8, device=dev)
     cap = fsz.fsz_compress_bound(nmax)
     out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    dout = torch.empty(nmax + 4, dtype=torch.float32, device=dev)
     nb = torch.zeros(1, dtype=torch.int64, device=dev)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     tot = 0
-    for x, rel, _ in reqs:
-        L.fsz_compress(x.data_ptr(), fsz.make_dims((x.numel(),)), 1, rel, out.data_ptr(), cap,
-                       nb.data_ptr(), ws.data_ptr(), ws_b, sp)
-        tot += 4 * x.numel()
+    for kind, data, n, rel in record:
+        if kind == serve.COMPRESS:
+            L.fsz_compress(data.data_ptr(), fsz.make_dims((n,)), 1, rel, out.data_ptr(), cap,
+                           nb.data_ptr(), ws.data_ptr(), ws_b, sp)
+        else:
+            L.fsz_decompress(data.data_ptr(), data.numel(), dout.data_ptr(), n, ws.data_ptr(), ws_b, sp)
+        tot += 4 * n
     torch.cuda.synchronize(dev)
     per_req_gbs = tot / (time.perf_counter() - t0) / 1e9
+    n_dec = sum(1 for k, _, _, _ in record if k == serve.DECOMPRESS)
+    n_rec = len(record)
+    del record, out, dout, ws
     mean_bytes = closed["bytes"] / closed["requests"]
     levels = []
     for load in (0.25, 0.5, 0.75, 1.0):
         rate = load * closed["gbs"] * 1e9 / mean_bytes
-        r = run(make_requests(), rate=rate)
+        r = run(make_requests(nreq), rate=rate)
         r["load"] = load
         r["offered_gbs"] = load * closed["gbs"]
         levels.append(r)
+    lru.clear()
     del pool
     torch.cuda.empty_cache()
     return {"workload": f"{nreq} requests per level, seed {seed}: log-uniform 16 KiB-256 MiB windows "
                         "of a device pool (k^-3 GRF, particle-like, zero-slab), 60% compress / 40% "
                         "decompress of an earlier result, REL in {1e-2,1e-3,1e-4}, 40 GB budget, "
                         "4 streams, batches of up to 32",
-            "closed_loop": closed, "per_request_compress_gbs": per_req_gbs,
+            "closed_loop": closed, "sample_decompress_share": n_dec / max(1, n_rec),
+            "per_request_gbs": per_req_gbs, "per_request_sample": n_rec,
             "closed_loop_vs_per_request": closed["gbs"] / per_req_gbs, "loads": levels}
 
 
@@ -404,6 +427,8 @@ def main():
                     help="skip the 512-field batched vs per-field comparison")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the continuous-batching serving measurement")
+    ap.add_argument("--serving-requests", type=int, default=20000,
+                    help="requests per serving level (the serving workload has 20,000)")
     ap.add_argument("--fields", default="grf,zero_slabs",
                     help="subset of grf,zero_slabs (smaller cases for profiling)")
     ap.add_argument("--rels", default=",".join(str(r) for r in RELS),
@@ -619,7 +644,7 @@ def main():
         batched = run_batched(fsz, inputs, dev)
     serving = None
     if not args.no_serving:
-        serving = run_serving(fsz, inputs, dev)
+        serving = run_serving(fsz, inputs, dev, nreq=args.serving_requests)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
                 "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,

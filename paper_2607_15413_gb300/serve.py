@@ -10,11 +10,14 @@ scheduler thread owns every GPU call:
   whole budget is rejected at once. A request that does not fit yet waits at the head of
   the queue: later requests do not overtake it, so nothing starves, and since in-flight
   work always completes and returns its memory, nothing deadlocks.
-* Batching: admitted requests of the head's kind (compress or decompress) form one batch
-  of up to `max_batch` requests, launched as one batched C-ABI call on the first free
-  stream slot. With several slots, batches overlap on the device; requests that arrive
-  while batches run are admitted and launched as soon as a slot and budget free up
-  (continuous batching), instead of waiting for the queue to drain.
+* Batching: the head's kind (compress or decompress) picks the batch; it takes up to
+  `max_batch` waiting requests of that kind in arrival order, reaching past requests of
+  the other kind (within a scan window) while holding their memory in reserve, so a
+  skipped request still fits when its own batch goes next. The batch is launched as one
+  batched C-ABI call on the first free stream slot. With several slots, batches overlap
+  on the device; requests that arrive while batches run are admitted and launched as soon
+  as a slot and budget free up (continuous batching), instead of waiting for the queue to
+  drain.
 * Completion: a CUDA event per batch; each request's future receives its result
   (the stream bytes for a compression, the decoded field for a decompression), its status
   and its latency (arrival to completion observed on the host).
@@ -176,8 +179,9 @@ class Server:
     """The scheduler. `submit()` is thread-safe; `close()` drains and stops."""
 
     def __init__(self, backend, budget_bytes: int, n_slots: int = 4, max_batch: int = 64,
-                 poll_s: float = 5e-5):
+                 poll_s: float = 5e-5, scan: int = 0):
         self.backend = backend
+        self.scan = scan or 4 * max_batch  # requests looked at per batch
         self.budget = int(budget_bytes)
         self.free_budget = int(budget_bytes)
         self.n_slots = n_slots
@@ -253,12 +257,21 @@ class Server:
             if head.cost > self.free_budget:
                 break                                  # wait for in-flight work to free memory
             kind = head.kind
-            batch = []
-            while (self._pending and len(batch) < self.max_batch and self._pending[0].kind == kind
-                   and self._pending[0].cost <= self.free_budget):
+            batch, skipped, reserved = [], [], 0
+            for _ in range(min(len(self._pending), self.scan)):
+                if len(batch) == self.max_batch:
+                    break
                 r = self._pending.popleft()
+                if r.kind != kind:
+                    skipped.append(r)       # waits for the next batch, its memory held back
+                    reserved += r.cost
+                    continue
+                if r.cost + reserved > self.free_budget:
+                    skipped.append(r)       # does not fit: nothing later overtakes it
+                    break
                 self.free_budget -= r.cost
                 batch.append(r)
+            self._pending.extendleft(reversed(skipped))
             slot = next(s for s in range(self.n_slots) if s not in self._inflight)
             if self._inflight:
                 self.stats["admitted_while_busy"] += len(batch)

@@ -135,3 +135,44 @@ def test_random_load_never_deadlocks():
     assert len(res) == 200
     assert srv.stats["completed"] + srv.stats["rejected"] == 200
     assert srv.free_budget == srv.budget                  # every admitted byte returned
+
+
+def test_batches_reach_past_the_other_kind():
+    """Alternating kinds still form full batches of each kind, in arrival order per kind."""
+    be = FakeBackend(service_s=0.05)
+    srv = Server(be, budget_bytes=10 ** 9, n_slots=1, max_batch=8)
+    try:
+        first = srv.submit(creq(100))                 # occupies the only slot
+        time.sleep(0.01)
+        fs = [srv.submit(creq(100 + i, COMPRESS if i % 2 else DECOMPRESS)) for i in range(16)]
+        for f in [first] + fs:
+            assert f.result(timeout=10).status == 0
+    finally:
+        srv.close()
+    sizes = [len(seqs) for _, _, _, seqs in be.launches]
+    assert sizes[0] == 1 and sizes[1:] == [8, 8]      # two full batches, one per kind
+    for _, _, _, seqs in be.launches:
+        assert seqs == sorted(seqs)
+
+
+def test_a_skipped_request_keeps_its_memory():
+    """A batch reaches past a request of the other kind only with memory to spare for it:
+    a later request that would fit only by spending the skipped request's memory waits."""
+    def run(z_elems):
+        be = FakeBackend(service_s=0.03)
+        srv = Server(be, budget_bytes=1000, n_slots=1, max_batch=8)
+        try:
+            fs = [srv.submit(creq(100))]                  # a: 400 bytes, takes the only slot
+            time.sleep(0.01)
+            fs.append(srv.submit(creq(50)))               # X: compress, 200
+            fs.append(srv.submit(creq(150, DECOMPRESS)))  # Y: decompress, 600
+            fs.append(srv.submit(creq(z_elems)))          # Z: compress
+            for f in fs:
+                assert f.result(timeout=5).status == 0
+        finally:
+            srv.close()
+        return [seqs for _, _, _, seqs in be.launches]
+    # Z = 200 bytes: X + Z + Y's 600 fit in 1000, so Z joins X's batch ahead of Y
+    assert run(50) == [[0], [1, 3], [2]]
+    # Z = 300 bytes: X + Z would leave less than Y's 600, so Z waits behind Y
+    assert run(75) == [[0], [1], [2], [3]]

@@ -32,7 +32,12 @@ constexpr int kStageTiles = 16;                    // tiles per TMA stage (half 
 constexpr int kStageElems = kStageTiles * kTile;
 constexpr int kStages = 2;                         // TMA input stages
 constexpr int kSets = 8;                           // chunks in flight per CTA
-constexpr int kRingBytes = 4096;                   // encoded-tile ring per compute warp
+#ifndef FSZ_LANE16
+#define FSZ_LANE16 1
+#endif
+// With FSZ_LANE16 a warp encodes two tiles at once (16 elements per lane), two CTAs per SM.
+constexpr int kCtasPerSm = FSZ_LANE16 ? 2 : 3;
+constexpr int kRingBytes = FSZ_LANE16 ? 8192 : 4096;  // encoded-tile ring per compute warp
 #ifndef FSZ_C_LOOKBACK
 #define FSZ_C_LOOKBACK 4
 #endif
@@ -46,6 +51,10 @@ static_assert(kCChunkTiles == 2 * kStageTiles, "a chunk is two stages");
 static_assert(kCChunkTiles <= 32, "one lane per tile in the chunk scan");
 static_assert(kRingBytes >= kMaxTileBytes * (kCChunkTiles / kComputeWarps) + kMaxTileBytes,
               "a ring holds a warp's worst-case share of one chunk, after any wrap");
+static_assert(!FSZ_LANE16 || kRingBytes >= 3 * 2 * kMaxTileBytes,
+              "with only the current chunk's first pair live, a free pair gap exists");
+static_assert((kRingBytes & (kRingBytes - 1)) == 0, "ring counters wrap with the ring");
+static_assert(!FSZ_LANE16 || kStageTiles == 2 * kComputeWarps, "one pair per warp per stage");
 static_assert(kRingBytes <= 65536, "ring offsets are 16-bit");
 static_assert(kMaxTileBytes % 4 == 0, "tiles are 32-bit words");
 
@@ -252,7 +261,167 @@ __device__ __forceinline__ uint32_t compress_tile(const float* __restrict__ tile
   return uint32_t(best);
 }
 
-__global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a) {
+// Compresses two tiles with one warp: lanes 0-15 take one tile and lanes 16-31 the next
+// (half = lane >> 4). Lane hl = lane & 15 owns elements 16 hl..16 hl + 15 of its tile, so
+// lanes 2g, 2g + 1 of a half own block g. The halves run the same steps as compress_tile
+// (same arithmetic, same summation order for mu, same bytes) with half the shuffles per
+// tile. `tile` and `hdr` are this half's; the first half's bytes go to `slot`, the second
+// half's right after them. A half with `live` false computes but stores nothing. Returns
+// this half's byte count (uniform within the half).
+__device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ tile,
+                                                    uint8_t* __restrict__ slot,
+                                                    uint8_t* __restrict__ hdr, const float r,
+                                                    const int lane, const bool live) {
+  constexpr uint32_t FULL = 0xffffffffu;
+  const int hl = lane & 15;
+  const float4* t4 = reinterpret_cast<const float4*>(tile) + 4 * hl;
+  float d[16];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = t4[k];
+    d[4 * k] = v.x; d[4 * k + 1] = v.y; d[4 * k + 2] = v.z; d[4 * k + 3] = v.w;
+  }
+  // Step 1, quantize (Sec. 4.2.2), as in compress_tile.
+  int Y[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) Y[i] = __float_as_int(__fadd_rn(__fmul_rn(d[i], r), kMagic));
+
+  // Tile sum, in compress_tile's order: the 8-element sums of elements 8j..8j+7 (here two
+  // per lane, V0 = j even, V1 = j odd), then the butterfly over j by 16, 8, 4, 2 (lane
+  // xor 8, 4, 2, 1 within the half) and finally by 1 (V0 + V1).
+  float V0 = d[0], V1 = d[8];
+#pragma unroll
+  for (int i = 1; i < 8; ++i) {
+    V0 = __fadd_rn(V0, d[i]);
+    V1 = __fadd_rn(V1, d[8 + i]);
+  }
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    V0 = __fadd_rn(V0, __shfl_xor_sync(FULL, V0, o));
+    V1 = __fadd_rn(V1, __shfl_xor_sync(FULL, V1, o));
+  }
+  const float P = __fadd_rn(V0, V1);
+  const int mu =
+      __float_as_int(__fadd_rn(__fmul_rn(__fmul_rn(P, 0.00390625f), r), kMagic)) - kMagicBits;
+
+  // LZ1 and LZ2 residuals with the state carried across lanes and blocks (Eq. 2).
+  int prevY = __shfl_up_sync(FULL, Y[15], 1, 16);
+  if (hl == 0) prevY = kMagicBits;
+  int l1[16], l2[16];
+  l1[0] = Y[0] - prevY;
+#pragma unroll
+  for (int i = 1; i < 16; ++i) l1[i] = Y[i] - Y[i - 1];
+  int prevL = __shfl_up_sync(FULL, l1[15], 1, 16);
+  if (hl == 0) prevL = 0;
+  l2[0] = l1[0] - prevL;
+#pragma unroll
+  for (int i = 1; i < 16; ++i) l2[i] = l1[i] - l1[i - 1];
+
+  uint32_t rest1 = 0, rest2 = 0;
+#pragma unroll
+  for (int i = 1; i < 16; ++i) rest1 |= uabs32(l1[i]);
+#pragma unroll
+  for (int i = 2; i < 16; ++i) rest2 |= uabs32(l2[i]);
+  const uint32_t o1 = rest1 | uabs32(l1[0]);
+  const uint32_t o2 = rest2 | uabs32(l2[0]) | uabs32(l2[1]);
+  const uint32_t x1 = __shfl_xor_sync(FULL, o1, 1);
+  const uint32_t y1 = __shfl_xor_sync(FULL, o2, 1);
+  const int R1 = 32 - __clz(int(o1 | x1));
+  const int R2 = 32 - __clz(int(o2 | y1));
+
+  // Centred block-0 rates (lane hl = 0), as in compress_tile.
+  const int q0 = Y[0] - kMagicBits;
+  const uint32_t c10 = uabs32(q0 - mu);
+  const uint32_t c21 = uabs32(l2[1] + mu);
+  const int R1c = 32 - __clz(int(rest1 | x1 | c10));
+  const int R2c = 32 - __clz(int(rest2 | y1 | c10 | c21));
+
+  // Block costs (Eq. 3): inclusive scan over the 8 blocks (lanes 2 apart); lane 15 of the
+  // half holds the tile costs.
+  const uint32_t pk = block_cost(R1) | (block_cost(R2) << 16);
+  uint32_t pinc = pk, tmp;
+  tmp = __shfl_up_sync(FULL, pinc, 2, 16); if (hl >= 2) pinc += tmp;
+  tmp = __shfl_up_sync(FULL, pinc, 4, 16); if (hl >= 4) pinc += tmp;
+  tmp = __shfl_up_sync(FULL, pinc, 8, 16); if (hl >= 8) pinc += tmp;
+  const uint32_t ptot = __shfl_sync(FULL, pinc, 15, 16);
+  const int C1 = int(ptot & 0xffffu), C2 = int(ptot >> 16);
+  uint32_t bc = (block_cost(R1c) - block_cost(R1) + 1024u) |
+                ((block_cost(R2c) - block_cost(R2) + 1024u) << 11) | (uint32_t(R1c) << 22) |
+                (uint32_t(R2c) << 27);
+  bc = __shfl_sync(FULL, bc, 0, 16);
+  const int dC1 = int(bc & 0x7ffu) - 1024, dC2 = int((bc >> 11) & 0x7ffu) - 1024;
+  const int C3 = 4 + C1 + dC1;
+  const int C4 = 4 + C2 + dC2;
+  const int R1c0 = int((bc >> 22) & 31u), R2c0 = int(bc >> 27);
+
+  // Step 3: first strict minimum in the order LZ1, LZ2, LZ1c, LZ2c.
+  int v = 0, best = C1;
+  if (C2 < best) { v = 1; best = C2; }
+  if (C3 < best) { v = 2; best = C3; }
+  if (C4 < best) { v = 3; best = C4; }
+  const bool second = (v & 1) != 0, centred = v >= 2;
+
+  const int g = hl >> 1, t2 = hl & 1;
+  int Rg = second ? R2 : R1;
+  if (g == 0 && centred) Rg = second ? R2c0 : R1c0;
+  if (t2 == 0 && live) {
+    uint32_t hb = uint32_t(Rg);
+    if (g == 0) hb |= (second ? 0x80u : 0u) | (centred ? 0x40u : 0u);
+    hdr[g] = uint8_t(hb);
+  }
+
+  // Step 5 (the variant differs between the halves: select, do not branch).
+  uint32_t vv[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) vv[i] = sign_mag(second ? l2[i] : l1[i]);
+  const bool fix = centred && hl == 0;
+  vv[0] = fix ? sign_mag(q0 - mu) : vv[0];
+  vv[1] = (fix && second) ? sign_mag(l2[1] + mu) : vv[1];
+
+  const uint32_t pexc = pinc - pk;
+  int off = int(second ? (pexc >> 16) : (pexc & 0xffffu));
+  if (centred) off += 4 + (g > 0 ? (second ? dC2 : dC1) : 0);
+  const uint32_t size_first = __shfl_sync(FULL, uint32_t(best), 0);
+  uint8_t* const my_slot = slot + (lane >= 16 ? size_first : 0u);
+  uint8_t* const blk = my_slot + off;
+  if (fix && live) *reinterpret_cast<float*>(my_slot) = __int2float_rn(mu);
+
+  const int Rmax = int(__reduce_max_sync(FULL, live ? uint32_t(Rg) : 0u));
+  if (Rmax > 0) {
+    const int nch = (Rmax + 8) >> 3;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      if (c < nch) {
+        const uint32_t sel = uint32_t(c) | (uint32_t(4 + c) << 4);
+        // two 8x8 transposes: elements 0-7 and 8-15 of the lane; byte b = plane 8c + b
+        uint32_t lo0 = __byte_perm(__byte_perm(vv[7], vv[6], sel), __byte_perm(vv[5], vv[4], sel), 0x5410);
+        uint32_t hi0 = __byte_perm(__byte_perm(vv[3], vv[2], sel), __byte_perm(vv[1], vv[0], sel), 0x5410);
+        uint32_t lo1 = __byte_perm(__byte_perm(vv[15], vv[14], sel), __byte_perm(vv[13], vv[12], sel), 0x5410);
+        uint32_t hi1 = __byte_perm(__byte_perm(vv[11], vv[10], sel), __byte_perm(vv[9], vv[8], sel), 0x5410);
+        transpose8x8(lo0, hi0);
+        transpose8x8(lo1, hi1);
+        // Lane t2 = 0 builds the words of planes 8c..8c+3, lane t2 = 1 those of 8c+4..8c+7;
+        // each needs the partner's bytes of those planes.
+        const uint32_t r0 = __shfl_xor_sync(FULL, t2 ? lo0 : hi0, 1);
+        const uint32_t r1 = __shfl_xor_sync(FULL, t2 ? lo1 : hi1, 1);
+        const uint32_t X0 = t2 ? r0 : lo0, X1 = t2 ? r1 : lo1;
+        const uint32_t Y0 = t2 ? hi0 : r0, Y1 = t2 ? hi1 : r1;
+        // word b = [X0.b, X1.b, Y0.b, Y1.b]: elements 0-7, 8-15, 16-23, 24-31
+        const uint32_t u0 = __byte_perm(X0, X1, 0x5140), u1 = __byte_perm(X0, X1, 0x7362);
+        const uint32_t u2 = __byte_perm(Y0, Y1, 0x5140), u3 = __byte_perm(Y0, Y1, 0x7362);
+        const uint32_t w[4] = {__byte_perm(u0, u2, 0x5410), __byte_perm(u0, u2, 0x7632),
+                               __byte_perm(u1, u3, 0x5410), __byte_perm(u1, u3, 0x7632)};
+        const int wb = 8 * c + 4 * t2;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (live && Rg > 0 && wb + b <= Rg) reinterpret_cast<uint32_t*>(blk)[wb + b] = w[b];
+      }
+    }
+  }
+  return uint32_t(best);
+}
+
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   CompressSmem& S = *reinterpret_cast<CompressSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -400,6 +569,17 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
         if (lane == 0) set_error(a.ctrl, ci.fi, FSZ_ERR_CAPACITY);
       } else {
         uint8_t* base = ci.out + ci.data_base + excl;
+#if FSZ_LANE16
+        // the warp's pair of each stage: contiguous in the ring and in the stream
+        const int nt = int(ci.ntiles);
+        for (int t0 = 2 * warp; t0 < nt; t0 += kStageTiles) {
+          const uint32_t ti = S.tinfo[b][t0];
+          const uint32_t nw = ((ti & 0xffffu) + (t0 + 1 < nt ? (S.tinfo[b][t0 + 1] & 0xffffu) : 0u)) >> 2;
+          const uint32_t* src = reinterpret_cast<const uint32_t*>(ring + (ti >> 16));
+          uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][t0]);
+          for (uint32_t q = lane; q < nw; q += 32) dst[q] = src[q];
+        }
+#else
         for (int tl = warp; tl < int(ci.ntiles); tl += kComputeWarps) {
           const uint32_t ti = S.tinfo[b][tl];
           const uint32_t nw = (ti & 0xffffu) >> 2;
@@ -407,6 +587,7 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
           uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][tl]);
           for (uint32_t q = lane; q < nw; q += 32) dst[q] = src[q];
         }
+#endif
         if (warp == 0 && lane == 0 && (ci.flags & kInfoLast)) write_preamble(ci.fi, excl + tot);
       }
     }
@@ -470,6 +651,49 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
       uint8_t* hdr_out = ci.out + 64 + 8 * ci.tile0;
       const int t_end = min(ntiles, int(h + 1) * kStageTiles);
       const bool ragged = cnt < uint32_t(kStageElems);
+#if FSZ_LANE16
+      const int ta = int(h) * kStageTiles + 2 * warp;  // this warp's pair in the stage
+      if (ta < t_end) {
+        const int half = lane >> 4;
+        const bool live = ta + half < t_end;
+        const int tl = live ? ta + half : ta;          // a missing second tile repeats the first
+        const int ts = tl - int(h) * kStageTiles;
+        float* tile = S.in[s] + ts * kTile;
+        // ragged end of a field: this lane's 16 elements past the bulk copy by plain loads
+        const uint32_t k0 = uint32_t(ts) * kTile + 16u * uint32_t(lane & 15);
+        if (ragged && live && k0 + 16 > bulk_elems) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const uint32_t k = k0 + uint32_t(i);
+            if (k >= bulk_elems) tile[16 * (lane & 15) + i] = k < cnt ? gin[k] : 0.0f;
+          }
+        }
+        __syncwarp();
+        // room for a worst-case pair, contiguous in the ring
+        constexpr uint32_t kPair = 2 * kMaxTileBytes;
+        uint32_t pos = head % kRingBytes;
+        uint32_t skip = pos + kPair > uint32_t(kRingBytes) ? kRingBytes - pos : 0u;
+        while (kRingBytes - (head - tail) < skip + kPair) {
+          if (placed == done || !place_oldest()) {  // cannot happen with <= one pair live
+            if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+            ok_run = false;
+            break;
+          }
+          pos = head % kRingBytes;
+          skip = pos + kPair > uint32_t(kRingBytes) ? kRingBytes - pos : 0u;
+        }
+        if (!ok_run) break;
+        head += skip;
+        pos = head % kRingBytes;
+        const uint32_t nb = compress_pair16(tile, ring + pos, hdr_out + 8 * tl, r, lane, live);
+        const uint32_t na = __shfl_sync(0xffffffffu, nb, 0);
+        const uint32_t nbb = __shfl_sync(0xffffffffu, nb, 16);
+        const bool second_live = ta + 1 < t_end;
+        if (lane == 0) S.tinfo[b][ta] = (pos << 16) | na;
+        if (lane == 16 && second_live) S.tinfo[b][ta + 1] = ((pos + na) << 16) | nbb;
+        head += na + (second_live ? nbb : 0u);
+      }
+#else
       for (int tl = int(h) * kStageTiles + warp; tl < t_end; tl += kComputeWarps) {
         const int ts = tl - int(h) * kStageTiles;  // tile within the stage
         float* tile = S.in[s] + ts * kTile;
@@ -503,6 +727,7 @@ __global__ void __launch_bounds__(kThreads, 3) fsz_compress_kernel(KernelArgs a)
         if (lane == 0) S.tinfo[b][tl] = (pos << 16) | nb;
         head += nb;
       }
+#endif
       if (!ok_run) break;
     }
     __syncwarp();

@@ -276,10 +276,20 @@ __device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ ti
   const int hl = lane & 15;
   const float4* t4 = reinterpret_cast<const float4*>(tile) + 4 * hl;
   float d[16];
+  // Load k of lane hl reads chunk (k + hl/2) mod 4 of its 64 bytes, so the 8 lanes of each
+  // 128-bit phase hit 8 different bank groups; two select stages put the chunks in order.
+  const int rot = (hl >> 1) & 3;
+  float4 q[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) q[k] = t4[(k + rot) & 3];
+  float4 u[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) u[c] = (rot & 1) ? q[(c + 3) & 3] : q[c];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) q[c] = (rot & 2) ? u[(c + 2) & 3] : u[c];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float4 v = t4[k];
-    d[4 * k] = v.x; d[4 * k + 1] = v.y; d[4 * k + 2] = v.z; d[4 * k + 3] = v.w;
+    d[4 * k] = q[k].x; d[4 * k + 1] = q[k].y; d[4 * k + 2] = q[k].z; d[4 * k + 3] = q[k].w;
   }
   // Step 1, quantize (Sec. 4.2.2), as in compress_tile.
   int Y[16];

@@ -5,10 +5,11 @@
 //   producer warp  takes a ticket per chunk of kCChunkTiles tiles and stages the chunk
 //                  in shared memory, one half of kStageTiles tiles per 1-D TMA bulk copy;
 //   compute warps  (8) quantize, predict, evaluate the four variants, select and encode
-//                  one tile at a time from registers into the warp's own ring buffer in
-//                  shared memory, and write the tile's rate header (steps 1-3 and 5; the
-//                  tile is read from HBM once). The last warp through a chunk scans its
-//                  tile sizes and publishes the chunk's aggregate flag;
+//                  two tiles at a time (16 elements per lane) from registers into the
+//                  warp's own ring buffer in shared memory, and write the tiles' rate
+//                  headers (steps 1-3 and 5; each tile is read from HBM once). The last
+//                  warp through a chunk scans its tile sizes and publishes the chunk's
+//                  aggregate flag;
 //   resolver warp  looks back for the chunk's exclusive byte offset (step 4, Sec. 4.4)
 //                  and publishes the inclusive prefix;
 //   compute warps  copy their tiles of each resolved chunk from the ring to the stream,
@@ -32,29 +33,17 @@ constexpr int kStageTiles = 16;                    // tiles per TMA stage (half 
 constexpr int kStageElems = kStageTiles * kTile;
 constexpr int kStages = 2;                         // TMA input stages
 constexpr int kSets = 8;                           // chunks in flight per CTA
-#ifndef FSZ_LANE16
-#define FSZ_LANE16 1
-#endif
-// With FSZ_LANE16 a warp encodes two tiles at once (16 elements per lane), two CTAs per SM.
-constexpr int kCtasPerSm = FSZ_LANE16 ? 2 : 3;
-constexpr int kRingBytes = FSZ_LANE16 ? 8192 : 4096;  // encoded-tile ring per compute warp
-#ifndef FSZ_C_LOOKBACK
-#define FSZ_C_LOOKBACK 4
-#endif
-constexpr int kLookbackPerLane = FSZ_C_LOOKBACK;   // lookback window: 32 x this flags
-#ifndef FSZ_TICKET_AHEAD
-#define FSZ_TICKET_AHEAD 2
-#endif
-constexpr int kTicketAhead = FSZ_TICKET_AHEAD;     // chunk tickets taken ahead of use
+constexpr int kCtasPerSm = 2;                      // 96 registers per thread
+constexpr int kRingBytes = 8192;                   // encoded-tile ring per compute warp
+constexpr int kLookbackPerLane = 4;                // lookback window: 128 flags
+constexpr int kTicketAhead = 2;                    // chunk tickets taken ahead of use
 constexpr uint32_t kNone = 0xffffffffu;
 static_assert(kCChunkTiles == 2 * kStageTiles, "a chunk is two stages");
 static_assert(kCChunkTiles <= 32, "one lane per tile in the chunk scan");
-static_assert(kRingBytes >= kMaxTileBytes * (kCChunkTiles / kComputeWarps) + kMaxTileBytes,
-              "a ring holds a warp's worst-case share of one chunk, after any wrap");
-static_assert(!FSZ_LANE16 || kRingBytes >= 3 * 2 * kMaxTileBytes,
+static_assert(kRingBytes >= 3 * 2 * kMaxTileBytes,
               "with only the current chunk's first pair live, a free pair gap exists");
 static_assert((kRingBytes & (kRingBytes - 1)) == 0, "ring counters wrap with the ring");
-static_assert(!FSZ_LANE16 || kStageTiles == 2 * kComputeWarps, "one pair per warp per stage");
+static_assert(kStageTiles == 2 * kComputeWarps, "one pair per warp per stage");
 static_assert(kRingBytes <= 65536, "ring offsets are 16-bit");
 static_assert(kMaxTileBytes % 4 == 0, "tiles are 32-bit words");
 
@@ -86,7 +75,7 @@ struct __align__(16) CompressSmem {
   float in[kStages][kStageElems];                 // TMA stages
   uint8_t ring[kComputeWarps][kRingBytes];        // encoded tiles awaiting their offset
   ChunkInfo meta[kSets];
-  ChunkInfo pre[kTicketAhead > 0 ? kTicketAhead : 1];  // producer's tickets taken ahead
+  ChunkInfo pre[kTicketAhead];                    // producer's tickets taken ahead
   uint64_t set_excl[kSets];
   uint32_t toff[kSets][kCChunkTiles];             // tile offsets inside the chunk
   uint32_t ring_mark[kComputeWarps][kSets];       // ring head after the warp's share
@@ -103,175 +92,17 @@ __device__ __forceinline__ uint32_t block_cost(int R) { return (uint32_t(R) + (R
 // v = 2|l| + sign: bit 0 is the sign-map bit, bit k + 1 magnitude bit-plane k (Sec. 4.3).
 __device__ __forceinline__ uint32_t sign_mag(int l) { return (uabs32(l) << 1) | (uint32_t(l) >> 31); }
 
-// Compresses the 256-element tile at `tile` (shared memory) with one warp. Lane j owns
-// elements 8j..8j+7; the 4 lanes 4g..4g+3 own block g. Writes the tile's 8 rate-header
-// bytes to hdr (global) and its encoded bytes to slot; returns the byte count
-// (warp-uniform).
-__device__ __forceinline__ uint32_t compress_tile(const float* __restrict__ tile,
-                                                  uint8_t* __restrict__ slot,
-                                                  uint8_t* __restrict__ hdr, const float r,
-                                                  const int lane) {
-  constexpr uint32_t FULL = 0xffffffffu;
-  const float4 A = reinterpret_cast<const float4*>(tile)[2 * lane];
-  const float4 B = reinterpret_cast<const float4*>(tile)[2 * lane + 1];
-  const float d[8] = {A.x, A.y, A.z, A.w, B.x, B.y, B.z, B.w};
-
-  // Step 1, quantize (Sec. 4.2.2): t = fl(d r) then the nearest integer, ties to even.
-  // Y holds q + bits(M); differences of Y are differences of q.
-  int Y[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) Y[i] = __float_as_int(__fadd_rn(__fmul_rn(d[i], r), kMagic));
-
-  // Tile sum for centring (Sec. 4.2.2, variant 3), in the fixed order: the lane's 8
-  // elements left to right, then a butterfly over lanes 16, 8, 4, 2, 1.
-  float P = d[0];
-#pragma unroll
-  for (int i = 1; i < 8; ++i) P = __fadd_rn(P, d[i]);
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) P = __fadd_rn(P, __shfl_xor_sync(FULL, P, o));
-  const int mu =
-      __float_as_int(__fadd_rn(__fmul_rn(__fmul_rn(P, 0.00390625f), r), kMagic)) - kMagicBits;
-
-  // LZ1 residuals with the state carried across lane and block boundaries (Eq. 2); the
-  // tile's first predecessor is zero. LZ2 as the difference of LZ1 residuals:
-  // l2_i = (q_i - q_{i-1}) - (q_{i-1} - q_{i-2}).
-  int prevY = __shfl_up_sync(FULL, Y[7], 1);
-  if (lane == 0) prevY = kMagicBits;
-  int l1[8], l2[8];
-  l1[0] = Y[0] - prevY;
-#pragma unroll
-  for (int i = 1; i < 8; ++i) l1[i] = Y[i] - Y[i - 1];
-  int prevL = __shfl_up_sync(FULL, l1[7], 1);
-  if (lane == 0) prevL = 0;
-  l2[0] = l1[0] - prevL;
-#pragma unroll
-  for (int i = 1; i < 8; ++i) l2[i] = l1[i] - l1[i - 1];
-
-  // Block maxima as ORs (same bit length). rest* leave out the tile's first residual(s),
-  // the only ones centring changes (Eq. 4); they are used by lane 0 only.
-  uint32_t rest1 = 0, rest2 = 0;
-#pragma unroll
-  for (int i = 1; i < 8; ++i) rest1 |= uabs32(l1[i]);
-#pragma unroll
-  for (int i = 2; i < 8; ++i) rest2 |= uabs32(l2[i]);
-  const uint32_t o1 = rest1 | uabs32(l1[0]);
-  const uint32_t o2 = rest2 | uabs32(l2[0]) | uabs32(l2[1]);
-  const uint32_t x1 = __shfl_xor_sync(FULL, o1, 1);
-  uint32_t b1 = o1 | x1;
-  const uint32_t x2 = __shfl_xor_sync(FULL, b1, 2);
-  b1 |= x2;
-  const uint32_t y1 = __shfl_xor_sync(FULL, o2, 1);
-  uint32_t b2 = o2 | y1;
-  const uint32_t y2 = __shfl_xor_sync(FULL, b2, 2);
-  b2 |= y2;
-  // Rate r_b = bit length of the block maximum (Sec. 4.1.2).
-  const int R1 = 32 - __clz(int(b1));
-  const int R2 = 32 - __clz(int(b2));
-
-  // Centred block-0 rates (lane 0): l1c_0 = q_0 - mu, l2c_0 = q_0 - mu,
-  // l2c_1 = q_1 - 2 q_0 + mu = l2_1 + mu; the rest of block 0 is unchanged.
-  const int q0 = Y[0] - kMagicBits;
-  const uint32_t c10 = uabs32(q0 - mu);
-  const uint32_t c21 = uabs32(l2[1] + mu);
-  const int R1c = 32 - __clz(int(rest1 | x1 | x2 | c10));
-  const int R2c = 32 - __clz(int(rest2 | y1 | y2 | c10 | c21));
-
-  // Block costs S_b (Eq. 3) of LZ1 and LZ2 as 16-bit halves. An inclusive scan over the
-  // 8 groups gives every block's end offset for both variants; lane 31 holds the tile
-  // costs C = sum of S_b.
-  const uint32_t pk = block_cost(R1) | (block_cost(R2) << 16);
-  uint32_t pinc = pk, tmp;
-  tmp = __shfl_up_sync(FULL, pinc, 4); if (lane >= 4) pinc += tmp;
-  tmp = __shfl_up_sync(FULL, pinc, 8); if (lane >= 8) pinc += tmp;
-  tmp = __shfl_up_sync(FULL, pinc, 16); if (lane >= 16) pinc += tmp;
-  const uint32_t ptot = __shfl_sync(FULL, pinc, 31);
-  const int C1 = int(ptot & 0xffffu), C2 = int(ptot >> 16);
-  // Centring changes block 0 only: its cost deltas and rates, from lane 0.
-  uint32_t bc = (block_cost(R1c) - block_cost(R1) + 1024u) |
-                ((block_cost(R2c) - block_cost(R2) + 1024u) << 11) | (uint32_t(R1c) << 22) |
-                (uint32_t(R2c) << 27);
-  bc = __shfl_sync(FULL, bc, 0);
-  const int dC1 = int(bc & 0x7ffu) - 1024, dC2 = int((bc >> 11) & 0x7ffu) - 1024;
-  // Variants 3 and 4 pay 4 bytes for mu (step 2).
-  const int C3 = 4 + C1 + dC1;
-  const int C4 = 4 + C2 + dC2;
-  const int R1c0 = int((bc >> 22) & 31u), R2c0 = int(bc >> 27);
-
-  // Step 3, adaptive select: first strict minimum in the order LZ1, LZ2, LZ1c, LZ2c.
-  int v = 0, best = C1;
-  if (C2 < best) { v = 1; best = C2; }
-  if (C3 < best) { v = 2; best = C3; }
-  if (C4 < best) { v = 3; best = C4; }
-  const bool second = (v & 1) != 0, centred = v >= 2;
-
-  const int g = lane >> 2, t = lane & 3;
-  int Rg = second ? R2 : R1;
-  if (g == 0 && centred) Rg = second ? R2c0 : R1c0;
-  // Rate header (Sec. 3.1): block 0 carries bit 7 = order 2, bit 6 = centred.
-  if (t == 0) {
-    uint32_t hb = uint32_t(Rg);
-    if (g == 0) hb |= (second ? 0x80u : 0u) | (centred ? 0x40u : 0u);
-    hdr[g] = uint8_t(hb);
-  }
-
-  // Step 5: residuals of the selected variant as sign-magnitude words v = 2|l| + sign,
-  // so that bit 0 is the sign map and bit k + 1 is magnitude bit-plane k (Sec. 4.3).
-  uint32_t vv[8];
-  if (second) {  // the variant is warp-uniform
-#pragma unroll
-    for (int i = 0; i < 8; ++i) vv[i] = sign_mag(l2[i]);
-  } else {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) vv[i] = sign_mag(l1[i]);
-  }
-  const bool fix = centred && lane == 0;
-  vv[0] = fix ? sign_mag(q0 - mu) : vv[0];
-  vv[1] = (fix && second) ? sign_mag(l2[1] + mu) : vv[1];
-
-  // Byte offset of block g inside the tile's data: the variant's exclusive prefix; when
-  // centred, mu's 4 bytes come first and block 0's cost changes by its delta.
-  const uint32_t pexc = pinc - pk;
-  int off = int(second ? (pexc >> 16) : (pexc & 0xffffu));
-  if (centred) off += 4 + (g > 0 ? (second ? dC2 : dC1) : 0);
-  uint8_t* blk = slot + off;
-  if (fix) *reinterpret_cast<float*>(slot) = __int2float_rn(mu);
-
-  const int Rmax = int(__reduce_max_sync(FULL, uint32_t(Rg)));
-  if (Rmax > 0) {
-    const int nch = (Rmax + 8) >> 3;  // 8-plane slices of v covering bits 0..Rmax
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (c < nch) {
-        // Byte c of v_7..v_4 into lo, of v_3..v_0 into hi (element order reversed), so the
-        // 8x8 transpose leaves plane 8c + b in byte b with element i at bit 7 - i.
-        const uint32_t sel = uint32_t(c) | (uint32_t(4 + c) << 4);
-        uint32_t lo = __byte_perm(__byte_perm(vv[7], vv[6], sel), __byte_perm(vv[5], vv[4], sel), 0x5410);
-        uint32_t hi = __byte_perm(__byte_perm(vv[3], vv[2], sel), __byte_perm(vv[1], vv[0], sel), 0x5410);
-        transpose8x8(lo, hi);
-        // Gather the 4 lanes' bytes of one plane into a 32-element word: lane t then
-        // holds words 8c + t and 8c + 4 + t of its block, bytes in memory order.
-        lo = transpose4x4_bytes(lo, t);
-        hi = transpose4x4_bytes(hi, t);
-        const int w0 = 8 * c + t, w1 = w0 + 4;
-        if (Rg > 0 && w0 <= Rg) reinterpret_cast<uint32_t*>(blk)[w0] = lo;
-        if (Rg > 0 && w1 <= Rg) reinterpret_cast<uint32_t*>(blk)[w1] = hi;
-      }
-    }
-  }
-  return uint32_t(best);
-}
-
 // Compresses two tiles with one warp: lanes 0-15 take one tile and lanes 16-31 the next
 // (half = lane >> 4). Lane hl = lane & 15 owns elements 16 hl..16 hl + 15 of its tile, so
-// lanes 2g, 2g + 1 of a half own block g. The halves run the same steps as compress_tile
-// (same arithmetic, same summation order for mu, same bytes) with half the shuffles per
-// tile. `tile` and `hdr` are this half's; the first half's bytes go to `slot`, the second
-// half's right after them. A half with `live` false computes but stores nothing. Returns
-// this half's byte count (uniform within the half).
-__device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ tile,
-                                                    uint8_t* __restrict__ slot,
-                                                    uint8_t* __restrict__ hdr, const float r,
-                                                    const int lane, const bool live) {
+// lanes 2g, 2g + 1 of a half own block g (Sec. 3.1: a tile is 8 blocks of 32 elements).
+// The halves run in lockstep but each takes its own decisions (variant, rates). `tile` and
+// `hdr` are this half's; the first half's bytes go to `slot`, the second half's right
+// after them. A half with `live` false computes but stores nothing. Returns this half's
+// byte count (uniform within the half).
+__device__ __forceinline__ uint32_t compress_pair(const float* __restrict__ tile,
+                                                  uint8_t* __restrict__ slot,
+                                                  uint8_t* __restrict__ hdr, const float r,
+                                                  const int lane, const bool live) {
   constexpr uint32_t FULL = 0xffffffffu;
   const int hl = lane & 15;
   const float4* t4 = reinterpret_cast<const float4*>(tile) + 4 * hl;
@@ -291,14 +122,16 @@ __device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ ti
   for (int k = 0; k < 4; ++k) {
     d[4 * k] = q[k].x; d[4 * k + 1] = q[k].y; d[4 * k + 2] = q[k].z; d[4 * k + 3] = q[k].w;
   }
-  // Step 1, quantize (Sec. 4.2.2), as in compress_tile.
+  // Step 1, quantize (Sec. 4.2.2): t = fl(d r) then the nearest integer, ties to even.
+  // Y holds q + bits(M); differences of Y are differences of q.
   int Y[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) Y[i] = __float_as_int(__fadd_rn(__fmul_rn(d[i], r), kMagic));
 
-  // Tile sum, in compress_tile's order: the 8-element sums of elements 8j..8j+7 (here two
-  // per lane, V0 = j even, V1 = j odd), then the butterfly over j by 16, 8, 4, 2 (lane
-  // xor 8, 4, 2, 1 within the half) and finally by 1 (V0 + V1).
+  // Tile sum for centring (Sec. 4.2.2, variant 3) in the fixed order: the sums of elements
+  // 8j..8j+7 left to right (two per lane: V0 for j even, V1 for j odd), then a butterfly
+  // over j by 16, 8, 4, 2 (lanes xor 8, 4, 2, 1 within the half) and finally by 1
+  // (V0 + V1). Float addition is commutative, so both partners of a step get equal sums.
   float V0 = d[0], V1 = d[8];
 #pragma unroll
   for (int i = 1; i < 8; ++i) {
@@ -314,7 +147,9 @@ __device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ ti
   const int mu =
       __float_as_int(__fadd_rn(__fmul_rn(__fmul_rn(P, 0.00390625f), r), kMagic)) - kMagicBits;
 
-  // LZ1 and LZ2 residuals with the state carried across lanes and blocks (Eq. 2).
+  // LZ1 residuals with the state carried across lane and block boundaries (Eq. 2); the
+  // tile's first predecessor is zero. LZ2 as the difference of LZ1 residuals:
+  // l2_i = (q_i - q_{i-1}) - (q_{i-1} - q_{i-2}).
   int prevY = __shfl_up_sync(FULL, Y[15], 1, 16);
   if (hl == 0) prevY = kMagicBits;
   int l1[16], l2[16];
@@ -327,6 +162,8 @@ __device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ ti
 #pragma unroll
   for (int i = 1; i < 16; ++i) l2[i] = l1[i] - l1[i - 1];
 
+  // Block maxima as ORs (same bit length); the block's two lanes combine by one shuffle.
+  // rest* leave out the tile's first residual(s), the only ones centring changes (Eq. 4).
   uint32_t rest1 = 0, rest2 = 0;
 #pragma unroll
   for (int i = 1; i < 16; ++i) rest1 |= uabs32(l1[i]);
@@ -336,18 +173,22 @@ __device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ ti
   const uint32_t o2 = rest2 | uabs32(l2[0]) | uabs32(l2[1]);
   const uint32_t x1 = __shfl_xor_sync(FULL, o1, 1);
   const uint32_t y1 = __shfl_xor_sync(FULL, o2, 1);
+  // Rate r_b = bit length of the block maximum (Sec. 4.1.2).
   const int R1 = 32 - __clz(int(o1 | x1));
   const int R2 = 32 - __clz(int(o2 | y1));
 
-  // Centred block-0 rates (lane hl = 0), as in compress_tile.
+  // Centred block-0 rates (lane hl = 0): l1c_0 = q_0 - mu, l2c_0 = q_0 - mu,
+  // l2c_1 = q_1 - 2 q_0 + mu = l2_1 + mu; the rest of block 0 is unchanged (Eq. 4).
   const int q0 = Y[0] - kMagicBits;
   const uint32_t c10 = uabs32(q0 - mu);
   const uint32_t c21 = uabs32(l2[1] + mu);
   const int R1c = 32 - __clz(int(rest1 | x1 | c10));
   const int R2c = 32 - __clz(int(rest2 | y1 | c10 | c21));
 
-  // Block costs (Eq. 3): inclusive scan over the 8 blocks (lanes 2 apart); lane 15 of the
-  // half holds the tile costs.
+  // Block costs S_b (Eq. 3) of LZ1 and LZ2 as 16-bit halves. An inclusive scan over the
+  // 8 blocks (lanes 2 apart) gives every block's end offset for both variants; lane 15 of
+  // the half holds the tile costs C = sum of S_b. Centring changes block 0 only: its cost
+  // deltas and rates come from lane 0; variants 3 and 4 pay 4 bytes for mu (step 2).
   const uint32_t pk = block_cost(R1) | (block_cost(R2) << 16);
   uint32_t pinc = pk, tmp;
   tmp = __shfl_up_sync(FULL, pinc, 2, 16); if (hl >= 2) pinc += tmp;
@@ -374,13 +215,16 @@ __device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ ti
   const int g = hl >> 1, t2 = hl & 1;
   int Rg = second ? R2 : R1;
   if (g == 0 && centred) Rg = second ? R2c0 : R1c0;
+  // Rate header (Sec. 3.1): block 0 carries bit 7 = order 2, bit 6 = centred.
   if (t2 == 0 && live) {
     uint32_t hb = uint32_t(Rg);
     if (g == 0) hb |= (second ? 0x80u : 0u) | (centred ? 0x40u : 0u);
     hdr[g] = uint8_t(hb);
   }
 
-  // Step 5 (the variant differs between the halves: select, do not branch).
+  // Step 5: residuals of the selected variant as sign-magnitude words v = 2|l| + sign,
+  // so that bit 0 is the sign map and bit k + 1 is magnitude bit-plane k (Sec. 4.3). The
+  // halves may select different variants: select per element rather than branch.
   uint32_t vv[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) vv[i] = sign_mag(second ? l2[i] : l1[i]);
@@ -388,6 +232,8 @@ __device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ ti
   vv[0] = fix ? sign_mag(q0 - mu) : vv[0];
   vv[1] = (fix && second) ? sign_mag(l2[1] + mu) : vv[1];
 
+  // Byte offset of block g inside the tile's data: the variant's exclusive prefix; when
+  // centred, mu's 4 bytes come first and block 0's cost changes by its delta.
   const uint32_t pexc = pinc - pk;
   int off = int(second ? (pexc >> 16) : (pexc & 0xffffu));
   if (centred) off += 4 + (g > 0 ? (second ? dC2 : dC1) : 0);
@@ -402,8 +248,10 @@ __device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ ti
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       if (c < nch) {
+        // Byte c of v_7..v_4 into lo, of v_3..v_0 into hi (element order reversed), so the
+        // 8x8 transpose leaves plane 8c + b in byte b with element i at bit 7 - i; the
+        // same for the lane's elements 8-15.
         const uint32_t sel = uint32_t(c) | (uint32_t(4 + c) << 4);
-        // two 8x8 transposes: elements 0-7 and 8-15 of the lane; byte b = plane 8c + b
         uint32_t lo0 = __byte_perm(__byte_perm(vv[7], vv[6], sel), __byte_perm(vv[5], vv[4], sel), 0x5410);
         uint32_t hi0 = __byte_perm(__byte_perm(vv[3], vv[2], sel), __byte_perm(vv[1], vv[0], sel), 0x5410);
         uint32_t lo1 = __byte_perm(__byte_perm(vv[15], vv[14], sel), __byte_perm(vv[13], vv[12], sel), 0x5410);
@@ -416,7 +264,8 @@ __device__ __forceinline__ uint32_t compress_pair16(const float* __restrict__ ti
         const uint32_t r1 = __shfl_xor_sync(FULL, t2 ? lo1 : hi1, 1);
         const uint32_t X0 = t2 ? r0 : lo0, X1 = t2 ? r1 : lo1;
         const uint32_t Y0 = t2 ? hi0 : r0, Y1 = t2 ? hi1 : r1;
-        // word b = [X0.b, X1.b, Y0.b, Y1.b]: elements 0-7, 8-15, 16-23, 24-31
+        // word b = [X0.b, X1.b, Y0.b, Y1.b] in memory order: elements 0-7, 8-15, 16-23,
+        // 24-31, each byte with its first element in the top bit (Sec. 4.3)
         const uint32_t u0 = __byte_perm(X0, X1, 0x5140), u1 = __byte_perm(X0, X1, 0x7362);
         const uint32_t u2 = __byte_perm(Y0, Y1, 0x5140), u3 = __byte_perm(Y0, Y1, 0x7362);
         const uint32_t w[4] = {__byte_perm(u0, u2, 0x5410), __byte_perm(u0, u2, 0x7632),
@@ -505,8 +354,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
         set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
         return;
       }
-      ChunkInfo& q = S.pre[kTicketAhead ? seq % kTicketAhead : 0];
-      if (kTicketAhead == 0) fetch(q);
+      ChunkInfo& q = S.pre[seq % kTicketAhead];
       S.meta[b] = q;
       if (q.chunk >= total) {
         S.meta[b].chunk = kNone;
@@ -525,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
         mbar_arrive_expect_tx(&S.full[s], bulk);
         if (bulk) tma_load_1d(S.in[s], q.in + e_h, bulk, &S.full[s]);
       }
-      if (kTicketAhead > 0) fetch(q);  // the ticket kTicketAhead chunks ahead
+      fetch(q);  // the ticket kTicketAhead chunks ahead
     }
   }
 
@@ -579,7 +427,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
         if (lane == 0) set_error(a.ctrl, ci.fi, FSZ_ERR_CAPACITY);
       } else {
         uint8_t* base = ci.out + ci.data_base + excl;
-#if FSZ_LANE16
         // the warp's pair of each stage: contiguous in the ring and in the stream
         const int nt = int(ci.ntiles);
         for (int t0 = 2 * warp; t0 < nt; t0 += kStageTiles) {
@@ -589,15 +436,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
           uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][t0]);
           for (uint32_t q = lane; q < nw; q += 32) dst[q] = src[q];
         }
-#else
-        for (int tl = warp; tl < int(ci.ntiles); tl += kComputeWarps) {
-          const uint32_t ti = S.tinfo[b][tl];
-          const uint32_t nw = (ti & 0xffffu) >> 2;
-          const uint32_t* src = reinterpret_cast<const uint32_t*>(ring + (ti >> 16));
-          uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][tl]);
-          for (uint32_t q = lane; q < nw; q += 32) dst[q] = src[q];
-        }
-#endif
         if (warp == 0 && lane == 0 && (ci.flags & kInfoLast)) write_preamble(ci.fi, excl + tot);
       }
     }
@@ -661,7 +499,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       uint8_t* hdr_out = ci.out + 64 + 8 * ci.tile0;
       const int t_end = min(ntiles, int(h + 1) * kStageTiles);
       const bool ragged = cnt < uint32_t(kStageElems);
-#if FSZ_LANE16
       const int ta = int(h) * kStageTiles + 2 * warp;  // this warp's pair in the stage
       if (ta < t_end) {
         const int half = lane >> 4;
@@ -695,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
         if (!ok_run) break;
         head += skip;
         pos = head % kRingBytes;
-        const uint32_t nb = compress_pair16(tile, ring + pos, hdr_out + 8 * tl, r, lane, live);
+        const uint32_t nb = compress_pair(tile, ring + pos, hdr_out + 8 * tl, r, lane, live);
         const uint32_t na = __shfl_sync(0xffffffffu, nb, 0);
         const uint32_t nbb = __shfl_sync(0xffffffffu, nb, 16);
         const bool second_live = ta + 1 < t_end;
@@ -703,41 +540,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
         if (lane == 16 && second_live) S.tinfo[b][ta + 1] = ((pos + na) << 16) | nbb;
         head += na + (second_live ? nbb : 0u);
       }
-#else
-      for (int tl = int(h) * kStageTiles + warp; tl < t_end; tl += kComputeWarps) {
-        const int ts = tl - int(h) * kStageTiles;  // tile within the stage
-        float* tile = S.in[s] + ts * kTile;
-        // Ragged end of a field: this lane's elements past the last 16-byte boundary of
-        // the bulk copy by plain loads; padding elements are zeros (they quantize to 0).
-        const uint32_t k0 = uint32_t(ts) * kTile + 8u * uint32_t(lane);
-        if (ragged && k0 + 8 > bulk_elems) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const uint32_t k = k0 + uint32_t(i);
-            if (k >= bulk_elems) tile[8 * lane + i] = k < cnt ? gin[k] : 0.0f;
-          }
-        }
-        // Room for a worst-case tile, contiguous in the ring (a tile never wraps). The
-        // counters only grow: a chunk this warp has no tile in still holds a mark.
-        uint32_t pos = head % kRingBytes;
-        uint32_t skip = pos + kMaxTileBytes > kRingBytes ? kRingBytes - pos : 0u;
-        while (kRingBytes - (head - tail) < skip + kMaxTileBytes) {
-          if (placed == done || !place_oldest()) {  // cannot happen with an empty ring
-            if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-            ok_run = false;
-            break;
-          }
-          pos = head % kRingBytes;
-          skip = pos + kMaxTileBytes > kRingBytes ? kRingBytes - pos : 0u;
-        }
-        if (!ok_run) break;
-        head += skip;
-        pos = head % kRingBytes;
-        const uint32_t nb = compress_tile(tile, ring + pos, hdr_out + 8 * tl, r, lane);
-        if (lane == 0) S.tinfo[b][tl] = (pos << 16) | nb;
-        head += nb;
-      }
-#endif
       if (!ok_run) break;
     }
     __syncwarp();

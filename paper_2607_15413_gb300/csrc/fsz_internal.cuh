@@ -306,9 +306,6 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 // Every spin is bounded by `deadline`; a wait that runs out reads as a zero inclusive
 // prefix and sets *timed_out (the caller records FSZ_ERR_TIMEOUT and still publishes, so
 // no successor waits forever).
-#ifndef FSZ_LOOKBACK_SLEEP_NS
-#define FSZ_LOOKBACK_SLEEP_NS 64
-#endif
 template <int K>
 __device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchunk, int64_t first,
                                              uint64_t deadline, bool* timed_out) {
@@ -355,7 +352,7 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchu
           if (wait_mask & (1u << k)) take(k, kFlagIncl);
         continue;
       }
-      __nanosleep(FSZ_LOOKBACK_SLEEP_NS);
+      __nanosleep(64);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const uint32_t d = uint32_t(32 * k + lane);

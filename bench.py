@@ -270,19 +270,22 @@ def run_batched(fsz, inputs, dev, reps: int = 3):
     return out
 
 
-def run_serving(fsz, inputs, dev, nreq: int = 20000, seed: int = 4):
-    """Serving workload: requests of log-uniform 16 KiB-256 MiB cut from a device-resident
-    pool of the batched mix's classes, 60 % compress / 40 % decompress of an earlier result
-    (the 64 newest streams), REL from {1e-2,1e-3,1e-4}, 40 GB admission budget, 4 stream
-    slots, batches of up to 32. First the closed loop (all requests at once: the peak),
-    then Poisson arrivals at 25/50/75/100 % of that peak; p50/p99 latency from the
-    scheduled arrival to completion, sustained GB/s. The baseline is the closed loop's first
+def run_serving(fsz, inputs, dev, nreq: int = 20000, seed: int = 4, linger_us: int = 200):
+    """Serving workload through the library's native server: requests of log-uniform
+    16 KiB-256 MiB cut from a device-resident pool of the batched mix's classes, 60 %
+    compress / 40 % decompress of one of 64 streams compressed beforehand, REL from
+    {1e-2,1e-3,1e-4}, 40 GB admission budget, 4 stream slots, batches of up to 32. First the
+    closed loop (every request arrives at once: the peak), then Poisson arrivals at
+    25/50/75/100 % of that peak. Each level is handed to the server as one trace (each
+    request with its arrival time; the server admits it then), so no client thread sits on
+    the clock. p50/p99 latency from the arrival to completion, sustained GB/s over the span
+    from the first arrival to the last completion. The baseline is the closed loop's first
     2000 requests issued as one library call each (fsz_compress / fsz_decompress) on one
     stream."""
     import math
     import random
-    import threading
 
+    import numpy as np
     import torch
 
     from paper_2607_15413_gb300 import serve
@@ -294,86 +297,96 @@ def run_serving(fsz, inputs, dev, nreq: int = 20000, seed: int = 4):
     del g
     torch.cuda.empty_cache()
     rng = random.Random(seed)
-    lock = threading.Lock()
-    lru = []  # (stream tensor, element count) of the newest successful compressions
+    srv = serve.Server(budget_bytes=40 << 30, n_slots=4, max_batch=32, max_batch_elems=4 << 30,
+                       linger_s=linger_us * 1e-6, futures=False)
+    L = fsz.lib()
+    next_id = [1]
 
-    def make_requests(count):
+    def windows(count):
         out = []
         for _ in range(count):
             src = pool[rng.randrange(3)]
             n = int(math.exp(rng.uniform(math.log(4096), math.log(64 << 20))))
             n = max(4, min(n, src.numel()) // 4 * 4)
             off = rng.randrange(0, (src.numel() - n) // 4 + 1) * 4
-            out.append((src[off:off + n], rng.choice([1e-2, 1e-3, 1e-4]), rng.random() < 0.4))
+            out.append((src.data_ptr() + 4 * off, n, rng.choice([1e-2, 1e-3, 1e-4])))
         return out
 
-    backend = serve.GpuBackend(n_slots=4, max_batch=32, max_elems=10 << 30, device=dev)
-
-    def run(reqs, rate=None, record=None):
-        """rate None: closed loop; else Poisson arrivals at `rate` requests/s. Results are
-        reduced to their status and latency as they complete (outputs are dropped, except
-        the newest compressions kept for later decompress requests)."""
-        srv = serve.Server(backend, budget_bytes=40 << 30, n_slots=4, max_batch=32)
-        lat, refused = [], [0]
-        remaining = [len(reqs)]
-        all_done = threading.Event()
-
-        def on_done(f, kind, n):
-            r = f.result()
-            with lock:
-                if r.status == 0:
-                    lat.append(r.latency_s * 1e3)
-                    if kind == serve.COMPRESS:
-                        # a view into its batch's output arena: the 64 newest results come
-                        # from the last few batches, so only their arenas stay resident
-                        lru.append((r.output, n))
-                        if len(lru) > 64:
-                            lru.pop(0)
-                else:
-                    refused[0] += 1
-                remaining[0] -= 1
-                if remaining[0] == 0:
-                    all_done.set()
-
-        nbytes = 0
-        t0 = time.perf_counter()
-        t_arr = t0
-        for x, rel, want_dec in reqs:
-            if rate is not None:
-                t_arr += rng.expovariate(rate)
-                delay = t_arr - time.perf_counter()
-                if delay > 1e-4:
-                    time.sleep(delay)
-            with lock:
-                prev = lru[rng.randrange(len(lru))] if (want_dec and lru) else None
-            arrival = t_arr if rate is not None else 0.0
-            if prev is not None:
-                req = serve.Request(kind=serve.DECOMPRESS, data=prev[0], n=prev[1], arrival=arrival)
-                n = prev[1]
+    def trace(count, sources, dec_share=0.4):
+        """A request table: compress requests of pool windows, and with `dec_share`
+        decompress requests of one of `sources` (stream pointer, bytes, n)."""
+        t = np.zeros(count, dtype=fsz.REQUEST_NP)
+        t["id"] = np.arange(next_id[0], next_id[0] + count, dtype=np.uint64)
+        next_id[0] += count
+        rows = []
+        for ptr, n, rel in windows(count):
+            if sources and rng.random() < dec_share:
+                sp, sb, sn = sources[rng.randrange(len(sources))]
+                rows.append((fsz.REQ_DECOMPRESS, 0, 0, 0, 0.0, sp, sb, sn))
             else:
-                n = x.numel()
-                req = serve.Request(kind=serve.COMPRESS, data=x, shape=(n,), eb=rel, mode=1,
-                                    arrival=arrival)
-            if record is not None and len(record) < record_cap:
-                record.append((req.kind, req.data, n, rel))
-            nbytes += 4 * n
-            srv.submit(req).add_done_callback(lambda f, k=req.kind, n=n: on_done(f, k, n))
-        all_done.wait(600)
-        wall = time.perf_counter() - t0
-        srv.close()
-        return {"gbs": nbytes / wall / 1e9, "p50_ms": serve.percentile(lat, 50),
-                "p99_ms": serve.percentile(lat, 99), "requests": len(reqs),
-                "refused": refused[0], "bytes": nbytes, "wall_s": wall,
-                "batches": srv.stats["batches"], "max_inflight": srv.stats["max_inflight"],
-                "admitted_while_busy": srv.stats["admitted_while_busy"]}
+                rows.append((fsz.REQ_COMPRESS, 1, 1, n, rel, ptr, 0, 0))
+        cols = list(zip(*rows))
+        for name, col in zip(("kind", "mode", "ndim", "d0", "eb", "d_in", "in_bytes", "n"), cols):
+            t[name] = col
+        return t
 
-    run(make_requests(max(64, nreq // 10)))      # warm-up; fills the stream LRU
-    record, record_cap = [], min(nreq, 2000)
-    closed = run(make_requests(nreq), record=record)
-    # the closed loop's requests, one library call each, one stream (the per-request baseline)
-    L = fsz.lib()
+    def elems(t):
+        return np.where(t["kind"] == fsz.REQ_COMPRESS, t["d0"], t["n"]).astype(np.int64)
+
+    cbuf = np.zeros(4096, dtype=fsz.COMPLETION_NP)
+
+    def run(t, rate=None, keep=False):
+        """Submits table `t` (closed loop, or Poisson arrivals at `rate` requests/s) and
+        takes every completion; releases the outputs unless `keep`."""
+        count = len(t)
+        t0 = time.monotonic_ns() + 2_000_000
+        if rate is None:
+            t["arrival_ns"] = t0
+        else:
+            gaps = np.array([rng.expovariate(rate) for _ in range(count)]) * 1e9
+            t["arrival_ns"] = t0 + np.cumsum(gaps).astype(np.uint64)
+        st0 = srv.stats()
+        code = L.fsz_server_submit_many(srv._h, t.ctypes.data, count)
+        if code:
+            raise fsz.FszError(code, "fsz_server_submit_many")
+        got = []
+        while sum(len(g) for g in got) < count:
+            k = L.fsz_server_poll(srv._h, cbuf.ctypes.data, len(cbuf), 2_000_000)
+            if k:
+                c = cbuf[:k].copy()
+                got.append(c)
+                ok = c["id"][c["status"] != fsz.ERR_REJECTED]
+                if not keep and len(ok):
+                    L.fsz_server_release_many(srv._h, np.ascontiguousarray(ok).ctypes.data, len(ok), None)
+        t_end = time.monotonic_ns()
+        st1 = srv.stats()
+        c = np.concatenate(got)
+        ok = c["status"] == 0
+        lat = c["latency_ns"][ok] * 1e-6
+        nbytes = int(4 * elems(t).sum())
+        wall = (t_end - t0) * 1e-9
+        return c, {"gbs": nbytes / wall / 1e9,
+                   "p50_ms": float(np.percentile(lat, 50)) if len(lat) else float("nan"),
+                   "p99_ms": float(np.percentile(lat, 99)) if len(lat) else float("nan"),
+                   "requests": count, "refused": int((~ok).sum()), "bytes": nbytes,
+                   "wall_s": wall, "batches": st1["batches"] - st0["batches"],
+                   "mean_batch": count / max(1, st1["batches"] - st0["batches"]),
+                   "max_inflight": st1["max_inflight"],
+                   "admitted_while_busy": st1["admitted_while_busy"] - st0["admitted_while_busy"]}
+
+    # 64 streams for the decompress requests, held for the whole run
+    src_t = trace(64, None)
+    src_c, _ = run(src_t, keep=True)
+    by_id = {int(r["id"]): r for r in src_c}
+    sources = [(int(by_id[int(i)]["d_out"]), int(by_id[int(i)]["out_bytes"]), int(n))
+               for i, n in zip(src_t["id"], src_t["d0"]) if by_id[int(i)]["status"] == 0]
+    run(trace(max(64, nreq // 10), sources))      # warm-up (pool, workspaces, clocks)
+    t_closed = trace(nreq, sources)
+    _, closed = run(t_closed)
+    # the closed loop's first requests, one library call each, one stream (the baseline)
+    rec = t_closed[:min(nreq, 2000)]
     sp = torch.cuda.current_stream(dev).cuda_stream
-    nmax = max(n for _, _, n, _ in record)
+    nmax = int(elems(rec).max())
     ws_b = fsz.fsz_workspace_bytes(nmax)
     ws = torch.empty(ws_b, dtype=torch.uint8, device=dev)
     cap = fsz.fsz_compress_bound(nmax)
@@ -382,36 +395,37 @@ def run_serving(fsz, inputs, dev, nreq: int = 20000, seed: int = 4):
     nb = torch.zeros(1, dtype=torch.int64, device=dev)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    tot = 0
-    for kind, data, n, rel in record:
-        if kind == serve.COMPRESS:
-            L.fsz_compress(data.data_ptr(), fsz.make_dims((n,)), 1, rel, out.data_ptr(), cap,
-                           nb.data_ptr(), ws.data_ptr(), ws_b, sp)
+    for r in rec:
+        if r["kind"] == fsz.REQ_COMPRESS:
+            L.fsz_compress(int(r["d_in"]), fsz.make_dims((int(r["d0"]),)), 1, float(r["eb"]),
+                           out.data_ptr(), cap, nb.data_ptr(), ws.data_ptr(), ws_b, sp)
         else:
-            L.fsz_decompress(data.data_ptr(), data.numel(), dout.data_ptr(), n, ws.data_ptr(), ws_b, sp)
-        tot += 4 * n
+            L.fsz_decompress(int(r["d_in"]), int(r["in_bytes"]), dout.data_ptr(), int(r["n"]),
+                             ws.data_ptr(), ws_b, sp)
     torch.cuda.synchronize(dev)
-    per_req_gbs = tot / (time.perf_counter() - t0) / 1e9
-    n_dec = sum(1 for k, _, _, _ in record if k == serve.DECOMPRESS)
-    n_rec = len(record)
-    del record, out, dout, ws
+    per_req_gbs = 4 * int(elems(rec).sum()) / (time.perf_counter() - t0) / 1e9
+    n_dec = int((rec["kind"] == fsz.REQ_DECOMPRESS).sum())
+    del out, dout, ws
     mean_bytes = closed["bytes"] / closed["requests"]
     levels = []
     for load in (0.25, 0.5, 0.75, 1.0):
         rate = load * closed["gbs"] * 1e9 / mean_bytes
-        r = run(make_requests(nreq), rate=rate)
+        _, r = run(trace(nreq, sources), rate=rate)
         r["load"] = load
         r["offered_gbs"] = load * closed["gbs"]
         levels.append(r)
-    lru.clear()
+    ids = np.ascontiguousarray(src_c["id"][src_c["status"] != fsz.ERR_REJECTED])
+    L.fsz_server_release_many(srv._h, ids.ctypes.data, len(ids), None)
+    srv.close()
     del pool
     torch.cuda.empty_cache()
     return {"workload": f"{nreq} requests per level, seed {seed}: log-uniform 16 KiB-256 MiB windows "
                         "of a device pool (k^-3 GRF, particle-like, zero-slab), 60% compress / 40% "
-                        "decompress of an earlier result, REL in {1e-2,1e-3,1e-4}, 40 GB budget, "
-                        "4 streams, batches of up to 32",
-            "closed_loop": closed, "sample_decompress_share": n_dec / max(1, n_rec),
-            "per_request_gbs": per_req_gbs, "per_request_sample": n_rec,
+                        "decompress of one of 64 earlier streams, REL in {1e-2,1e-3,1e-4}, 40 GB "
+                        f"budget, 4 streams, batches of up to 32, linger {linger_us} us while busy; "
+                        "native scheduler (fsz_server_*), each level replayed as a trace",
+            "closed_loop": closed, "sample_decompress_share": n_dec / max(1, len(rec)),
+            "per_request_gbs": per_req_gbs, "per_request_sample": len(rec),
             "closed_loop_vs_per_request": closed["gbs"] / per_req_gbs, "loads": levels}
 
 

@@ -53,7 +53,8 @@ typedef enum {
   FSZ_ERR_CORRUPT = 6,      /* the compressed stream is malformed (device-detected) */
   FSZ_ERR_TIMEOUT = 7,      /* a lookback wait ran past its time limit (device-detected) */
   FSZ_ERR_CUDA = 8,         /* a CUDA runtime call or a kernel launch failed */
-  FSZ_ERR_WORKSPACE = 9     /* the workspace is smaller than fsz_*_workspace_bytes() */
+  FSZ_ERR_WORKSPACE = 9,    /* the workspace is smaller than fsz_*_workspace_bytes() */
+  FSZ_ERR_REJECTED = 10     /* a served request that can never fit the server's limits */
 } fsz_status;
 
 typedef enum { FSZ_EB_ABS = 0, FSZ_EB_REL = 1 } fsz_eb_mode;
@@ -210,6 +211,105 @@ fsz_status fsz_read_header(const void* h_first64, uint64_t* n, fsz_dims* dims, d
 fsz_status fsz_compress_noalloc(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
                                 void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
                                 uint32_t* d_status, fsz_stream stream);
+
+/* ------------------------------------------------------------------ serving */
+
+/* A continuous-batching request server (no counterpart in the paper: the serving pattern
+ * this library adds around the batched path). Clients submit compress and decompress
+ * requests whose inputs are on the device; one native scheduler thread owns every GPU call:
+ *  - Arrival: a request enters the queue at its arrival_ns (at once if that has passed or
+ *    is 0), in submission order: submitting requests ahead of their arrival times replays
+ *    a trace without a client thread on the clock.
+ *  - Admission: requests are admitted in arrival order while the device-memory budget
+ *    allows. The budget counts the output memory the server allocates for the requests
+ *    in flight (see fsz_server_request_cost), from admission to completion. A
+ *    request that can never fit (cost above the whole budget, or more elements than a
+ *    batch may hold) completes at once with FSZ_ERR_REJECTED. A request that does not fit
+ *    yet waits at the head of the queue; later requests do not overtake it.
+ *  - Batching: the head's kind (compress or decompress) picks the batch. It takes up to
+ *    max_batch waiting requests of that kind in arrival order, reaching past requests of
+ *    the other kind within a window of `scan` requests while holding their memory in
+ *    reserve, so a skipped request still fits when its own batch goes next. A batch runs as
+ *    one fsz_compress_batched / fsz_decompress_batched call on the first free slot (a
+ *    stream of its own, with its own workspace). Requests that arrive while batches run
+ *    are admitted and launched as slots and budget free up. With linger_us > 0, while
+ *    other batches are running, a batch short of max_batch is launched only once its
+ *    first request has waited linger_us, so that small requests arriving close together
+ *    share a batch; an idle server launches at once.
+ *  - Completion: a CUDA event per batch; each request's completion carries its status
+ *    (that field's device status), its output and its latency (arrival to completion on
+ *    the host's monotonic clock).
+ * Outputs live in one device allocation per batch, from a memory pool of the server's own.
+ * Outputs that the client holds after completion are no longer charged to the budget.
+ * An output stays valid until fsz_server_release; the batch's allocation is freed when all
+ * its outputs are released. Every completion other than FSZ_ERR_REJECTED must be released.
+ * With sim_service_ns > 0 the server makes no CUDA call: a batch completes that long after
+ * its launch, outputs are NULL (for testing the scheduling rules without a GPU). */
+typedef struct fsz_server_s* fsz_server;
+typedef enum { FSZ_REQ_COMPRESS = 0, FSZ_REQ_DECOMPRESS = 1 } fsz_request_kind;
+
+typedef struct {
+  uint64_t budget_bytes;     /* output memory the server may hold */
+  uint32_t slots;            /* concurrent batches, 1..16 */
+  uint32_t max_batch;        /* requests per batch, 1..4096 */
+  uint32_t scan;             /* waiting requests looked at per batch (0: 4 * max_batch) */
+  uint32_t linger_us;        /* while batches run, a batch short of max_batch waits up to this
+                                long after its first request's arrival for more (0: none) */
+  uint64_t max_batch_elems;  /* most elements one batch may hold; sizes the workspaces */
+  uint64_t sim_service_ns;   /* 0 for the GPU; > 0 for the no-GPU test mode */
+} fsz_server_config;
+
+typedef struct {
+  uint64_t id;          /* the caller's tag, returned with the completion */
+  uint32_t kind;        /* fsz_request_kind */
+  uint32_t mode;        /* compress: fsz_eb_mode */
+  fsz_dims dims;        /* compress: the field's shape; decompress: unused (zeros) */
+  double eb;            /* compress: the error bound */
+  const void* d_in;     /* device: the float32 field, or the stream (16-byte aligned) */
+  uint64_t in_bytes;    /* decompress: the stream's size */
+  uint64_t n;           /* decompress: the element count */
+  uint64_t arrival_ns;  /* monotonic clock (CLOCK_MONOTONIC) of arrival; 0 = at submission */
+} fsz_request;
+
+typedef struct {
+  uint64_t id;
+  int32_t status;       /* fsz_status of this request */
+  uint32_t batch_size;  /* requests in its batch */
+  uint64_t batch;       /* its batch's launch index (0, 1, ...); UINT64_MAX if rejected */
+  void* d_out;          /* device: the stream (compress) or the float32 values (decompress) */
+  uint64_t out_bytes;   /* the stream's size, or 4n */
+  uint64_t latency_ns;  /* arrival to completion */
+} fsz_completion;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, batches, max_inflight, max_batch_seen;
+  uint64_t admitted_while_busy, budget_free, bytes_in;
+} fsz_server_stats;
+
+/* Output bytes the server charges to its budget for a request (its allocation, rounded). */
+uint64_t fsz_server_request_cost(const fsz_request* req);
+fsz_status fsz_server_create(const fsz_server_config* cfg, fsz_server* out);
+/* Queues a request (thread-safe, non-blocking). Argument errors are returned here. */
+fsz_status fsz_server_submit(fsz_server s, const fsz_request* req);
+/* Queues `count` requests from the host array h_reqs in order, under one lock; all or none
+ * (the first argument error is returned and nothing is queued). */
+fsz_status fsz_server_submit_many(fsz_server s, const fsz_request* h_reqs, uint64_t count);
+/* Copies up to `max` completions to h_out, waiting up to wait_ns for the first; returns
+ * how many (thread-safe). */
+uint32_t fsz_server_poll(fsz_server s, fsz_completion* h_out, uint32_t max, uint64_t wait_ns);
+/* Gives back request id's output; the memory is freed in order on `stream` once every
+ * output of its batch has been released (thread-safe). */
+fsz_status fsz_server_release(fsz_server s, uint64_t id, fsz_stream stream);
+/* fsz_server_release for each of the `count` ids in h_ids; returns FSZ_ERR_INVALID_ARG if
+ * any id was not held (the others are released all the same). */
+fsz_status fsz_server_release_many(fsz_server s, const uint64_t* h_ids, uint64_t count,
+                                   fsz_stream stream);
+fsz_status fsz_server_get_stats(fsz_server s, fsz_server_stats* h_stats);
+/* Finishes the queued and running work, then frees the server. Outputs not yet released
+ * are freed with it. */
+fsz_status fsz_server_destroy(fsz_server s);
+/* Device-to-device copy on `stream` (for clients without a CUDA binding of their own). */
+fsz_status fsz_copy_device(void* d_dst, const void* d_src, uint64_t bytes, fsz_stream stream);
 
 /* Test hooks for failure detection (not for production use): the chunk whose global
  * index equals skip_chunk publishes no lookback flag, so its successor's bounded wait

@@ -16,10 +16,11 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_lib", "libfsz.so")
 
 OK, ERR_INVALID_ARG, ERR_ALIGN, ERR_NONFINITE, ERR_EB_TOO_SMALL = 0, 1, 2, 3, 4
-ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA, ERR_WORKSPACE = 5, 6, 7, 8, 9
+ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA, ERR_WORKSPACE, ERR_REJECTED = 5, 6, 7, 8, 9, 10
 STATUS_NAMES = {0: "FSZ_OK", 1: "FSZ_ERR_INVALID_ARG", 2: "FSZ_ERR_ALIGN", 3: "FSZ_ERR_NONFINITE",
                 4: "FSZ_ERR_EB_TOO_SMALL", 5: "FSZ_ERR_CAPACITY", 6: "FSZ_ERR_CORRUPT",
-                7: "FSZ_ERR_TIMEOUT", 8: "FSZ_ERR_CUDA", 9: "FSZ_ERR_WORKSPACE"}
+                7: "FSZ_ERR_TIMEOUT", 8: "FSZ_ERR_CUDA", 9: "FSZ_ERR_WORKSPACE",
+                10: "FSZ_ERR_REJECTED"}
 EB_ABS, EB_REL = 0, 1
 
 # Every entry point include/fsz.h declares.
@@ -28,7 +29,10 @@ EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_byt
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
            "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc",
            "fsz_graph_compress_batched", "fsz_graph_decompress_batched", "fsz_graph_launch",
-           "fsz_graph_destroy", "fsz_set_schedule", "fsz_get_schedule_limits"]
+           "fsz_graph_destroy", "fsz_set_schedule", "fsz_get_schedule_limits",
+           "fsz_server_request_cost", "fsz_server_create", "fsz_server_submit", "fsz_server_poll",
+           "fsz_server_submit_many", "fsz_server_release_many", "fsz_server_release", "fsz_server_get_stats", "fsz_server_destroy", "fsz_copy_device"]
+REQ_COMPRESS, REQ_DECOMPRESS = 0, 1
 
 
 class FszDims(ctypes.Structure):
@@ -40,6 +44,30 @@ class FszCField(ctypes.Structure):
     _fields_ = [("in_", ctypes.c_void_p), ("dims", FszDims), ("mode", ctypes.c_uint32),
                 ("reserved", ctypes.c_uint32), ("eb", ctypes.c_double), ("out", ctypes.c_void_p),
                 ("out_capacity", ctypes.c_uint64), ("out_bytes", ctypes.c_void_p)]
+
+
+class FszServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("slots", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("scan", ctypes.c_uint32), ("linger_us", ctypes.c_uint32),
+                ("max_batch_elems", ctypes.c_uint64), ("sim_service_ns", ctypes.c_uint64)]
+
+
+class FszRequest(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("kind", ctypes.c_uint32), ("mode", ctypes.c_uint32),
+                ("dims", FszDims), ("eb", ctypes.c_double), ("d_in", ctypes.c_void_p),
+                ("in_bytes", ctypes.c_uint64), ("n", ctypes.c_uint64), ("arrival_ns", ctypes.c_uint64)]
+
+
+class FszCompletion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_uint32),
+                ("batch", ctypes.c_uint64), ("d_out", ctypes.c_void_p), ("out_bytes", ctypes.c_uint64),
+                ("latency_ns", ctypes.c_uint64)]
+
+
+class FszServerStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "rejected", "batches",
+                                               "max_inflight", "max_batch_seen", "admitted_while_busy",
+                                               "budget_free", "bytes_in")]
 
 
 class FszDField(ctypes.Structure):
@@ -57,11 +85,21 @@ def _np_dtypes():
                    "offsets": [0, 8, 12, 16, 24, 32, 40, 44, 48, 56, 64, 72], "itemsize": 80})
     df = np.dtype({"names": ["in_", "in_bytes", "out", "out_capacity_elems"],
                    "formats": ["<u8", "<u8", "<u8", "<u8"], "offsets": [0, 8, 16, 24], "itemsize": 32})
+    rq = np.dtype({"names": ["id", "kind", "mode", "ndim", "dreserved", "d0", "d1", "d2", "eb",
+                             "d_in", "in_bytes", "n", "arrival_ns"],
+                   "formats": ["<u8", "<u4", "<u4", "<u4", "<u4", "<u8", "<u8", "<u8", "<f8", "<u8",
+                               "<u8", "<u8", "<u8"],
+                   "offsets": [0, 8, 12, 16, 20, 24, 32, 40, 48, 56, 64, 72, 80], "itemsize": 88})
+    cp = np.dtype({"names": ["id", "status", "batch_size", "batch", "d_out", "out_bytes",
+                             "latency_ns"],
+                   "formats": ["<u8", "<i4", "<u4", "<u8", "<u8", "<u8", "<u8"],
+                   "offsets": [0, 8, 12, 16, 24, 32, 40], "itemsize": 48})
     assert cf.itemsize == ctypes.sizeof(FszCField) and df.itemsize == ctypes.sizeof(FszDField)
-    return cf, df
+    assert rq.itemsize == ctypes.sizeof(FszRequest) and cp.itemsize == ctypes.sizeof(FszCompletion)
+    return cf, df, rq, cp
 
 
-CFIELD_NP, DFIELD_NP = _np_dtypes()
+CFIELD_NP, DFIELD_NP, REQUEST_NP, COMPLETION_NP = _np_dtypes()
 
 
 class FszError(RuntimeError):
@@ -125,6 +163,26 @@ def lib():
             L.fsz_get_schedule_limits.restype = i32
             L.fsz_version.argtypes = []
             L.fsz_version.restype = ctypes.c_char_p
+            L.fsz_server_request_cost.argtypes = [P]
+            L.fsz_server_request_cost.restype = u64
+            L.fsz_server_create.argtypes = [P, P]
+            L.fsz_server_create.restype = i32
+            L.fsz_server_submit.argtypes = [P, P]
+            L.fsz_server_submit.restype = i32
+            L.fsz_server_submit_many.argtypes = [P, P, u64]
+            L.fsz_server_submit_many.restype = i32
+            L.fsz_server_release_many.argtypes = [P, P, u64, P]
+            L.fsz_server_release_many.restype = i32
+            L.fsz_server_poll.argtypes = [P, P, u32, u64]
+            L.fsz_server_poll.restype = u32
+            L.fsz_server_release.argtypes = [P, u64, P]
+            L.fsz_server_release.restype = i32
+            L.fsz_server_get_stats.argtypes = [P, P]
+            L.fsz_server_get_stats.restype = i32
+            L.fsz_server_destroy.argtypes = [P]
+            L.fsz_server_destroy.restype = i32
+            L.fsz_copy_device.argtypes = [P, P, u64, P]
+            L.fsz_copy_device.restype = i32
             _lib = L
     return _lib
 

@@ -17,7 +17,7 @@ torch = pytest.importorskip("torch")
 def test_results_alone_equal_results_in_the_mix(fszlib):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    from paper_2607_15413_gb300.serve import COMPRESS, DECOMPRESS, GpuBackend, Request, Server
+    from paper_2607_15413_gb300.serve import COMPRESS, DECOMPRESS, Request, Server
     dev = torch.device("cuda:0")
     pool = [torch.from_numpy(inputs.sinusoids(1 << 22, seed=1)).to(dev),
             inputs.particles(1 << 22, seed=2, device="cuda"),
@@ -45,8 +45,8 @@ def test_results_alone_equal_results_in_the_mix(fszlib):
     alone_dec = [fszlib.decompress(s, n=x.numel()).clone() if s is not None else None
                  for s, (x, _, _) in zip(alone, reqs)]
     # in the mix: 60 % compress, 40 % decompress of an earlier result, from 3 client threads
-    backend = GpuBackend(n_slots=4, max_batch=16, max_elems=sum(x.numel() for x, _, _ in reqs), device=dev)
-    srv = Server(backend, budget_bytes=256 << 20, n_slots=4, max_batch=16)
+    srv = Server(budget_bytes=256 << 20, n_slots=4, max_batch=16,
+                 max_batch_elems=sum(x.numel() for x, _, _ in reqs))
     futs = [None] * len(reqs)
 
     def client(k):
@@ -67,18 +67,22 @@ def test_results_alone_equal_results_in_the_mix(fszlib):
         for t in ts:
             t.join()
         res = [f.result(timeout=60) for f in futs]
+        for i, r in enumerate(res):
+            assert r.status == status[i], (i, r.status, status[i])
+            if status[i]:
+                r.release()
+                continue
+            if i % 5 < 3:
+                assert r.nbytes == alone[i].numel()
+                assert torch.equal(r.tensor(torch.uint8), alone[i]), f"request {i}: compressed stream differs"
+            else:
+                got = r.tensor(torch.float32)
+                assert torch.equal(got.view(torch.int32), alone_dec[i].view(torch.int32)), f"request {i}"
+            r.release()
+        st = srv.stats()
     finally:
         srv.close()
-    for i, r in enumerate(res):
-        assert r.status == status[i], (i, r.status, status[i])
-        if status[i]:
-            continue
-        if i % 5 < 3:
-            assert r.nbytes == alone[i].numel()
-            assert torch.equal(r.output, alone[i]), f"request {i}: compressed stream differs"
-        else:
-            assert torch.equal(r.output.view(torch.int32), alone_dec[i].view(torch.int32)), f"request {i}"
-    assert srv.stats["completed"] == len(reqs)
-    assert srv.stats["max_inflight"] >= 2
-    assert srv.stats["admitted_while_busy"] > 0
-    assert srv.free_budget == srv.budget
+    assert st["completed"] == len(reqs)
+    assert st["max_inflight"] >= 2
+    assert st["admitted_while_busy"] > 0
+    assert st["budget_free"] == 256 << 20

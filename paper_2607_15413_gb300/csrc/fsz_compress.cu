@@ -92,6 +92,12 @@ __device__ __forceinline__ uint32_t block_cost(int R) { return (uint32_t(R) + (R
 // v = 2|l| + sign: bit 0 is the sign-map bit, bit k + 1 magnitude bit-plane k (Sec. 4.3).
 __device__ __forceinline__ uint32_t sign_mag(int l) { return (uabs32(l) << 1) | (uint32_t(l) >> 31); }
 
+// The sign-magnitude word by multiply-adds: 2|l| + s = l (2 - 4s) + s with s the sign bit.
+__device__ __forceinline__ uint32_t sign_mag_fma(int l) {
+  const int sg = int(uint32_t(l) >> 31);
+  return uint32_t(mad_s32(l, mad_s32(sg, -4, 2), sg));
+}
+
 // Compresses two tiles with one warp: lanes 0-15 take one tile and lanes 16-31 the next
 // (half = lane >> 4). Lane hl = lane & 15 owns elements 16 hl..16 hl + 15 of its tile, so
 // lanes 2g, 2g + 1 of a half own block g (Sec. 3.1: a tile is 8 blocks of 32 elements).
@@ -99,29 +105,31 @@ __device__ __forceinline__ uint32_t sign_mag(int l) { return (uabs32(l) << 1) | 
 // `hdr` are this half's; the first half's bytes go to `slot`, the second half's right
 // after them. A half with `live` false computes but stores nothing. Returns this half's
 // byte count (uniform within the half).
-__device__ __forceinline__ uint32_t compress_pair(const float* __restrict__ tile,
+__device__ __forceinline__ void load_pair(const float* __restrict__ tile, const int lane,
+                                          float (&d)[16]) {
+  const int hl = lane & 15;
+  const float4* t4 = reinterpret_cast<const float4*>(tile) + 4 * hl;
+  // Load k of lane hl reads chunk (k + 2 (hl/2 mod 2)) mod 4 of its 64 bytes, so each
+  // 128-bit phase of 8 lanes hits every bank group twice rather than two of them four
+  // times; one select stage puts the chunks back in order.
+  const int rot = (hl >> 1) & 1;
+  float4 u[4], q[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) u[k] = t4[(k + 2 * rot) & 3];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) q[c] = rot ? u[(c + 2) & 3] : u[c];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    d[4 * k] = q[k].x; d[4 * k + 1] = q[k].y; d[4 * k + 2] = q[k].z; d[4 * k + 3] = q[k].w;
+  }
+}
+
+__device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
                                                   uint8_t* __restrict__ slot,
                                                   uint8_t* __restrict__ hdr, const float r,
                                                   const int lane, const bool live) {
   constexpr uint32_t FULL = 0xffffffffu;
   const int hl = lane & 15;
-  const float4* t4 = reinterpret_cast<const float4*>(tile) + 4 * hl;
-  float d[16];
-  // Load k of lane hl reads chunk (k + hl/2) mod 4 of its 64 bytes, so the 8 lanes of each
-  // 128-bit phase hit 8 different bank groups; two select stages put the chunks in order.
-  const int rot = (hl >> 1) & 3;
-  float4 q[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) q[k] = t4[(k + rot) & 3];
-  float4 u[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) u[c] = (rot & 1) ? q[(c + 3) & 3] : q[c];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) q[c] = (rot & 2) ? u[(c + 2) & 3] : u[c];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    d[4 * k] = q[k].x; d[4 * k + 1] = q[k].y; d[4 * k + 2] = q[k].z; d[4 * k + 3] = q[k].w;
-  }
   // Step 1, quantize (Sec. 4.2.2): t = fl(d r) then the nearest integer, ties to even.
   // Y holds q + bits(M); differences of Y are differences of q.
   int Y[16];
@@ -190,10 +198,10 @@ __device__ __forceinline__ uint32_t compress_pair(const float* __restrict__ tile
   // the half holds the tile costs C = sum of S_b. Centring changes block 0 only: its cost
   // deltas and rates come from lane 0; variants 3 and 4 pay 4 bytes for mu (step 2).
   const uint32_t pk = block_cost(R1) | (block_cost(R2) << 16);
-  uint32_t pinc = pk, tmp;
-  tmp = __shfl_up_sync(FULL, pinc, 2, 16); if (hl >= 2) pinc += tmp;
-  tmp = __shfl_up_sync(FULL, pinc, 4, 16); if (hl >= 4) pinc += tmp;
-  tmp = __shfl_up_sync(FULL, pinc, 8, 16); if (hl >= 8) pinc += tmp;
+  uint32_t pinc = pk;
+  pinc = scan_step_up<16>(pinc, 2);
+  pinc = scan_step_up<16>(pinc, 4);
+  pinc = scan_step_up<16>(pinc, 8);
   const uint32_t ptot = __shfl_sync(FULL, pinc, 15, 16);
   const int C1 = int(ptot & 0xffffu), C2 = int(ptot >> 16);
   uint32_t bc = (block_cost(R1c) - block_cost(R1) + 1024u) |
@@ -225,9 +233,12 @@ __device__ __forceinline__ uint32_t compress_pair(const float* __restrict__ tile
   // Step 5: residuals of the selected variant as sign-magnitude words v = 2|l| + sign,
   // so that bit 0 is the sign map and bit k + 1 is magnitude bit-plane k (Sec. 4.3). The
   // halves may select different variants: select per element rather than branch.
+  // The selected residual is l1_i + m l1_{i-1} with m = 0 (LZ1) or -1 (LZ2).
+  const int m = second ? -1 : 0;
   uint32_t vv[16];
+  vv[0] = sign_mag_fma(mad_s32(prevL, m, l1[0]));
 #pragma unroll
-  for (int i = 0; i < 16; ++i) vv[i] = sign_mag(second ? l2[i] : l1[i]);
+  for (int i = 1; i < 16; ++i) vv[i] = sign_mag_fma(mad_s32(l1[i - 1], m, l1[i]));
   const bool fix = centred && hl == 0;
   vv[0] = fix ? sign_mag(q0 - mu) : vv[0];
   vv[1] = (fix && second) ? sign_mag(l2[1] + mu) : vv[1];
@@ -242,6 +253,7 @@ __device__ __forceinline__ uint32_t compress_pair(const float* __restrict__ tile
   uint8_t* const blk = my_slot + off;
   if (fix && live) *reinterpret_cast<float*>(my_slot) = __int2float_rn(mu);
 
+  const int nwords = live && Rg > 0 ? Rg + 1 : 0;  // block g's words: sign map + Rg planes
   const int Rmax = int(__reduce_max_sync(FULL, live ? uint32_t(Rg) : 0u));
   if (Rmax > 0) {
     const int nch = (Rmax + 8) >> 3;
@@ -273,7 +285,7 @@ __device__ __forceinline__ uint32_t compress_pair(const float* __restrict__ tile
         const int wb = 8 * c + 4 * t2;
 #pragma unroll
         for (int b = 0; b < 4; ++b)
-          if (live && Rg > 0 && wb + b <= Rg) reinterpret_cast<uint32_t*>(blk)[wb + b] = w[b];
+          if (wb + b < nwords) reinterpret_cast<uint32_t*>(blk)[wb + b] = w[b];
       }
     }
   }
@@ -490,6 +502,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
     const int ntiles = int(ci.ntiles);
     const bool end = (c == kNone);
     const bool last_half = end || (h + 1 == (ntiles > kStageTiles ? 2u : 1u));
+    bool released = false;
     if (!end && (flags & kInfoOk)) {
       const float r = ci.r;
       const uint32_t e_h = h * kStageElems;
@@ -516,6 +529,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
           }
         }
         __syncwarp();
+        float d[16];
+        load_pair(tile, lane, d);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[s]);  // the pair is in registers
+        released = true;
         // room for a worst-case pair, contiguous in the ring
         constexpr uint32_t kPair = 2 * kMaxTileBytes;
         uint32_t pos = head % kRingBytes;
@@ -532,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
         if (!ok_run) break;
         head += skip;
         pos = head % kRingBytes;
-        const uint32_t nb = compress_pair(tile, ring + pos, hdr_out + 8 * tl, r, lane, live);
+        const uint32_t nb = compress_pair(d, ring + pos, hdr_out + 8 * tl, r, lane, live);
         const uint32_t na = __shfl_sync(0xffffffffu, nb, 0);
         const uint32_t nbb = __shfl_sync(0xffffffffu, nb, 16);
         const bool second_live = ta + 1 < t_end;
@@ -543,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       if (!ok_run) break;
     }
     __syncwarp();
-    if (!end && lane == 0) mbar_arrive(&S.empty[s]);  // done reading the stage
+    if (!end && !released && lane == 0) mbar_arrive(&S.empty[s]);  // done reading the stage
     if (last_half) {
       // This warp is through the chunk: the last warp to get here scans the chunk's tile
       // sizes and publishes its aggregate (step 4, thread and warp levels).

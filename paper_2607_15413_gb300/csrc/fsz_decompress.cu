@@ -113,14 +113,15 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
   // d4: decode and bit-unshuffle: words -> per-lane plane bytes -> 8x8 transpose.
   uint32_t vv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   const int Rmax = int(__reduce_max_sync(FULL, uint32_t(Rg)));
+  const int nwords = Rg > 0 ? Rg + 1 : 0;  // block g's words: sign map + Rg planes
   if (Rmax > 0) {
     const int nch = (Rmax + 8) >> 3;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       if (c < nch) {
         const int w0 = 8 * c + t, w1 = w0 + 4;
-        uint32_t lo = (Rg > 0 && w0 <= Rg) ? reinterpret_cast<const uint32_t*>(blk)[w0] : 0u;
-        uint32_t hi = (Rg > 0 && w1 <= Rg) ? reinterpret_cast<const uint32_t*>(blk)[w1] : 0u;
+        uint32_t lo = w0 < nwords ? reinterpret_cast<const uint32_t*>(blk)[w0] : 0u;
+        uint32_t hi = w1 < nwords ? reinterpret_cast<const uint32_t*>(blk)[w1] : 0u;
         lo = transpose4x4_bytes(lo, t);
         hi = transpose4x4_bytes(hi, t);
         transpose8x8(lo, hi);
@@ -141,8 +142,7 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
   uint32_t x[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const uint32_t m = vv[i] >> 1;
-    x[i] = (vv[i] & 1u) ? 0u - m : m;
+    x[i] = uint32_t(mad_s32(int(vv[i] >> 1), mad_s32(int(vv[i] & 1u), -2, 1), 0));
   }
   // d5: inverse prediction. With zero predecessors, LZ1's q_i = l_i + q_{i-1} is an
   // inclusive prefix sum over the tile; LZ2's q_i = l_i + 2 q_{i-1} - q_{i-2} is the prefix
@@ -153,10 +153,7 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
     const uint32_t tot = v[7];
     uint32_t inc = tot;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(FULL, inc, o);
-      if (lane >= o) inc += y;
-    }
+    for (int o = 1; o < 32; o <<= 1) inc = scan_step_up(inc, o);
     const uint32_t ex = inc - tot;
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] += ex;

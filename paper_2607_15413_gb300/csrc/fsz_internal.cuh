@@ -262,15 +262,43 @@ __device__ __forceinline__ uint32_t uabs32(int32_t v) {
   return v < 0 ? 0u - static_cast<uint32_t>(v) : static_cast<uint32_t>(v);
 }
 
+// a * b + c as an integer multiply-add. The kernels' integer-logic pipe is their busiest
+// and the multiply-add pipe has room, so shifts and selections by a 0/-1 factor that sit
+// on the hot path are written this way.
+__device__ __forceinline__ int mad_s32(int a, int b, int c) {
+  int d;
+  asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+// x << k as a multiply.
+__device__ __forceinline__ uint32_t shl_fma(uint32_t x, int k) {
+  return uint32_t(mad_s32(int(x), 1 << k, 0));
+}
+
 // 8x8 bit-matrix transpose of the 64-bit word hi:lo: bit 8r + c <-> bit 8c + r.
-// Three delta swaps (Hacker's Delight, "transposing a bit matrix"), on 32-bit halves.
+// Three delta swaps (Hacker's Delight, "transposing a bit matrix"), on 32-bit halves; the
+// left shifts are multiplies (shl_fma).
 __device__ __forceinline__ void transpose8x8(uint32_t& lo, uint32_t& hi) {
   uint32_t t;
-  t = (lo ^ (lo >> 7)) & 0x00AA00AAu; lo = lo ^ t ^ (t << 7);
-  t = (hi ^ (hi >> 7)) & 0x00AA00AAu; hi = hi ^ t ^ (t << 7);
-  t = (lo ^ (lo >> 14)) & 0x0000CCCCu; lo = lo ^ t ^ (t << 14);
-  t = (hi ^ (hi >> 14)) & 0x0000CCCCu; hi = hi ^ t ^ (t << 14);
-  t = (lo ^ (hi << 4)) & 0xF0F0F0F0u; lo ^= t; hi ^= (t >> 4);
+  t = (lo ^ (lo >> 7)) & 0x00AA00AAu; lo = lo ^ t ^ shl_fma(t, 7);
+  t = (hi ^ (hi >> 7)) & 0x00AA00AAu; hi = hi ^ t ^ shl_fma(t, 7);
+  t = (lo ^ (lo >> 14)) & 0x0000CCCCu; lo = lo ^ t ^ shl_fma(t, 14);
+  t = (hi ^ (hi >> 14)) & 0x0000CCCCu; hi = hi ^ t ^ shl_fma(t, 14);
+  t = (lo ^ shl_fma(hi, 4)) & 0xF0F0F0F0u; lo ^= t; hi ^= (t >> 4);
+}
+
+// One step of an inclusive scan: v += v of lane - o, where that lane exists within the
+// segment of `width` lanes. The shuffle's own in-range predicate guards the add, so no
+// lane-index compare is needed.
+template <int kWidth = 32>
+__device__ __forceinline__ uint32_t scan_step_up(uint32_t v, int o) {
+  asm("{\n\t.reg .pred p;\n\t.reg .b32 y;\n\t"
+      "shfl.sync.up.b32 y|p, %0, %1, %2, 0xffffffff;\n\t"
+      "@p add.u32 %0, %0, y;\n\t}"
+      : "+r"(v)
+      : "r"(o), "n"((32 - kWidth) << 8));
+  return v;
 }
 
 // 4x4 byte transpose across the 4 lanes of a group (t = lane & 3): afterwards byte k of

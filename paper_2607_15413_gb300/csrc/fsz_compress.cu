@@ -472,8 +472,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
     const int s = int(u % kStages);
     const uint32_t par = (u / kStages) & 1u;
     // Wait for the stage, placing resolved chunks meanwhile (the producer may be waiting
-    // for this warp to free a set).
-    {
+    // for this warp to free a set). The stage is usually full already: one test, no timer.
+    if (!mbar_test(&S.full[s], par)) {
       const uint64_t deadline = globaltimer_ns() + wait_ns;
       bool got = false;
       while (!got) {

@@ -24,7 +24,7 @@ constexpr int kDecodeWarps = 8;
 constexpr int kHeaderWarp = kDecodeWarps;
 constexpr int kLoaderWarp = kDecodeWarps + 1;
 constexpr int kThreads = (kDecodeWarps + 2) * 32;
-constexpr int kStages = 3;   // payload stages
+constexpr int kStages = 2;   // payload stages
 constexpr int kRecs = 6;     // chunk records in flight (fetched .. decoded)
 constexpr int kPayloadBytes = kDChunkTiles * kMaxDecTileBytes + 32;
 static_assert(kDChunkTiles <= 32, "one lane per tile in the chunk scan");
@@ -168,7 +168,7 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
   return __all_sync(FULL, good);
 }
 
-__global__ void __launch_bounds__(kThreads, 3) fsz_decompress_kernel(KernelArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   DecompressSmem& S = *reinterpret_cast<DecompressSmem*>(smem_raw);
   constexpr uint32_t FULL = 0xffffffffu;

@@ -22,6 +22,11 @@ _LIB = os.path.join(_LIBDIR, "libfsz_oracle.so")
 
 ABS, REL = 0, 1
 LZ1, LZ2, LZ1C, LZ2C = 0, 1, 2, 3
+# Features switched off (Sec. 6.4 ablation); 0 is the full method.
+OFF_CROSS, OFF_CENTER, OFF_LZ2 = 1, 2, 4
+# The ablation's cumulative steps: Base (LZ1, independent blocks), +Cross, +Cent., +LZ2.
+ABLATION = (("base", OFF_CROSS | OFF_CENTER | OFF_LZ2), ("+cross", OFF_CENTER | OFF_LZ2),
+            ("+center", OFF_LZ2), ("+lz2", 0))
 OK, ERR_INVALID_ARG, ERR_NONFINITE, ERR_EB_TOO_SMALL, ERR_CAPACITY, ERR_CORRUPT = 0, 1, 3, 4, 5, 6
 
 # -ffp-contract=off keeps every float32 multiply and add a separate IEEE
@@ -84,6 +89,18 @@ def lib():
             L.fszo_compress_tiles.argtypes = [P, u64, f32, u64, u64, P, P, u64, P]
             L.fszo_decompress.argtypes = [P, u64, P, u64, P]
             L.fszo_decompress_q.argtypes = [P, u64, P, u64, P]
+            L.fszo_features_valid.argtypes = [u32]
+            L.fszo_tile_residuals_f.argtypes = [P, i32, ctypes.c_int, u32, P]
+            L.fszo_tile_residuals_f.restype = None
+            L.fszo_tile_costs_single_pass_f.argtypes = [P, i32, u32, P, P]
+            L.fszo_tile_costs_single_pass_f.restype = None
+            L.fszo_tile_costs_four_pass_f.argtypes = [P, i32, u32, P, P]
+            L.fszo_tile_costs_four_pass_f.restype = None
+            L.fszo_select_f.argtypes = [P, u32]
+            L.fszo_compress_f.argtypes = [P, u32, P, ctypes.c_int, f64, u32, P, u64, P,
+                                          ctypes.c_int]
+            L.fszo_compress_tiles_f.argtypes = [P, u64, f32, u64, u64, u32, P, P, u64, P]
+            L.fszo_read_preamble_f.argtypes = [P, u64, P, P, P, P, P, P, P]
             _lib = L
     return _lib
 
@@ -130,12 +147,16 @@ def tile_mu(d256: np.ndarray, r: float) -> int:
     return lib().fszo_tile_mu(_ptr(d), r)
 
 
-def tile_residuals(q256: np.ndarray, mu: int, variant: int) -> np.ndarray:
+def tile_residuals(q256: np.ndarray, mu: int, variant: int, features_off: int = 0) -> np.ndarray:
     q = np.ascontiguousarray(q256, dtype=np.int32)
     assert q.size == 256
     out = np.zeros(256, np.int32)
-    lib().fszo_tile_residuals(_ptr(q), mu, variant, _ptr(out))
+    lib().fszo_tile_residuals_f(_ptr(q), mu, variant, features_off, _ptr(out))
     return out
+
+
+def features_valid(features_off: int) -> bool:
+    return bool(lib().fszo_features_valid(features_off))
 
 
 def rate(maxabs: int) -> int:
@@ -146,26 +167,27 @@ def block_cost(r: int) -> int:
     return lib().fszo_block_cost(r)
 
 
-def tile_costs(q256: np.ndarray, mu: int, four_pass: bool = False):
+def tile_costs(q256: np.ndarray, mu: int, four_pass: bool = False, features_off: int = 0):
     q = np.ascontiguousarray(q256, dtype=np.int32)
     assert q.size == 256
     C = np.zeros(4, np.uint32)
     rates = np.zeros(32, np.uint8)
-    fn = lib().fszo_tile_costs_four_pass if four_pass else lib().fszo_tile_costs_single_pass
-    fn(_ptr(q), mu, _ptr(C), _ptr(rates))
+    fn = lib().fszo_tile_costs_four_pass_f if four_pass else lib().fszo_tile_costs_single_pass_f
+    fn(_ptr(q), mu, features_off, _ptr(C), _ptr(rates))
     return C, rates.reshape(4, 8)
 
 
-def select(C: np.ndarray) -> int:
+def select(C: np.ndarray, features_off: int = 0) -> int:
     c = np.ascontiguousarray(C, dtype=np.uint32)
-    return lib().fszo_select(_ptr(c))
+    return lib().fszo_select_f(_ptr(c), features_off)
 
 
 def compress_bound(n: int) -> int:
     return lib().fszo_compress_bound(n)
 
 
-def compress(d: np.ndarray, eb: float, mode: int = REL, dims=None, force_variant: int = -1) -> bytes:
+def compress(d: np.ndarray, eb: float, mode: int = REL, dims=None, force_variant: int = -1,
+             features_off: int = 0) -> bytes:
     d = np.ascontiguousarray(d, dtype=np.float32)
     if dims is None:
         dims = d.shape if d.ndim >= 1 else (d.size,)
@@ -174,22 +196,22 @@ def compress(d: np.ndarray, eb: float, mode: int = REL, dims=None, force_variant
     cap = compress_bound(d.size)
     out = np.zeros(cap, np.uint8)
     nb = ctypes.c_uint64()
-    st = lib().fszo_compress(_ptr(d), len(dims), _ptr(dims_arr), mode, eb, _ptr(out), cap,
-                             ctypes.byref(nb), force_variant)
+    st = lib().fszo_compress_f(_ptr(d), len(dims), _ptr(dims_arr), mode, eb, features_off,
+                               _ptr(out), cap, ctypes.byref(nb), force_variant)
     if st != OK:
         raise OracleError(st, "compress")
     return out[: nb.value].tobytes()
 
 
-def compress_tiles(d: np.ndarray, r: float, t0: int, t1: int):
+def compress_tiles(d: np.ndarray, r: float, t0: int, t1: int, features_off: int = 0):
     """Headers (8 bytes per tile) and data of tiles [t0, t1) of field d, given r = 1/s."""
     d = np.ascontiguousarray(d, dtype=np.float32).ravel()
     hdr = np.zeros(8 * max(t1 - t0, 1), np.uint8)
     cap = 708 * max(t1 - t0, 1)
     data = np.zeros(cap, np.uint8)
     nb = ctypes.c_uint64()
-    st = lib().fszo_compress_tiles(_ptr(d), d.size, r, t0, t1, _ptr(hdr), _ptr(data), cap,
-                                   ctypes.byref(nb))
+    st = lib().fszo_compress_tiles_f(_ptr(d), d.size, r, t0, t1, features_off, _ptr(hdr),
+                                     _ptr(data), cap, ctypes.byref(nb))
     if st != OK:
         raise OracleError(st, "compress_tiles")
     return hdr[: 8 * (t1 - t0)].tobytes(), data[: nb.value].tobytes()
@@ -200,12 +222,14 @@ def read_preamble(stream: bytes):
     n, ndim, s, db = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_float(), ctypes.c_uint64()
     dims = np.zeros(3, np.uint64)
     eb = ctypes.c_double()
-    st = lib().fszo_read_preamble(_ptr(buf), buf.size, ctypes.byref(n), ctypes.byref(ndim),
-                                  _ptr(dims), ctypes.byref(eb), ctypes.byref(s), ctypes.byref(db))
+    off = ctypes.c_uint32()
+    st = lib().fszo_read_preamble_f(_ptr(buf), buf.size, ctypes.byref(n), ctypes.byref(ndim),
+                                    _ptr(dims), ctypes.byref(eb), ctypes.byref(s),
+                                    ctypes.byref(db), ctypes.byref(off))
     if st != OK:
         raise OracleError(st, "read_preamble")
     return dict(n=n.value, ndim=ndim.value, dims=tuple(int(x) for x in dims[: ndim.value]),
-                eb=eb.value, s=s.value, data_bytes=db.value)
+                eb=eb.value, s=s.value, data_bytes=db.value, features_off=off.value)
 
 
 def decompress(stream: bytes, q: bool = False) -> np.ndarray:

@@ -7,6 +7,7 @@
 #include "fsz_oracle.h"
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <vector>
 
@@ -152,10 +153,19 @@ int32_t fszo_tile_mu(const float d[256], float r) {
 // element(s) lack predecessors, which are read as zero (reading: zero-initialised
 // state, so l1_0 = qh_0, l2_0 = qh_0 and l2_1 = qh_1 - 2 qh_0).
 void fszo_tile_residuals(const int32_t q[256], int32_t mu, int variant, int32_t l[256]) {
+  fszo_tile_residuals_f(q, mu, variant, 0, l);
+}
+
+// The same with features switched off (Sec. 6.4 ablation). Without the cross-block state
+// (FSZO_OFF_CROSS) every block restarts from zero predecessors, as its first element(s)
+// would at a tile start (Sec. 2, C1: "restart prediction state at every boundary").
+void fszo_tile_residuals_f(const int32_t q[256], int32_t mu, int variant, uint32_t off,
+                           int32_t l[256]) {
   const bool centred = (variant == FSZO_LZ1C || variant == FSZO_LZ2C);
   const bool second = (variant == FSZO_LZ2 || variant == FSZO_LZ2C);
   int32_t prev1 = 0, prev2 = 0;  // qh_{i-1}, qh_{i-2}
   for (int i = 0; i < kTile; ++i) {
+    if ((off & FSZO_OFF_CROSS) && i % kBlock == 0) prev1 = prev2 = 0;
     int32_t qh = centred ? wsub(q[i], mu) : q[i];
     if (!second) {
       l[i] = wsub(qh, prev1);
@@ -178,9 +188,14 @@ uint32_t fszo_rate(uint32_t maxabs) {
 uint32_t fszo_block_cost(uint32_t rate) { return rate == 0 ? 0u : 4u + 4u * rate; }
 
 void fszo_tile_costs_four_pass(const int32_t q[256], int32_t mu, uint32_t C[4], uint8_t rates[32]) {
+  fszo_tile_costs_four_pass_f(q, mu, 0, C, rates);
+}
+
+void fszo_tile_costs_four_pass_f(const int32_t q[256], int32_t mu, uint32_t off, uint32_t C[4],
+                                 uint8_t rates[32]) {
   int32_t l[kTile];
   for (int v = 0; v < 4; ++v) {
-    fszo_tile_residuals(q, mu, v, l);
+    fszo_tile_residuals_f(q, mu, v, off, l);
     uint32_t cost = (v == FSZO_LZ1C || v == FSZO_LZ2C) ? 4u : 0u;  // the 4-byte mean
     for (int b = 0; b < kBlocksPerTile; ++b) {
       uint32_t m = 0;
@@ -199,6 +214,39 @@ void fszo_tile_costs_four_pass(const int32_t q[256], int32_t mu, uint32_t C[4], 
 // keeps block 0's maxima over i >= k, and the centred block-0 rate is that maximum
 // joined with the centred boundary residuals, computed after the loop.
 void fszo_tile_costs_single_pass(const int32_t q[256], int32_t mu, uint32_t C[4], uint8_t rates[32]) {
+  fszo_tile_costs_single_pass_f(q, mu, 0, C, rates);
+}
+
+// With features switched off: without the cross-block state the loop restarts at every
+// block and only LZ1 and LZ2 are costed (centring needs the carried state: its costs are
+// left at UINT32_MAX and its rates at 0).
+void fszo_tile_costs_single_pass_f(const int32_t q[256], int32_t mu, uint32_t off, uint32_t C[4],
+                                   uint8_t rates[32]) {
+  if (off & FSZO_OFF_CROSS) {
+    int32_t prev1 = 0, prev2 = 0;
+    C[FSZO_LZ1] = C[FSZO_LZ2] = 0;
+    C[FSZO_LZ1C] = C[FSZO_LZ2C] = UINT32_MAX;
+    for (int b = 0; b < kBlocksPerTile; ++b) {
+      uint32_t M1 = 0, M2 = 0;
+      prev1 = prev2 = 0;
+      for (int j = 0; j < kBlock; ++j) {
+        int32_t qi = q[b * kBlock + j];
+        uint32_t a1 = uabs(wsub(qi, prev1));
+        uint32_t a2 = uabs(wadd(wsub(qi, wadd(prev1, prev1)), prev2));
+        if (a1 > M1) M1 = a1;
+        if (a2 > M2) M2 = a2;
+        prev2 = prev1;
+        prev1 = qi;
+      }
+      uint32_t r1 = fszo_rate(M1), r2 = fszo_rate(M2);
+      rates[FSZO_LZ1 * 8 + b] = uint8_t(r1);
+      rates[FSZO_LZ2 * 8 + b] = uint8_t(r2);
+      rates[FSZO_LZ1C * 8 + b] = rates[FSZO_LZ2C * 8 + b] = 0;
+      C[FSZO_LZ1] += fszo_block_cost(r1);
+      C[FSZO_LZ2] += fszo_block_cost(r2);
+    }
+    return;
+  }
   uint32_t M1[8] = {0}, M2[8] = {0};
   uint32_t M1_rest0 = 0, M2_rest0 = 0;  // block 0 over i >= 1 (LZ1) and i >= 2 (LZ2)
   int32_t prev1 = 0, prev2 = 0;
@@ -243,11 +291,24 @@ void fszo_tile_costs_single_pass(const int32_t q[256], int32_t mu, uint32_t C[4]
 // Reading: the first strict minimum in the listed order, so ties go to LZ1 over LZ2
 // and centring is taken only when strictly cheaper ("enabled only when its 4-byte
 // cost for mu is outweighed by the savings", Sec. 4.2.2).
-int fszo_select(const uint32_t C[4]) {
+int fszo_select(const uint32_t C[4]) { return fszo_select_f(C, 0); }
+
+// Among the variants whose features are on: LZ2 needs FSZO_OFF_LZ2 clear, the centred
+// ones FSZO_OFF_CENTER clear (and LZ2C both).
+int fszo_select_f(const uint32_t C[4], uint32_t off) {
+  const bool on[4] = {true, !(off & FSZO_OFF_LZ2), !(off & FSZO_OFF_CENTER),
+                      !(off & FSZO_OFF_LZ2) && !(off & FSZO_OFF_CENTER)};
   int best = 0;
   for (int v = 1; v < 4; ++v)
-    if (C[v] < C[best]) best = v;
+    if (on[v] && C[v] < C[best]) best = v;
   return best;
+}
+
+int fszo_features_valid(uint32_t off) {
+  if (off & ~uint32_t(FSZO_OFF_CROSS | FSZO_OFF_CENTER | FSZO_OFF_LZ2)) return 0;
+  // centring is defined on the carried state (Eq. 4): off with it
+  if ((off & FSZO_OFF_CROSS) && !(off & FSZO_OFF_CENTER)) return 0;
+  return 1;
 }
 
 uint64_t fszo_compress_bound(uint64_t n) {
@@ -261,7 +322,7 @@ namespace {
 
 // Steps 1-5 of Sec. 3.1 for one tile: quantize, tile mean, four-way costs, select, then the
 // 8 rate-header bytes and the tile's data appended to `data`.
-void encode_tile(const float dt[256], float r, int force_variant, uint8_t header[8],
+void encode_tile(const float dt[256], float r, int force_variant, uint32_t off, uint8_t header[8],
                  std::vector<uint8_t>& data) {
   int32_t q[kTile], l[kTile];
   // Step 1: quantize (Sec. 3.1, Sec. 4.2.2).
@@ -270,8 +331,8 @@ void encode_tile(const float dt[256], float r, int force_variant, uint8_t header
   // Steps 2-3: four-way evaluation and adaptive select.
   uint32_t C[4];
   uint8_t rates[32];
-  fszo_tile_costs_single_pass(q, mu, C, rates);
-  const int v = force_variant >= 0 ? force_variant : fszo_select(C);
+  fszo_tile_costs_single_pass_f(q, mu, off, C, rates);
+  const int v = force_variant >= 0 ? force_variant : fszo_select_f(C, off);
   const bool centred = (v == FSZO_LZ1C || v == FSZO_LZ2C);
   const bool second = (v == FSZO_LZ2 || v == FSZO_LZ2C);
   // Rate header (Sec. 3.1 "Compressed format"): block 0 carries bit 7 = LZ order
@@ -279,7 +340,7 @@ void encode_tile(const float dt[256], float r, int force_variant, uint8_t header
   for (int b = 0; b < kBlocksPerTile; ++b) header[b] = rates[v * 8 + b];
   header[0] = uint8_t(header[0] | (second ? 0x80 : 0) | (centred ? 0x40 : 0));
   // Step 5: encode with the selected variant.
-  fszo_tile_residuals(q, mu, v, l);
+  fszo_tile_residuals_f(q, mu, v, off, l);
   if (centred) {
     // Tile mean: a 4-byte float stored inline, first in the tile's data (reading
     // of "stored inline"); it holds the integer mu exactly.
@@ -321,12 +382,18 @@ extern "C" {
 int fszo_compress_tiles(const float* d, uint64_t n, float r, uint64_t t0, uint64_t t1,
                         uint8_t* header_out, uint8_t* data_out, uint64_t data_cap,
                         uint64_t* data_bytes) {
-  if (t1 < t0 || t1 > tiles_of(n)) return FSZO_ERR_INVALID_ARG;
+  return fszo_compress_tiles_f(d, n, r, t0, t1, 0, header_out, data_out, data_cap, data_bytes);
+}
+
+int fszo_compress_tiles_f(const float* d, uint64_t n, float r, uint64_t t0, uint64_t t1,
+                          uint32_t off, uint8_t* header_out, uint8_t* data_out,
+                          uint64_t data_cap, uint64_t* data_bytes) {
+  if (t1 < t0 || t1 > tiles_of(n) || !fszo_features_valid(off)) return FSZO_ERR_INVALID_ARG;
   std::vector<uint8_t> data;
   float dt[kTile];
   for (uint64_t t = t0; t < t1; ++t) {
     load_tile(d, n, t, dt);
-    encode_tile(dt, r, -1, header_out + 8 * (t - t0), data);
+    encode_tile(dt, r, -1, off, header_out + 8 * (t - t0), data);
   }
   if (data_bytes) *data_bytes = data.size();
   if (data.size() > data_cap) return FSZO_ERR_CAPACITY;
@@ -336,8 +403,21 @@ int fszo_compress_tiles(const float* d, uint64_t n, float r, uint64_t t0, uint64
 
 int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode, double eb_req,
                   uint8_t* out, uint64_t out_capacity, uint64_t* out_bytes, int force_variant) {
+  return fszo_compress_f(d, ndim, dims, mode, eb_req, 0, out, out_capacity, out_bytes,
+                         force_variant);
+}
+
+int fszo_compress_f(const float* d, uint32_t ndim, const uint64_t* dims, int mode, double eb_req,
+                    uint32_t off, uint8_t* out, uint64_t out_capacity, uint64_t* out_bytes,
+                    int force_variant) {
   if (ndim < 1 || ndim > 3 || dims == nullptr) return FSZO_ERR_INVALID_ARG;
   if (force_variant < -1 || force_variant > 3) return FSZO_ERR_INVALID_ARG;
+  if (!fszo_features_valid(off)) return FSZO_ERR_INVALID_ARG;
+  if (force_variant >= 0) {  // a forced variant must be one whose features are on
+    if ((force_variant == FSZO_LZ2 || force_variant == FSZO_LZ2C) && (off & FSZO_OFF_LZ2))
+      return FSZO_ERR_INVALID_ARG;
+    if (force_variant >= FSZO_LZ1C && (off & FSZO_OFF_CENTER)) return FSZO_ERR_INVALID_ARG;
+  }
   uint64_t n = 1;
   for (uint32_t k = 0; k < ndim; ++k) {
     if (dims[k] != 0 && n > kMaxElems / dims[k]) return FSZO_ERR_INVALID_ARG;
@@ -358,7 +438,7 @@ int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode,
   float dt[kTile];
   for (uint64_t t = 0; t < T; ++t) {
     load_tile(d, n, t, dt);
-    encode_tile(dt, p.r, force_variant, header.data() + 8 * t, data);
+    encode_tile(dt, p.r, force_variant, off, header.data() + 8 * t, data);
   }
   const uint64_t total = kPreamble + 8 * T + uint64_t(data.size());
   if (out_bytes) *out_bytes = total;
@@ -377,7 +457,7 @@ int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode,
   uint32_t sbits;
   std::memcpy(&sbits, &p.s, 4);
   put_u32(out + 48, sbits);
-  put_u32(out + 52, 0);
+  put_u32(out + 52, off);  // features switched off (0: the full method)
   put_u64(out + 56, uint64_t(data.size()));
   if (T) std::memcpy(out + kPreamble, header.data(), header.size());
   if (!data.empty()) std::memcpy(out + kPreamble + 8 * T, data.data(), data.size());
@@ -386,6 +466,12 @@ int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode,
 
 int fszo_read_preamble(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint32_t* ndim,
                        uint64_t dims[3], double* eb_req, float* s, uint64_t* data_bytes) {
+  return fszo_read_preamble_f(in, in_bytes, n, ndim, dims, eb_req, s, data_bytes, nullptr);
+}
+
+int fszo_read_preamble_f(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint32_t* ndim,
+                         uint64_t dims[3], double* eb_req, float* s, uint64_t* data_bytes,
+                         uint32_t* features_off) {
   if (in == nullptr || in_bytes < kPreamble) return FSZO_ERR_CORRUPT;
   if (in[0] != 'F' || in[1] != 'S' || in[2] != 'Z' || in[3] != '1') return FSZO_ERR_CORRUPT;
   if (get_u16(in + 4) != 1) return FSZO_ERR_CORRUPT;
@@ -405,7 +491,8 @@ int fszo_read_preamble(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint32
   uint32_t sbits = get_u32(in + 48); float sv; std::memcpy(&sv, &sbits, 4);
   if (!(eb > 0.0) || !std::isfinite(eb)) return FSZO_ERR_CORRUPT;
   if (!(sv >= std::ldexp(1.0f, -99)) || !std::isfinite(sv)) return FSZO_ERR_CORRUPT;
-  if (get_u32(in + 52) != 0) return FSZO_ERR_CORRUPT;
+  const uint32_t off = get_u32(in + 52);
+  if (!fszo_features_valid(off)) return FSZO_ERR_CORRUPT;
   uint64_t db = get_u64(in + 56);
   uint64_t T = tiles_of(nn);
   if (in_bytes - kPreamble < 8 * T) return FSZO_ERR_CORRUPT;
@@ -415,6 +502,7 @@ int fszo_read_preamble(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint32
   if (eb_req) *eb_req = eb;
   if (s) *s = sv;
   if (data_bytes) *data_bytes = db;
+  if (features_off) *features_off = off;
   return FSZO_OK;
 }
 
@@ -423,8 +511,8 @@ namespace {
 // Decompression steps d1-d5 (Sec. 3.1 "Decompression"), writing the integers q.
 int decode_to_q(const uint8_t* in, uint64_t in_bytes, std::vector<int32_t>& qout, uint64_t cap,
                 uint64_t* n_out, float* s_out) {
-  uint64_t n, db; uint32_t nd; uint64_t dims[3]; double eb; float s;
-  int st = fszo_read_preamble(in, in_bytes, &n, &nd, dims, &eb, &s, &db);
+  uint64_t n, db; uint32_t nd; uint64_t dims[3]; double eb; float s; uint32_t feat_off;
+  int st = fszo_read_preamble_f(in, in_bytes, &n, &nd, dims, &eb, &s, &db, &feat_off);
   if (st != FSZO_OK) return st;
   if (n > cap) return FSZO_ERR_CAPACITY;
   const uint64_t T = tiles_of(n);
@@ -435,6 +523,9 @@ int decode_to_q(const uint8_t* in, uint64_t in_bytes, std::vector<int32_t>& qout
   for (uint64_t t = 0; t < T; ++t) {
     const uint8_t* h = header + 8 * t;
     if (h[0] & 0x20) return FSZO_ERR_CORRUPT;  // bit 5 of block 0 is unused
+    // a tile may not use a feature the stream has switched off
+    if ((h[0] & 0x80) && (feat_off & FSZO_OFF_LZ2)) return FSZO_ERR_CORRUPT;
+    if ((h[0] & 0x40) && (feat_off & FSZO_OFF_CENTER)) return FSZO_ERR_CORRUPT;
     uint64_t bytes = (h[0] & 0x40) ? 4 : 0;
     for (int b = 0; b < kBlocksPerTile; ++b) {
       if (b > 0 && (h[b] & 0xE0)) return FSZO_ERR_CORRUPT;  // blocks 1-7 carry only a rate
@@ -478,6 +569,7 @@ int decode_to_q(const uint8_t* in, uint64_t in_bytes, std::vector<int32_t>& qout
     // d5: inverse prediction with the carried state, then + mu.
     int32_t prev1 = 0, prev2 = 0;
     for (int i = 0; i < kTile; ++i) {
+      if ((feat_off & FSZO_OFF_CROSS) && i % kBlock == 0) prev1 = prev2 = 0;  // independent blocks
       int32_t qh = second ? wsub(wadd(l[i], wadd(prev1, prev1)), prev2) : wadd(l[i], prev1);
       prev2 = prev1;
       prev1 = qh;

@@ -34,6 +34,12 @@ enum { FSZO_EB_ABS = 0, FSZO_EB_REL = 1 };
 
 /* Variants in the paper's listed order (Sec. 4.2.2, "Four-Way Cost Analysis"). */
 enum { FSZO_LZ1 = 0, FSZO_LZ2 = 1, FSZO_LZ1C = 2, FSZO_LZ2C = 3 };
+/* Features of the method that can be switched off, for the ablation of Sec. 6.4 (0: the
+ * full method). OFF_CROSS: every block restarts from zero predecessors (independent
+ * blocks); OFF_CENTER: no centred variants; OFF_LZ2: no second-order variants. Centring is
+ * defined on the carried state, so OFF_CROSS requires OFF_CENTER. The stream's preamble
+ * records the bits (u32 at byte 52). */
+enum { FSZO_OFF_CROSS = 1, FSZO_OFF_CENTER = 2, FSZO_OFF_LZ2 = 4 };
 
 typedef struct {
   double eb;      /* absolute bound promised to the caller (ABS as given, REL x range) */
@@ -95,6 +101,26 @@ int fszo_compress_tiles(const float* d, uint64_t n, float r, uint64_t t0, uint64
 int fszo_read_preamble(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint32_t* ndim,
                        uint64_t dims[3], double* eb_req, float* s, uint64_t* data_bytes);
 
+/* The functions above with features switched off (FSZO_OFF_* bits; 0 = the full method).
+ * Single-pass costs without the carried state cover LZ1 and LZ2 only (C = UINT32_MAX for
+ * the centred ones); the four-pass costs evaluate all four residual sets as defined. */
+int fszo_features_valid(uint32_t off);
+void fszo_tile_residuals_f(const int32_t q[256], int32_t mu, int variant, uint32_t off,
+                           int32_t l[256]);
+void fszo_tile_costs_single_pass_f(const int32_t q[256], int32_t mu, uint32_t off, uint32_t C[4],
+                                   uint8_t rates[32]);
+void fszo_tile_costs_four_pass_f(const int32_t q[256], int32_t mu, uint32_t off, uint32_t C[4],
+                                 uint8_t rates[32]);
+int fszo_select_f(const uint32_t C[4], uint32_t off);
+int fszo_compress_f(const float* d, uint32_t ndim, const uint64_t* dims, int mode, double eb_req,
+                    uint32_t off, uint8_t* out, uint64_t out_capacity, uint64_t* out_bytes,
+                    int force_variant);
+int fszo_compress_tiles_f(const float* d, uint64_t n, float r, uint64_t t0, uint64_t t1,
+                          uint32_t off, uint8_t* header_out, uint8_t* data_out,
+                          uint64_t data_cap, uint64_t* data_bytes);
+int fszo_read_preamble_f(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint32_t* ndim,
+                         uint64_t dims[3], double* eb_req, float* s, uint64_t* data_bytes,
+                         uint32_t* features_off);
 /* Whole-stream decompression (Sec. 3.1 "Decompression", steps d1-d5). */
 int fszo_decompress(const uint8_t* in, uint64_t in_bytes, float* out, uint64_t out_capacity_elems,
                     uint64_t* n_out);

@@ -17,7 +17,8 @@
  * this library): [preamble 64 B][rate header: 8 B per tile][tile data].
  * Preamble, little-endian: 0 magic "FSZ1"; 4 version u16 = 1; 6 ndim u8;
  * 7 eb mode u8; 8 n u64; 16/24/32 dims u64 (unused dims 0); 40 requested eb
- * f64; 48 step s f32; 52 reserved u32 = 0; 56 data bytes u64.
+ * f64; 48 step s f32; 52 features switched off u32 (fsz_feature_off bits; 0 for
+ * the full method); 56 data bytes u64.
  *
  * Conventions for every call below:
  *  - Pointers named d_* are device pointers; h_* are host pointers. The caller
@@ -59,6 +60,16 @@ typedef enum {
 
 typedef enum { FSZ_EB_ABS = 0, FSZ_EB_REL = 1 } fsz_eb_mode;
 
+/* Features of the method a compression may switch off, for the ablation of Sec. 6.4
+ * (Table 7); 0 is the full method. FSZ_OFF_CROSS_BLOCK: every 32-element block restarts
+ * from zero predecessors (independent blocks, as Sec. 2 C1 describes block-parallel
+ * compressors) instead of carrying the state across blocks (Eq. 2). FSZ_OFF_CENTERING:
+ * no centred variants (Sec. 4.2.2, variants 3-4). FSZ_OFF_LZ2: no second-order variants.
+ * Centring is defined on the carried state (Eq. 4), so FSZ_OFF_CROSS_BLOCK requires
+ * FSZ_OFF_CENTERING (FSZ_ERR_INVALID_ARG otherwise). The stream records the bits and
+ * fsz_decompress honours them; a tile that uses a switched-off feature is corrupt. */
+typedef enum { FSZ_OFF_CROSS_BLOCK = 1, FSZ_OFF_CENTERING = 2, FSZ_OFF_LZ2 = 4 } fsz_feature_off;
+
 /* Shape metadata: n = dims[0] * ... * dims[ndim-1], row-major, dims[ndim-1] fastest.
  * The method itself is one-dimensional over the flattened array (Sec. 3.1). */
 typedef struct {
@@ -72,7 +83,7 @@ typedef struct {
   const float* in;       /* device, 16-byte aligned, dims product elements */
   fsz_dims dims;
   uint32_t mode;         /* fsz_eb_mode */
-  uint32_t reserved;     /* must be 0 */
+  uint32_t features_off; /* fsz_feature_off bits; 0 for the full method */
   double eb;             /* absolute bound (ABS) or fraction of max - min (REL) */
   void* out;             /* device, 16-byte aligned */
   uint64_t out_capacity; /* bytes; fsz_compress_bound(n) always suffices */
@@ -109,6 +120,13 @@ uint64_t fsz_batch_workspace_bytes(uint64_t n_total, uint32_t nfields);
 fsz_status fsz_compress(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
                         void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
                         void* d_ws, uint64_t ws_bytes, fsz_stream stream);
+
+/* fsz_compress with features of the method switched off (fsz_feature_off bits), for
+ * ablation studies; features_off = 0 is fsz_compress. */
+fsz_status fsz_compress_features(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                                 uint32_t features_off, void* d_out, uint64_t out_capacity,
+                                 uint64_t* d_out_bytes, void* d_ws, uint64_t ws_bytes,
+                                 fsz_stream stream);
 
 /* The two halves of fsz_compress, for callers that time or schedule them apart.
  * fsz_compress_prepare: value-range pass (Sec. 5.1: eb = REL x (max - min)) and the

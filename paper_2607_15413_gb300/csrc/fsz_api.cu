@@ -63,11 +63,13 @@ struct CompressCall {
 };
 
 fsz_status check_compress(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb, void* d_out,
-                          uint64_t out_capacity, void* d_ws, uint64_t ws_bytes, CompressCall* call) {
+                          uint64_t out_capacity, void* d_ws, uint64_t ws_bytes, CompressCall* call,
+                          uint32_t features_off = 0) {
   uint64_t n = 0;
   fsz_status st = dims_count(dims, &n);
   if (st != FSZ_OK) return st;
   if (mode != FSZ_EB_ABS && mode != FSZ_EB_REL) return FSZ_ERR_INVALID_ARG;
+  if (!features_valid(features_off)) return FSZ_ERR_INVALID_ARG;
   if (!(eb > 0.0) || !std::isfinite(eb)) return FSZ_ERR_INVALID_ARG;
   if (d_out == nullptr || d_ws == nullptr || (n > 0 && d_in == nullptr)) return FSZ_ERR_INVALID_ARG;
   if (misaligned(d_in) || misaligned(d_out) || misaligned(d_ws)) return FSZ_ERR_ALIGN;
@@ -86,8 +88,27 @@ fsz_status check_compress(const float* d_in, fsz_dims dims, fsz_eb_mode mode, do
   d.ndim = dims.ndim;
   d.mode = uint32_t(mode);
   d.eb_req = eb;
+  d.features_off = features_off;
   d.nchunks = (T + kCChunkTiles - 1) / kCChunkTiles;
   return FSZ_OK;
+}
+
+// Value-range pass and step for one field, with its switched-off features recorded in
+// the workspace's field record (read by the compression kernel and the preamble).
+fsz_status prepare_one(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                       uint32_t features_off, void* d_out, uint64_t out_capacity,
+                       uint64_t* d_out_bytes, void* d_ws, uint64_t ws_bytes, fsz_stream stream) {
+  CompressCall call;
+  fsz_status st = check_compress(d_in, dims, mode, eb, d_out, out_capacity, d_ws, ws_bytes, &call,
+                                 features_off);
+  if (st != FSZ_OK) return st;
+  call.desc.out_bytes = d_out_bytes;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_ws, 0, call.L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
+  const KernelArgs a = make_args(d_ws, call.L);
+  launch_setup_compress(a, call.desc, s);
+  if (call.desc.nchunks > 0) launch_stats(a, s);
+  return launched();
 }
 
 template <typename F>
@@ -134,16 +155,8 @@ uint64_t fsz_batch_workspace_bytes(uint64_t n_total, uint32_t nfields) {
 fsz_status fsz_compress_prepare(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
                                 void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
                                 void* d_ws, uint64_t ws_bytes, fsz_stream stream) {
-  CompressCall call;
-  fsz_status st = check_compress(d_in, dims, mode, eb, d_out, out_capacity, d_ws, ws_bytes, &call);
-  if (st != FSZ_OK) return st;
-  call.desc.out_bytes = d_out_bytes;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(d_ws, 0, call.L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
-  const KernelArgs a = make_args(d_ws, call.L);
-  launch_setup_compress(a, call.desc, s);
-  if (call.desc.nchunks > 0) launch_stats(a, s);
-  return launched();
+  return prepare_one(d_in, dims, mode, eb, 0, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes,
+                     stream);
 }
 
 fsz_status fsz_compress_encode(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
@@ -163,6 +176,17 @@ fsz_status fsz_compress(const float* d_in, fsz_dims dims, fsz_eb_mode mode, doub
                         fsz_stream stream) {
   fsz_status st = fsz_compress_prepare(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws,
                                        ws_bytes, stream);
+  if (st != FSZ_OK) return st;
+  return fsz_compress_encode(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes,
+                             stream);
+}
+
+fsz_status fsz_compress_features(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                                 uint32_t features_off, void* d_out, uint64_t out_capacity,
+                                 uint64_t* d_out_bytes, void* d_ws, uint64_t ws_bytes,
+                                 fsz_stream stream) {
+  fsz_status st = prepare_one(d_in, dims, mode, eb, features_off, d_out, out_capacity, d_out_bytes,
+                              d_ws, ws_bytes, stream);
   if (st != FSZ_OK) return st;
   return fsz_compress_encode(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes,
                              stream);

@@ -63,7 +63,7 @@ struct ChunkInfo {
   uint32_t cnt;          // valid elements in the chunk
   float r;
   uint32_t flags;        // kInfo* bits
-  uint32_t pad;
+  uint32_t off;          // the field's switched-off features (kOff* bits)
 };
 
 struct StageInfo {
@@ -98,13 +98,8 @@ __device__ __forceinline__ uint32_t sign_mag_fma(int l) {
   return uint32_t(mad_s32(l, mad_s32(sg, -4, 2), sg));
 }
 
-// Compresses two tiles with one warp: lanes 0-15 take one tile and lanes 16-31 the next
-// (half = lane >> 4). Lane hl = lane & 15 owns elements 16 hl..16 hl + 15 of its tile, so
-// lanes 2g, 2g + 1 of a half own block g (Sec. 3.1: a tile is 8 blocks of 32 elements).
-// The halves run in lockstep but each takes its own decisions (variant, rates). `tile` and
-// `hdr` are this half's; the first half's bytes go to `slot`, the second half's right
-// after them. A half with `live` false computes but stores nothing. Returns this half's
-// byte count (uniform within the half).
+// Loads lane hl = lane & 15's 16 elements (16 hl..16 hl + 15) of its half's tile from
+// the stage into registers, in element order.
 __device__ __forceinline__ void load_pair(const float* __restrict__ tile, const int lane,
                                           float (&d)[16]) {
   const int hl = lane & 15;
@@ -124,12 +119,24 @@ __device__ __forceinline__ void load_pair(const float* __restrict__ tile, const 
   }
 }
 
+// Compresses two tiles with one warp: lanes 0-15 take one tile and lanes 16-31 the next
+// (half = lane >> 4). Lane hl = lane & 15 holds elements 16 hl..16 hl + 15 of its tile in
+// d, so lanes 2g, 2g + 1 of a half own block g (Sec. 3.1: a tile is 8 blocks of 32
+// elements). The halves run in lockstep but each takes its own decisions (variant, rates).
+// `hdr` is this half's; the first half's bytes go to `slot`, the second half's right after
+// them. A half with `live` false computes but stores nothing. Returns this half's byte
+// count (uniform within the half). `feat_off` switches features off (kOff* bits): without the
+// cross-block state every block's first lane restarts from zero predecessors; a
+// switched-off variant's cost is raised past any tile's so that it is never selected.
 __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
                                                   uint8_t* __restrict__ slot,
                                                   uint8_t* __restrict__ hdr, const float r,
-                                                  const int lane, const bool live) {
+                                                  const int lane, const bool live,
+                                                  const uint32_t feat_off) {
   constexpr uint32_t FULL = 0xffffffffu;
   const int hl = lane & 15;
+  // zero predecessors: the tile's first lane, or with independent blocks every block's
+  const bool restart = hl == 0 || ((feat_off & kOffCross) && (hl & 1) == 0);
   // Step 1, quantize (Sec. 4.2.2): t = fl(d r) then the nearest integer, ties to even.
   // Y holds q + bits(M); differences of Y are differences of q.
   int Y[16];
@@ -159,13 +166,13 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
   // tile's first predecessor is zero. LZ2 as the difference of LZ1 residuals:
   // l2_i = (q_i - q_{i-1}) - (q_{i-1} - q_{i-2}).
   int prevY = __shfl_up_sync(FULL, Y[15], 1, 16);
-  if (hl == 0) prevY = kMagicBits;
+  if (restart) prevY = kMagicBits;
   int l1[16], l2[16];
   l1[0] = Y[0] - prevY;
 #pragma unroll
   for (int i = 1; i < 16; ++i) l1[i] = Y[i] - Y[i - 1];
   int prevL = __shfl_up_sync(FULL, l1[15], 1, 16);
-  if (hl == 0) prevL = 0;
+  if (restart) prevL = 0;
   l2[0] = l1[0] - prevL;
 #pragma unroll
   for (int i = 1; i < 16; ++i) l2[i] = l1[i] - l1[i - 1];
@@ -209,13 +216,15 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
                 (uint32_t(R2c) << 27);
   bc = __shfl_sync(FULL, bc, 0, 16);
   const int dC1 = int(bc & 0x7ffu) - 1024, dC2 = int((bc >> 11) & 0x7ffu) - 1024;
-  const int C3 = 4 + C1 + dC1;
-  const int C4 = 4 + C2 + dC2;
+  const int pen2 = (feat_off & kOffLz2) ? 0x10000 : 0;
+  const int pen3 = (feat_off & kOffCenter) ? 0x10000 : 0;
+  const int C3 = 4 + C1 + dC1 + pen3;
+  const int C4 = 4 + C2 + dC2 + pen2 + pen3;
   const int R1c0 = int((bc >> 22) & 31u), R2c0 = int(bc >> 27);
 
   // Step 3: first strict minimum in the order LZ1, LZ2, LZ1c, LZ2c.
   int v = 0, best = C1;
-  if (C2 < best) { v = 1; best = C2; }
+  if (C2 + pen2 < best) { v = 1; best = C2; }
   if (C3 < best) { v = 2; best = C3; }
   if (C4 < best) { v = 3; best = C4; }
   const bool second = (v & 1) != 0, centred = v >= 2;
@@ -343,6 +352,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       ci.ntiles = uint32_t(min(uint64_t(kCChunkTiles), T - tile0));
       ci.cnt = uint32_t(min(fi->n - e0, uint64_t(kCChunkElems)));
       ci.r = fi->r;
+      ci.off = fi->features_off;
       ci.flags = (fi->s > 0.0f ? kInfoOk : 0u) |  // a field without a step has nothing to load
                  (lc + 1 == fi->nchunks ? kInfoLast : 0u) | (lc == 0 ? kInfoFirst : 0u) |
                  (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
@@ -550,7 +560,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
         if (!ok_run) break;
         head += skip;
         pos = head % kRingBytes;
-        const uint32_t nb = compress_pair(d, ring + pos, hdr_out + 8 * tl, r, lane, live);
+        const uint32_t nb = compress_pair(d, ring + pos, hdr_out + 8 * tl, r, lane, live, ci.off);
         const uint32_t na = __shfl_sync(0xffffffffu, nb, 0);
         const uint32_t nbb = __shfl_sync(0xffffffffu, nb, 16);
         const bool second_live = ta + 1 < t_end;

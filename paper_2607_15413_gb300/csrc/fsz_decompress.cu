@@ -54,6 +54,8 @@ struct ChunkRec {
   uint32_t shift;        // payload start inside the stage
   uint32_t ntiles;
   uint32_t cnt;          // valid elements of the chunk
+  uint32_t seg;          // prefix-sum segment mask: whole warp, or 4-lane blocks when the
+                         // stream's blocks are independent
   float step;
 };
 
@@ -86,10 +88,13 @@ __device__ __forceinline__ bool header_reserved_bits_set(uint64_t h) {
 }
 
 // Decodes one tile with one warp; returns false if the tile's mean slot is malformed.
+// `seg` is the shuffle segment mask of the inverse prediction's prefix sums: 0 for a tile
+// whose state runs across its blocks, (32 - 4) << 8 for independent blocks (each block's
+// 4 lanes sum on their own, from zero predecessors).
 __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t boff,
                                                 const uint8_t* __restrict__ tp,
                                                 float* __restrict__ out, const float s,
-                                                const int lane) {
+                                                const int lane, const uint32_t seg) {
   constexpr uint32_t FULL = 0xffffffffu;
   const int g = lane >> 2, t = lane & 3;
   const bool second = (h & 0x80u) != 0, centred = (h & 0x40u) != 0;
@@ -153,7 +158,7 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
     const uint32_t tot = v[7];
     uint32_t inc = tot;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) inc = scan_step_up(inc, o);
+    for (int o = 1; o < 32; o <<= 1) inc = scan_step_up_seg(inc, o, seg);
     const uint32_t ex = inc - tot;
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] += ex;
@@ -222,7 +227,11 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
         q.hdr[lane] = hb;
         q.boff[lane] = block_word_offsets(hb);
       }
-      const bool bad_hdr = __any_sync(FULL, lane < ntiles && header_reserved_bits_set(hb));
+      // a tile may not use a feature the stream has switched off
+      const uint32_t foff = fi->features_off;
+      const uint64_t forbid = ((foff & kOffLz2) ? 0x80u : 0u) | ((foff & kOffCenter) ? 0x40u : 0u);
+      const bool bad_hdr =
+          __any_sync(FULL, lane < ntiles && (header_reserved_bits_set(hb) || (hb & forbid)));
       const uint32_t mine = lane < ntiles ? tile_bytes_from_header(hb) : 0u;
       uint32_t inc = mine;
 #pragma unroll
@@ -248,6 +257,7 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
         q.ntiles = uint32_t(ntiles);
         q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kDChunkElems)));
         q.step = fi->s;
+        q.seg = (foff & kOffCross) ? uint32_t(32 - 4) << 8 : 0u;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.fetched[r]);
@@ -344,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
         float* buf = S.out[warp][nstore & 1u];
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         __syncwarp();
-        good &= decompress_tile(st.hdr[tl], st.boff[tl], pay + st.toff[tl], buf, step, lane);
+        good &= decompress_tile(st.hdr[tl], st.boff[tl], pay + st.toff[tl], buf, step, lane, st.seg);
         fence_proxy_async();
         __syncwarp();
         const uint32_t k0 = uint32_t(tl) * kTile;

@@ -74,8 +74,19 @@ struct alignas(16) FieldInfo {
   float e, s, r;
   uint32_t Q;
   uint32_t status;
-  uint32_t pad;
+  uint32_t features_off;  // method features switched off (kOff* bits; 0: the full method)
 };
+
+// Features a compression may switch off, for the ablation of Sec. 6.4: the state carried
+// across block boundaries (off: every block restarts from zero predecessors), the centred
+// variants, the second-order variants. Centring is defined on the carried state (Eq. 4),
+// so switching the state off requires switching centring off. The preamble records the
+// bits (u32 at byte 52).
+constexpr uint32_t kOffCross = 1u, kOffCenter = 2u, kOffLz2 = 4u;
+__host__ __device__ __forceinline__ bool features_valid(uint32_t off) {
+  return (off & ~(kOffCross | kOffCenter | kOffLz2)) == 0 &&
+         (!(off & kOffCross) || (off & kOffCenter));
+}
 
 struct alignas(64) Ctrl {
   uint32_t status;       // first device-detected error of the call
@@ -290,7 +301,8 @@ __device__ __forceinline__ void transpose8x8(uint32_t& lo, uint32_t& hi) {
 
 // One step of an inclusive scan: v += v of lane - o, where that lane exists within the
 // segment of `width` lanes. The shuffle's own in-range predicate guards the add, so no
-// lane-index compare is needed.
+// lane-index compare is needed. scan_step_up_seg takes the segment as the shuffle's
+// segment-mask operand, (32 - width) << 8, at run time.
 template <int kWidth = 32>
 __device__ __forceinline__ uint32_t scan_step_up(uint32_t v, int o) {
   asm("{\n\t.reg .pred p;\n\t.reg .b32 y;\n\t"
@@ -298,6 +310,14 @@ __device__ __forceinline__ uint32_t scan_step_up(uint32_t v, int o) {
       "@p add.u32 %0, %0, y;\n\t}"
       : "+r"(v)
       : "r"(o), "n"((32 - kWidth) << 8));
+  return v;
+}
+__device__ __forceinline__ uint32_t scan_step_up_seg(uint32_t v, int o, uint32_t segmask) {
+  asm("{\n\t.reg .pred p;\n\t.reg .b32 y;\n\t"
+      "shfl.sync.up.b32 y|p, %0, %1, %2, 0xffffffff;\n\t"
+      "@p add.u32 %0, %0, y;\n\t}"
+      : "+r"(v)
+      : "r"(o), "r"(segmask));
   return v;
 }
 
@@ -431,7 +451,7 @@ __device__ __forceinline__ void write_preamble(FieldInfo* fi, uint64_t data_byte
   w[10] = uint32_t(eb);
   w[11] = uint32_t(eb >> 32);
   w[12] = __float_as_uint(fi->s);
-  w[13] = 0;
+  w[13] = fi->features_off;
   w[14] = uint32_t(data_bytes);
   w[15] = uint32_t(data_bytes >> 32);
   uint4* dst = reinterpret_cast<uint4*>(fi->out);

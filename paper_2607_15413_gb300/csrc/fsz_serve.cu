@@ -181,7 +181,7 @@ fsz_status fsz_server_s::start_batch(Slot& sl, uint32_t kind, std::vector<Req>&&
       t[i].in = static_cast<const float*>(r.d_in);
       t[i].dims = r.dims;
       t[i].mode = fsz_eb_mode(r.mode);
-      t[i].reserved = 0;
+      t[i].features_off = 0;
       t[i].eb = r.eb;
       t[i].out = static_cast<uint8_t*>(sl.arena->base) + sl.offs[i];
       t[i].out_capacity = request_cap(r);

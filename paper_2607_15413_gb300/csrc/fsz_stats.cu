@@ -164,7 +164,8 @@ __device__ uint32_t plan_cfield(FieldInfo* fi, const fsz_cfield& d) {
   fi->eb_req = d.eb;
   fi->ndim = d.dims.ndim;
   fi->nchunks = 0;
-  if (d.dims.ndim < 1 || d.dims.ndim > 3 || d.dims.reserved != 0 || d.reserved != 0 ||
+  fi->features_off = d.features_off;
+  if (d.dims.ndim < 1 || d.dims.ndim > 3 || d.dims.reserved != 0 || !features_valid(d.features_off) ||
       d.mode > 1 || !(d.eb > 0.0) || isinf(d.eb) || d.out == nullptr)
     return FSZ_ERR_INVALID_ARG;
   uint64_t n = 1;
@@ -225,7 +226,8 @@ __device__ uint32_t plan_dfield(FieldInfo* fi, const uint8_t* in, uint64_t in_by
   const float sv = __uint_as_float(w[12]);
   if (!(eb > 0.0) || isinf(eb)) return FSZ_ERR_CORRUPT;
   if (!(sv >= 1.5777218104420236e-30f) || isinf(sv)) return FSZ_ERR_CORRUPT;  // 2^-99
-  if (w[13] != 0) return FSZ_ERR_CORRUPT;
+  if (!features_valid(w[13])) return FSZ_ERR_CORRUPT;
+  fi->features_off = w[13];
   const uint64_t db = uint64_t(w[14]) | (uint64_t(w[15]) << 32);
   const uint64_t T = (n + kTile - 1) / kTile;
   if (in_bytes - 64 < 8 * T) return FSZ_ERR_CORRUPT;
@@ -257,6 +259,7 @@ __global__ void fsz_setup_compress_kernel(KernelArgs a, FieldInfo desc) {
   fi->n = desc.n; fi->T = desc.T;
   fi->dims[0] = desc.dims[0]; fi->dims[1] = desc.dims[1]; fi->dims[2] = desc.dims[2];
   fi->ndim = desc.ndim; fi->mode = desc.mode; fi->eb_req = desc.eb_req;
+  fi->features_off = desc.features_off;
   fi->chunk_first = 0;
   fi->nchunks = desc.nchunks;
   a.ctrl->nfields = 1;

@@ -22,9 +22,12 @@ STATUS_NAMES = {0: "FSZ_OK", 1: "FSZ_ERR_INVALID_ARG", 2: "FSZ_ERR_ALIGN", 3: "F
                 7: "FSZ_ERR_TIMEOUT", 8: "FSZ_ERR_CUDA", 9: "FSZ_ERR_WORKSPACE",
                 10: "FSZ_ERR_REJECTED"}
 EB_ABS, EB_REL = 0, 1
+# Features switched off (fsz_feature_off), for the ablation of Sec. 6.4; 0 is the full method.
+OFF_CROSS_BLOCK, OFF_CENTERING, OFF_LZ2 = 1, 2, 4
 
 # Every entry point include/fsz.h declares.
 EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_bytes", "fsz_compress",
+           "fsz_compress_features",
            "fsz_compress_prepare", "fsz_compress_encode", "fsz_decompress", "fsz_compress_batched",
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
            "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc",
@@ -42,7 +45,7 @@ class FszDims(ctypes.Structure):
 
 class FszCField(ctypes.Structure):
     _fields_ = [("in_", ctypes.c_void_p), ("dims", FszDims), ("mode", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("eb", ctypes.c_double), ("out", ctypes.c_void_p),
+                ("features_off", ctypes.c_uint32), ("eb", ctypes.c_double), ("out", ctypes.c_void_p),
                 ("out_capacity", ctypes.c_uint64), ("out_bytes", ctypes.c_void_p)]
 
 
@@ -78,7 +81,7 @@ class FszDField(ctypes.Structure):
 # numpy views of the same layouts, for filling many descriptors at once
 def _np_dtypes():
     import numpy as np
-    cf = np.dtype({"names": ["in_", "ndim", "dreserved", "d0", "d1", "d2", "mode", "reserved", "eb",
+    cf = np.dtype({"names": ["in_", "ndim", "dreserved", "d0", "d1", "d2", "mode", "features_off", "eb",
                              "out", "out_capacity", "out_bytes"],
                    "formats": ["<u8", "<u4", "<u4", "<u8", "<u8", "<u8", "<u4", "<u4", "<f8", "<u8",
                                "<u8", "<u8"],
@@ -133,6 +136,8 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = [P, FszDims, i32, f64, P, u64, P, P, u64, P]
                 fn.restype = i32
+            L.fsz_compress_features.argtypes = [P, FszDims, i32, f64, u32, P, u64, P, P, u64, P]
+            L.fsz_compress_features.restype = i32
             L.fsz_decompress.argtypes = [P, u64, P, u64, P, u64, P]
             L.fsz_decompress.restype = i32
             L.fsz_compress_batched.argtypes = [P, u32, u64, P, u64, P]
@@ -216,6 +221,12 @@ def fsz_batch_workspace_bytes(n_total: int, nfields: int) -> int:
 def fsz_compress(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes, stream) -> int:
     return lib().fsz_compress(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes,
                               stream)
+
+
+def fsz_compress_features(d_in, dims, mode, eb, features_off, d_out, out_capacity, d_out_bytes, d_ws,
+                          ws_bytes, stream) -> int:
+    return lib().fsz_compress_features(d_in, dims, mode, eb, features_off, d_out, out_capacity,
+                                       d_out_bytes, d_ws, ws_bytes, stream)
 
 
 def fsz_compress_prepare(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes,
@@ -344,8 +355,9 @@ class Workspace:
 
 
 def compress(x, eb: float, mode: int = EB_REL, shape=None, ws: Workspace | None = None,
-             out=None, stream=None, check: bool = True):
-    """Compress a contiguous float32 CUDA tensor. Returns (stream_bytes_tensor, nbytes)."""
+             out=None, stream=None, check: bool = True, features_off: int = 0):
+    """Compress a contiguous float32 CUDA tensor. Returns (stream_bytes_tensor, nbytes).
+    features_off switches features of the method off (OFF_* bits, for ablations)."""
     import torch
     assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
     shape = tuple(x.shape) if shape is None else tuple(shape)
@@ -358,8 +370,12 @@ def compress(x, eb: float, mode: int = EB_REL, shape=None, ws: Workspace | None 
     ws = ws if ws is not None else Workspace(n, x.device)
     nbytes = torch.zeros(2, dtype=torch.int64, device=x.device)
     sp = _stream_ptr(stream)
-    st = fsz_compress(x.data_ptr(), make_dims(shape), mode, eb, out.data_ptr(), out.numel(),
-                      nbytes.data_ptr(), ws.ptr, ws.bytes, sp)
+    if features_off:
+        st = fsz_compress_features(x.data_ptr(), make_dims(shape), mode, eb, features_off,
+                                   out.data_ptr(), out.numel(), nbytes.data_ptr(), ws.ptr, ws.bytes, sp)
+    else:
+        st = fsz_compress(x.data_ptr(), make_dims(shape), mode, eb, out.data_ptr(), out.numel(),
+                          nbytes.data_ptr(), ws.ptr, ws.bytes, sp)
     _check(st, "fsz_compress")
     if check:
         _check(fsz_check(ws.ptr, sp), "fsz_compress (device)")
@@ -403,7 +419,7 @@ class CompressBatch:
     def __init__(self, fields, device="cuda"):
         import torch
         self.device = torch.device(device)
-        self.fields = list(fields)  # (tensor, shape, mode, eb)
+        self.fields = list(fields)  # (tensor, shape, mode, eb[, features_off])
         self.n = [int(x.numel()) for x, *_ in self.fields]
         self.n_total = sum(self.n)
         caps = [_align16(fsz_compress_bound(k)) for k in self.n]
@@ -414,12 +430,13 @@ class CompressBatch:
         self.arena = torch.empty(max(16, self.offsets[-1]), dtype=torch.uint8, device=self.device)
         self.sizes = torch.zeros(len(self.fields), dtype=torch.int64, device=self.device)
         arr = (FszCField * len(self.fields))()
-        for i, (x, shape, mode, eb) in enumerate(self.fields):
+        for i, (x, shape, mode, eb, *rest) in enumerate(self.fields):
+            off = rest[0] if rest else 0
             assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
             arr[i].in_ = x.data_ptr() if x.numel() else 0
             arr[i].dims = make_dims(shape)
             arr[i].mode = int(mode)
-            arr[i].reserved = 0
+            arr[i].features_off = int(off)
             arr[i].eb = float(eb)
             arr[i].out = self.arena.data_ptr() + self.offsets[i]
             arr[i].out_capacity = caps[i]

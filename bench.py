@@ -429,6 +429,72 @@ def run_serving(fsz, inputs, dev, nreq: int = 20000, seed: int = 4, linger_us: i
             "closed_loop_vs_per_request": closed["gbs"] / per_req_gbs, "loads": levels}
 
 
+def run_ablation(fsz, fields, rels, dev, shape):
+    """Sec. 6.4 (Table 7) and Sec. 6.3 on the bench fields: the compression ratio at each
+    ablation step (Base = LZ1 with independent blocks, +Cross = the state carried across
+    blocks, +Cent. = centred variants, +LZ2 = the full method), and the compression time of
+    the single-pass evaluation against the multipass one (a pass per variant writing tile
+    costs, then the encoding pass selecting from them; identical streams)."""
+    import math
+    import statistics
+
+    import torch
+    levels = (("base", fsz.OFF_CROSS_BLOCK | fsz.OFF_CENTERING | fsz.OFF_LZ2),
+              ("+cross", fsz.OFF_CENTERING | fsz.OFF_LZ2), ("+center", fsz.OFF_LZ2), ("+lz2", 0))
+    n = fields[0][1].numel()
+    T = (n + 255) // 256
+    cap = fsz.fsz_compress_bound(n)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    out2 = torch.empty(cap, dtype=torch.uint8, device=dev)
+    ws = fsz.Workspace(n, dev)
+    costs = torch.empty((4, T), dtype=torch.int32, device=dev)
+    nb = torch.zeros(2, dtype=torch.int64, device=dev)
+    dims = fsz.make_dims(shape)
+    L = fsz.lib()
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    rows, timing = [], []
+
+    def timed(fn, reps=6):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            if st != 0:
+                raise fsz.FszError(st, "ablation")
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts[1:])
+
+    for name, x in fields:
+        for rel in rels:
+            row = {"field": name, "rel": rel}
+            for lname, off in levels:
+                _, k = fsz.compress(x, rel, fsz.EB_REL, shape=shape, ws=ws, out=out, features_off=off)
+                row[lname] = 4 * n / k
+            rows.append(row)
+            single = timed(lambda: L.fsz_compress(x.data_ptr(), dims, 1, rel, out.data_ptr(), cap,
+                                                  nb.data_ptr(), ws.ptr, ws.bytes, sp))
+            k1 = int(nb[0].item())
+            multi = timed(lambda: L.fsz_compress_multipass(x.data_ptr(), dims, 1, rel, out2.data_ptr(), cap,
+                                                           nb.data_ptr(), costs.data_ptr(), ws.ptr,
+                                                           ws.bytes, sp))
+            if fsz.fsz_check(ws.ptr, sp) != 0:
+                raise fsz.FszError(fsz.fsz_check(ws.ptr, sp), "multipass (device)")
+            k2 = int(nb[0].item())
+            same = k1 == k2 and torch.equal(out[:k1], out2[:k2])
+            timing.append({"field": name, "rel": rel, "single_pass_ms": single, "multipass_ms": multi,
+                           "single_pass_gbs": 4 * n / single / 1e6, "multipass_gbs": 4 * n / multi / 1e6,
+                           "speedup": multi / single, "identical_stream": bool(same)})
+    geo = lambda v: math.exp(sum(math.log(a) for a in v) / len(v))
+    gains = {lname: geo([r[lname] / r["base"] for r in rows]) for lname, _ in levels}
+    return {"workload": "the bench fields (512^3 k^-3 GRF, zero-slab variant) at each REL",
+            "features_off": {lname: off for lname, off in levels},
+            "cr": rows, "cr_gain_over_base_geomean": gains, "single_vs_multipass": timing,
+            "single_pass_speedup_geomean": geo([t["speedup"] for t in timing])}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -439,6 +505,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-field batched vs per-field comparison")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the ablation ladder and the multipass comparison")
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the continuous-batching serving measurement")
     ap.add_argument("--serving-requests", type=int, default=20000,
@@ -694,9 +762,16 @@ def main():
                         "decompress_hbm_gbs": (4 * n + sizes[j]) / med(dec_ms[j]) / 1e6})
     njobs, nfields_main = len(jobs), len(fields)
     clock_summary = clocks.summary()
+    ablation = None
+    if not args.no_ablation:
+        del outs, recon
+        torch.cuda.empty_cache()
+        ablation = run_ablation(fsz, fields, rels, dev, SHAPE)
     batched = None
     if not args.no_batched:
-        del fields, jobs, outs, recon, g
+        del fields, jobs, g
+        if args.no_ablation:
+            del outs, recon
         torch.cuda.empty_cache()
         batched = run_batched(fsz, inputs, dev)
     serving = None
@@ -714,7 +789,8 @@ def main():
                            "l2": "inputs 512 MiB > L2; streams read back after >= 2.5 GB of traffic"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps,
-                "clocks": clock_summary, "jobs": per_job, "batched": batched, "serving": serving,
+                "clocks": clock_summary, "jobs": per_job, "ablation": ablation, "batched": batched,
+                "serving": serving,
                 "max_abs_err_last_job": p_last}
         print(json.dumps(line))
     barrier(world)

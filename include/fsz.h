@@ -128,6 +128,18 @@ fsz_status fsz_compress_features(const float* d_in, fsz_dims dims, fsz_eb_mode m
                                  uint64_t* d_out_bytes, void* d_ws, uint64_t ws_bytes,
                                  fsz_stream stream);
 
+/* The multipass evaluation that Sec. 6.3 ("Single-pass evaluation benefit") compares the
+ * single-pass design against, for measuring that benefit: each of the four variants
+ * (LZ1, LZ2, LZ1c, LZ2c) is costed in a pass of its own over the field, writing every
+ * tile's cost (Eq. 3, plus 4 bytes for the mean of a centred variant) to
+ * d_costs[v * T + t] (device, 4 T uint32, 16-byte aligned, T = ceil(n / 256)); a fifth
+ * pass, the compression kernel, selects from those costs and encodes. The stream is the
+ * same as fsz_compress's; the input is read five times instead of once. */
+fsz_status fsz_compress_multipass(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                                  void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
+                                  uint32_t* d_costs, void* d_ws, uint64_t ws_bytes,
+                                  fsz_stream stream);
+
 /* The two halves of fsz_compress, for callers that time or schedule them apart.
  * fsz_compress_prepare: value-range pass (Sec. 5.1: eb = REL x (max - min)) and the
  * quantization step, written into the workspace. fsz_compress_encode: the single-pass

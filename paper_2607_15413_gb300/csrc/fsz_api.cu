@@ -192,6 +192,26 @@ fsz_status fsz_compress_features(const float* d_in, fsz_dims dims, fsz_eb_mode m
                              stream);
 }
 
+fsz_status fsz_compress_multipass(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                                  void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes,
+                                  uint32_t* d_costs, void* d_ws, uint64_t ws_bytes,
+                                  fsz_stream stream) {
+  if (d_costs == nullptr) return FSZ_ERR_INVALID_ARG;
+  if (misaligned(d_costs)) return FSZ_ERR_ALIGN;
+  CompressCall call;
+  fsz_status st = check_compress(d_in, dims, mode, eb, d_out, out_capacity, d_ws, ws_bytes, &call);
+  if (st != FSZ_OK) return st;
+  st = prepare_one(d_in, dims, mode, eb, 0, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes, stream);
+  if (st != FSZ_OK || call.desc.nchunks == 0) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  KernelArgs a = make_args(d_ws, call.L);
+  for (int v = 0; v < 4; ++v) launch_cost_pass(a, v, d_costs, s);
+  a.given_costs = d_costs;
+  a.given_T = call.desc.T;
+  launch_compress_given(a, s);
+  return launched();
+}
+
 fsz_status fsz_decompress(const void* d_in, uint64_t in_bytes, float* d_out, uint64_t out_capacity_elems,
                           void* d_ws, uint64_t ws_bytes, fsz_stream stream) {
   if (d_in == nullptr || d_out == nullptr || d_ws == nullptr) return FSZ_ERR_INVALID_ARG;

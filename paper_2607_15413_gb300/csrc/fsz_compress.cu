@@ -128,11 +128,17 @@ __device__ __forceinline__ void load_pair(const float* __restrict__ tile, const 
 // count (uniform within the half). `feat_off` switches features off (kOff* bits): without the
 // cross-block state every block's first lane restarts from zero predecessors; a
 // switched-off variant's cost is raised past any tile's so that it is never selected.
+// With kGiven the four tile costs come from `given` (this half's tile, stride gT between
+// variants) rather than from the costs computed here: the multipass evaluation's
+// encoding pass. They are equal, so the stream is the same.
+template <bool kGiven>
 __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
                                                   uint8_t* __restrict__ slot,
                                                   uint8_t* __restrict__ hdr, const float r,
                                                   const int lane, const bool live,
-                                                  const uint32_t feat_off) {
+                                                  const uint32_t feat_off,
+                                                  const uint32_t* __restrict__ given,
+                                                  const uint64_t gT) {
   constexpr uint32_t FULL = 0xffffffffu;
   const int hl = lane & 15;
   // zero predecessors: the tile's first lane, or with independent blocks every block's
@@ -210,7 +216,7 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
   pinc = scan_step_up<16>(pinc, 4);
   pinc = scan_step_up<16>(pinc, 8);
   const uint32_t ptot = __shfl_sync(FULL, pinc, 15, 16);
-  const int C1 = int(ptot & 0xffffu), C2 = int(ptot >> 16);
+  int C1 = int(ptot & 0xffffu), C2 = int(ptot >> 16);
   uint32_t bc = (block_cost(R1c) - block_cost(R1) + 1024u) |
                 ((block_cost(R2c) - block_cost(R2) + 1024u) << 11) | (uint32_t(R1c) << 22) |
                 (uint32_t(R2c) << 27);
@@ -218,8 +224,14 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
   const int dC1 = int(bc & 0x7ffu) - 1024, dC2 = int((bc >> 11) & 0x7ffu) - 1024;
   const int pen2 = (feat_off & kOffLz2) ? 0x10000 : 0;
   const int pen3 = (feat_off & kOffCenter) ? 0x10000 : 0;
-  const int C3 = 4 + C1 + dC1 + pen3;
-  const int C4 = 4 + C2 + dC2 + pen2 + pen3;
+  int C3 = 4 + C1 + dC1 + pen3;
+  int C4 = 4 + C2 + dC2 + pen2 + pen3;
+  if constexpr (kGiven) {
+    C1 = int(given[0]);
+    C2 = int(given[gT]);
+    C3 = int(given[2 * gT]);
+    C4 = int(given[3 * gT]);
+  }
   const int R1c0 = int((bc >> 22) & 31u), R2c0 = int(bc >> 27);
 
   // Step 3: first strict minimum in the order LZ1, LZ2, LZ1c, LZ2c.
@@ -301,7 +313,8 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
   return uint32_t(best);
 }
 
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(KernelArgs a) {
+template <bool kGiven>
+__device__ __forceinline__ void compress_body(const KernelArgs& a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   CompressSmem& S = *reinterpret_cast<CompressSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -560,7 +573,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
         if (!ok_run) break;
         head += skip;
         pos = head % kRingBytes;
-        const uint32_t nb = compress_pair(d, ring + pos, hdr_out + 8 * tl, r, lane, live, ci.off);
+        const uint32_t nb = compress_pair<kGiven>(d, ring + pos, hdr_out + 8 * tl, r, lane, live,
+                                                  ci.off, a.given_costs + ci.tile0 + tl, a.given_T);
         const uint32_t na = __shfl_sync(0xffffffffu, nb, 0);
         const uint32_t nbb = __shfl_sync(0xffffffffu, nb, 16);
         const bool second_live = ta + 1 < t_end;
@@ -620,6 +634,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
   }
 }
 
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(KernelArgs a) {
+  compress_body<false>(a);
+}
+
+// The multipass evaluation's encoding pass (selection from a.given_costs).
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_given_kernel(KernelArgs a) {
+  compress_body<true>(a);
+}
+
 }  // namespace
 
 LaunchCfg compress_cfg() {
@@ -627,6 +650,8 @@ LaunchCfg compress_cfg() {
     LaunchCfg c;
     c.smem = int(sizeof(CompressSmem));
     cudaFuncSetAttribute(fsz_compress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
+    cudaFuncSetAttribute(fsz_compress_given_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         c.smem);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -642,6 +667,11 @@ LaunchCfg compress_cfg() {
 void launch_compress(const KernelArgs& a, cudaStream_t st) {
   const LaunchCfg c = compress_cfg();
   fsz_compress_kernel<<<sched_grid(c, kSchedCompress), kThreads, c.smem, st>>>(a);
+}
+
+void launch_compress_given(const KernelArgs& a, cudaStream_t st) {
+  const LaunchCfg c = compress_cfg();
+  fsz_compress_given_kernel<<<sched_grid(c, kSchedCompress), kThreads, c.smem, st>>>(a);
 }
 
 }  // namespace fsz

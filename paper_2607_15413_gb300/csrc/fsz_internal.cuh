@@ -122,6 +122,10 @@ struct KernelArgs {
   uint64_t* flags;
   uint64_t skip_chunk;  // test hook: this chunk publishes no flag
   uint64_t timeout_ns;  // bound on every spin-wait
+  // multipass compression only: the four variants' tile costs, variant-major (given_T
+  // per variant), from which the encoding pass selects
+  const uint32_t* given_costs = nullptr;
+  uint64_t given_T = 0;
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -486,6 +490,10 @@ LaunchCfg decompress_cfg();
 
 void launch_stats(const KernelArgs& a, cudaStream_t st);
 void launch_compress(const KernelArgs& a, cudaStream_t st);
+// The multipass evaluation: one pass per variant writing its tile costs, then the
+// compression kernel selecting from them (a.given_costs).
+void launch_cost_pass(const KernelArgs& a, int variant, uint32_t* costs, cudaStream_t st);
+void launch_compress_given(const KernelArgs& a, cudaStream_t st);
 void launch_decompress(const KernelArgs& a, cudaStream_t st);
 void launch_setup_compress(const KernelArgs& a, const FieldInfo& fi, cudaStream_t st);
 void launch_setup_decompress(const KernelArgs& a, const uint8_t* in, uint64_t in_bytes, float* out,

@@ -27,7 +27,7 @@ OFF_CROSS_BLOCK, OFF_CENTERING, OFF_LZ2 = 1, 2, 4
 
 # Every entry point include/fsz.h declares.
 EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_bytes", "fsz_compress",
-           "fsz_compress_features",
+           "fsz_compress_features", "fsz_compress_multipass",
            "fsz_compress_prepare", "fsz_compress_encode", "fsz_decompress", "fsz_compress_batched",
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
            "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc",
@@ -138,6 +138,8 @@ def lib():
                 fn.restype = i32
             L.fsz_compress_features.argtypes = [P, FszDims, i32, f64, u32, P, u64, P, P, u64, P]
             L.fsz_compress_features.restype = i32
+            L.fsz_compress_multipass.argtypes = [P, FszDims, i32, f64, P, u64, P, P, P, u64, P]
+            L.fsz_compress_multipass.restype = i32
             L.fsz_decompress.argtypes = [P, u64, P, u64, P, u64, P]
             L.fsz_decompress.restype = i32
             L.fsz_compress_batched.argtypes = [P, u32, u64, P, u64, P]
@@ -381,6 +383,36 @@ def compress(x, eb: float, mode: int = EB_REL, shape=None, ws: Workspace | None 
         _check(fsz_check(ws.ptr, sp), "fsz_compress (device)")
     nb = int(nbytes[0].item())
     return out[:nb], nb
+
+
+def compress_multipass(x, eb: float, mode: int = EB_REL, shape=None, ws: Workspace | None = None,
+                       out=None, costs=None, stream=None, check: bool = True):
+    """compress() through the multipass evaluation (four cost passes, then the encoding
+    pass selecting from them). Returns (stream_bytes_tensor, nbytes, costs) with costs a
+    uint32-valued int32 tensor of shape (4, T)."""
+    import torch
+    assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
+    shape = tuple(x.shape) if shape is None else tuple(shape)
+    if len(shape) == 0:
+        shape = (x.numel(),)
+    n = x.numel()
+    T = (n + 255) // 256
+    cap = fsz_compress_bound(n)
+    if out is None:
+        out = _dev_buffer(cap, x.device)
+    if costs is None:
+        costs = torch.zeros((4, max(T, 1)), dtype=torch.int32, device=x.device)
+    ws = ws if ws is not None else Workspace(n, x.device)
+    nbytes = torch.zeros(2, dtype=torch.int64, device=x.device)
+    sp = _stream_ptr(stream)
+    st = lib().fsz_compress_multipass(x.data_ptr(), make_dims(shape), mode, eb, out.data_ptr(),
+                                      out.numel(), nbytes.data_ptr(), costs.data_ptr(), ws.ptr,
+                                      ws.bytes, sp)
+    _check(st, "fsz_compress_multipass")
+    if check:
+        _check(fsz_check(ws.ptr, sp), "fsz_compress_multipass (device)")
+    nb = int(nbytes[0].item())
+    return out[:nb], nb, costs[:, :T]
 
 
 def decompress(stream_bytes, n: int | None = None, ws: Workspace | None = None, out=None,

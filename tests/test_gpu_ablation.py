@@ -25,7 +25,7 @@ def _cuda():
 FIELDS = {
     "offset": lambda n, s: (10.0 * inputs.sinusoids(n, seed=s) + 280.0).astype(np.float32),
     "particles": lambda n, s: inputs.particles(n, seed=s, ncenters=max(4, n // 2048)),
-    "zero_slabs": lambda n, s: inputs.zero_slabs((n // 4096, 64, 64), seed=s).ravel(),
+    "zero_slabs": lambda n, s: inputs.zero_slabs((max(24, -(-n // 4096)), 64, 64), seed=s).ravel()[:n],
 }
 
 
@@ -122,3 +122,42 @@ def test_decoder_checks_the_feature_word(fszlib, oracle):
         b[52:56] = int(off).to_bytes(4, "little")
         assert _decode_status(fszlib, bytes(b), x.size) == fszlib.ERR_CORRUPT, off
         assert oracle.decompress_status(bytes(b)) == oracle.ERR_CORRUPT
+
+
+# ---------------------------------------------------------------- multipass evaluation
+
+@pytest.mark.parametrize("n", [1, 255, 257, 8193, 4096 * 24, 3 * 8192 + 17])
+@pytest.mark.parametrize("field", sorted(FIELDS))
+def test_multipass_stream_is_the_single_pass_stream(fszlib, oracle, field, n):
+    """Sec. 6.3: the multipass evaluation produces identical streams; its four cost arrays
+    are the oracle's four-pass costs (one residual pass per variant) tile by tile."""
+    dev = _cuda()
+    x = FIELDS[field](n, 7)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    for rel in (1e-2, 1e-3):
+        sb, nb, costs = fszlib.compress_multipass(xd, rel, fszlib.EB_REL)
+        ref = oracle.compress(x, rel, oracle.REL)
+        assert sb.cpu().numpy().tobytes() == ref
+        p = oracle.params_for(x, oracle.REL, rel)
+        T = (x.size + 255) // 256
+        xp = np.zeros(T * 256, np.float32)
+        xp[: x.size] = x
+        q = oracle.quantize(xp, p.r)
+        c = costs.cpu().numpy().view(np.uint32)
+        for t in sorted({0, T // 2, T - 1} | set(range(0, T, max(1, T // 17)))):
+            d = xp[256 * t: 256 * t + 256]
+            C, _ = oracle.tile_costs(q[256 * t: 256 * t + 256], oracle.tile_mu(d, p.r), four_pass=True)
+            assert list(c[:, t]) == [int(v) for v in C], t
+
+
+def test_multipass_refuses_missing_or_misaligned_costs(fszlib):
+    dev = _cuda()
+    x = torch.linspace(0, 1, 5000, device=dev)
+    ws = fszlib.Workspace(5000, dev)
+    out = torch.empty(fszlib.fsz_compress_bound(5000), dtype=torch.uint8, device=dev)
+    costs = torch.zeros(4 * 20 + 4, dtype=torch.int32, device=dev)
+    sp = torch.cuda.current_stream().cuda_stream
+    L = fszlib.lib()
+    args = (x.data_ptr(), fszlib.make_dims((5000,)), 1, 1e-3, out.data_ptr(), out.numel(), None)
+    assert L.fsz_compress_multipass(*args, None, ws.ptr, ws.bytes, sp) == fszlib.ERR_INVALID_ARG
+    assert L.fsz_compress_multipass(*args, costs.data_ptr() + 4, ws.ptr, ws.bytes, sp) == fszlib.ERR_ALIGN

@@ -66,8 +66,13 @@ typedef enum { FSZ_EB_ABS = 0, FSZ_EB_REL = 1 } fsz_eb_mode;
  * compressors) instead of carrying the state across blocks (Eq. 2). FSZ_OFF_CENTERING:
  * no centred variants (Sec. 4.2.2, variants 3-4). FSZ_OFF_LZ2: no second-order variants.
  * Centring is defined on the carried state (Eq. 4), so FSZ_OFF_CROSS_BLOCK requires
- * FSZ_OFF_CENTERING (FSZ_ERR_INVALID_ARG otherwise). The stream records the bits and
- * fsz_decompress honours them; a tile that uses a switched-off feature is corrupt. */
+ * FSZ_OFF_CENTERING (FSZ_ERR_INVALID_ARG otherwise). The stream records the bits; a tile
+ * that uses a switched-off feature is corrupt. fsz_decompress decodes streams with
+ * centring or LZ2 switched off; a stream without the cross-block state needs
+ * fsz_decompress_any (fsz_decompress and fsz_decompress_batched record
+ * FSZ_ERR_INVALID_ARG for it). The compression and decompression kernels are built in
+ * instances with and without the switched-off features' handling, so the full method
+ * pays nothing for them. */
 typedef enum { FSZ_OFF_CROSS_BLOCK = 1, FSZ_OFF_CENTERING = 2, FSZ_OFF_LZ2 = 4 } fsz_feature_off;
 
 /* Shape metadata: n = dims[0] * ... * dims[ndim-1], row-major, dims[ndim-1] fastest.
@@ -157,6 +162,13 @@ fsz_status fsz_compress_encode(const float* d_in, fsz_dims dims, fsz_eb_mode mod
 fsz_status fsz_decompress(const void* d_in, uint64_t in_bytes, float* d_out,
                           uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
                           fsz_stream stream);
+
+/* fsz_decompress for any stream, including those compressed with FSZ_OFF_CROSS_BLOCK
+ * (its inverse prediction restarts at every block). About 3 % slower than fsz_decompress
+ * on the full method's streams, for which fsz_decompress is the call. */
+fsz_status fsz_decompress_any(const void* d_in, uint64_t in_bytes, float* d_out,
+                              uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
+                              fsz_stream stream);
 
 /* ------------------------------------------------------------------ batches */
 

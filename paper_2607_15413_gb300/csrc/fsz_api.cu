@@ -111,6 +111,25 @@ fsz_status prepare_one(const float* d_in, fsz_dims dims, fsz_eb_mode mode, doubl
   return launched();
 }
 
+// One stream's decompression; `any` selects the decoder instance that also takes streams
+// without the cross-block state.
+fsz_status decompress_one(const void* d_in, uint64_t in_bytes, float* d_out,
+                          uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
+                          fsz_stream stream, bool any) {
+  if (d_in == nullptr || d_out == nullptr || d_ws == nullptr) return FSZ_ERR_INVALID_ARG;
+  if (misaligned(d_in) || misaligned(d_out) || misaligned(d_ws)) return FSZ_ERR_ALIGN;
+  if (out_capacity_elems > kMaxElems) out_capacity_elems = kMaxElems;
+  const WsLayout L = ws_layout((out_capacity_elems + kTile - 1) / kTile, 1);
+  if (ws_bytes < L.bytes) return FSZ_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_ws, 0, L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
+  const KernelArgs a = make_args(d_ws, L);
+  launch_setup_decompress(a, static_cast<const uint8_t*>(d_in), in_bytes, d_out, out_capacity_elems,
+                          L.chunk_cap, s);
+  launch_decompress(a, s, any);
+  return launched();
+}
+
 template <typename F>
 fsz_status capture_graph(F&& record, fsz_graph* out) {
   if (out == nullptr) return FSZ_ERR_INVALID_ARG;
@@ -167,7 +186,7 @@ fsz_status fsz_compress_encode(const float* d_in, fsz_dims dims, fsz_eb_mode mod
   fsz_status st = check_compress(d_in, dims, mode, eb, d_out, out_capacity, d_ws, ws_bytes, &call);
   if (st != FSZ_OK) return st;
   if (call.desc.nchunks == 0) return FSZ_OK;
-  launch_compress(make_args(d_ws, call.L), reinterpret_cast<cudaStream_t>(stream));
+  launch_compress(make_args(d_ws, call.L), reinterpret_cast<cudaStream_t>(stream), kCompressFull);
   return launched();
 }
 
@@ -187,9 +206,15 @@ fsz_status fsz_compress_features(const float* d_in, fsz_dims dims, fsz_eb_mode m
                                  fsz_stream stream) {
   fsz_status st = prepare_one(d_in, dims, mode, eb, features_off, d_out, out_capacity, d_out_bytes,
                               d_ws, ws_bytes, stream);
-  if (st != FSZ_OK) return st;
-  return fsz_compress_encode(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws, ws_bytes,
-                             stream);
+  if (st != FSZ_OK || features_off == 0)
+    return st != FSZ_OK ? st
+                        : fsz_compress_encode(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes,
+                                              d_ws, ws_bytes, stream);
+  CompressCall call;
+  st = check_compress(d_in, dims, mode, eb, d_out, out_capacity, d_ws, ws_bytes, &call, features_off);
+  if (st != FSZ_OK || call.desc.nchunks == 0) return st;
+  launch_compress(make_args(d_ws, call.L), reinterpret_cast<cudaStream_t>(stream), kCompressFeatures);
+  return launched();
 }
 
 fsz_status fsz_compress_multipass(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
@@ -208,24 +233,19 @@ fsz_status fsz_compress_multipass(const float* d_in, fsz_dims dims, fsz_eb_mode 
   for (int v = 0; v < 4; ++v) launch_cost_pass(a, v, d_costs, s);
   a.given_costs = d_costs;
   a.given_T = call.desc.T;
-  launch_compress_given(a, s);
+  launch_compress(a, s, kCompressGiven);
   return launched();
 }
 
 fsz_status fsz_decompress(const void* d_in, uint64_t in_bytes, float* d_out, uint64_t out_capacity_elems,
                           void* d_ws, uint64_t ws_bytes, fsz_stream stream) {
-  if (d_in == nullptr || d_out == nullptr || d_ws == nullptr) return FSZ_ERR_INVALID_ARG;
-  if (misaligned(d_in) || misaligned(d_out) || misaligned(d_ws)) return FSZ_ERR_ALIGN;
-  if (out_capacity_elems > kMaxElems) out_capacity_elems = kMaxElems;
-  const WsLayout L = ws_layout((out_capacity_elems + kTile - 1) / kTile, 1);
-  if (ws_bytes < L.bytes) return FSZ_ERR_WORKSPACE;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(d_ws, 0, L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
-  const KernelArgs a = make_args(d_ws, L);
-  launch_setup_decompress(a, static_cast<const uint8_t*>(d_in), in_bytes, d_out, out_capacity_elems,
-                          L.chunk_cap, s);
-  launch_decompress(a, s);
-  return launched();
+  return decompress_one(d_in, in_bytes, d_out, out_capacity_elems, d_ws, ws_bytes, stream, false);
+}
+
+fsz_status fsz_decompress_any(const void* d_in, uint64_t in_bytes, float* d_out,
+                              uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
+                              fsz_stream stream) {
+  return decompress_one(d_in, in_bytes, d_out, out_capacity_elems, d_ws, ws_bytes, stream, true);
 }
 
 fsz_status fsz_compress_batched(const fsz_cfield* d_fields, uint32_t nfields, uint64_t n_total,
@@ -239,7 +259,7 @@ fsz_status fsz_compress_batched(const fsz_cfield* d_fields, uint32_t nfields, ui
   const KernelArgs a = make_args(d_ws, L);
   launch_plan_compress(a, d_fields, nfields, L.chunk_cap, s);
   launch_stats(a, s);
-  launch_compress(a, s);
+  launch_compress(a, s, kCompressFeatures);  // fields may switch features off
   return launched();
 }
 

@@ -125,9 +125,11 @@ __device__ __forceinline__ void load_pair(const float* __restrict__ tile, const 
 // elements). The halves run in lockstep but each takes its own decisions (variant, rates).
 // `hdr` is this half's; the first half's bytes go to `slot`, the second half's right after
 // them. A half with `live` false computes but stores nothing. Returns this half's byte
-// count (uniform within the half). `feat_off` switches features off (kOff* bits): without the
-// cross-block state every block's first lane restarts from zero predecessors; a
-// switched-off variant's cost is raised past any tile's so that it is never selected.
+// count (uniform within the half). Switched-off features (kOff* bits) arrive as `restart`
+// (this lane starts from zero predecessors: the tile's first lane, and without the
+// cross-block state every block's first lane) and as penalties pen2, pen3 (2^16 for the
+// second-order and the centred variants when off), which raise a switched-off variant's
+// cost past any tile's so that it is never selected.
 // With kGiven the four tile costs come from `given` (this half's tile, stride gT between
 // variants) rather than from the costs computed here: the multipass evaluation's
 // encoding pass. They are equal, so the stream is the same.
@@ -136,13 +138,12 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
                                                   uint8_t* __restrict__ slot,
                                                   uint8_t* __restrict__ hdr, const float r,
                                                   const int lane, const bool live,
-                                                  const uint32_t feat_off,
+                                                  const bool restart, const int pen2,
+                                                  const int pen3,
                                                   const uint32_t* __restrict__ given,
                                                   const uint64_t gT) {
   constexpr uint32_t FULL = 0xffffffffu;
   const int hl = lane & 15;
-  // zero predecessors: the tile's first lane, or with independent blocks every block's
-  const bool restart = hl == 0 || ((feat_off & kOffCross) && (hl & 1) == 0);
   // Step 1, quantize (Sec. 4.2.2): t = fl(d r) then the nearest integer, ties to even.
   // Y holds q + bits(M); differences of Y are differences of q.
   int Y[16];
@@ -222,8 +223,6 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
                 (uint32_t(R2c) << 27);
   bc = __shfl_sync(FULL, bc, 0, 16);
   const int dC1 = int(bc & 0x7ffu) - 1024, dC2 = int((bc >> 11) & 0x7ffu) - 1024;
-  const int pen2 = (feat_off & kOffLz2) ? 0x10000 : 0;
-  const int pen3 = (feat_off & kOffCenter) ? 0x10000 : 0;
   int C3 = 4 + C1 + dC1 + pen3;
   int C4 = 4 + C2 + dC2 + pen2 + pen3;
   if constexpr (kGiven) {
@@ -313,8 +312,11 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
   return uint32_t(best);
 }
 
-template <bool kGiven>
-__device__ __forceinline__ void compress_body(const KernelArgs& a) {
+// kGiven: the multipass evaluation's encoding pass (selection from a.given_costs).
+// kFeat: fields' switched-off features honoured; without it the full method is compiled
+// with none of that handling.
+template <bool kGiven, bool kFeat>
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   CompressSmem& S = *reinterpret_cast<CompressSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -573,8 +575,15 @@ __device__ __forceinline__ void compress_body(const KernelArgs& a) {
         if (!ok_run) break;
         head += skip;
         pos = head % kRingBytes;
+        // switched-off features: zero predecessors for every block's first lane without
+        // the carried state; cost penalties for switched-off variants
+        const uint32_t foff = kFeat ? ci.off : 0u;
+        const bool restart = (lane & 15) == 0 || ((foff & kOffCross) && (lane & 1) == 0);
+        const int pen2 = (foff & kOffLz2) ? 0x10000 : 0;
+        const int pen3 = (foff & kOffCenter) ? 0x10000 : 0;
         const uint32_t nb = compress_pair<kGiven>(d, ring + pos, hdr_out + 8 * tl, r, lane, live,
-                                                  ci.off, a.given_costs + ci.tile0 + tl, a.given_T);
+                                                  restart, pen2, pen3,
+                                                  a.given_costs + ci.tile0 + tl, a.given_T);
         const uint32_t na = __shfl_sync(0xffffffffu, nb, 0);
         const uint32_t nbb = __shfl_sync(0xffffffffu, nb, 16);
         const bool second_live = ta + 1 < t_end;
@@ -634,28 +643,23 @@ __device__ __forceinline__ void compress_body(const KernelArgs& a) {
   }
 }
 
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(KernelArgs a) {
-  compress_body<false>(a);
-}
-
-// The multipass evaluation's encoding pass (selection from a.given_costs).
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_given_kernel(KernelArgs a) {
-  compress_body<true>(a);
-}
-
 }  // namespace
 
 LaunchCfg compress_cfg() {
   static LaunchCfg cfg = [] {
     LaunchCfg c;
     c.smem = int(sizeof(CompressSmem));
-    cudaFuncSetAttribute(fsz_compress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
-    cudaFuncSetAttribute(fsz_compress_given_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         c.smem);
+    cudaFuncSetAttribute(fsz_compress_kernel<false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
+    cudaFuncSetAttribute(fsz_compress_kernel<false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
+    cudaFuncSetAttribute(fsz_compress_kernel<true, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_compress_kernel, kThreads, c.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_compress_kernel<false, false>, kThreads,
+                                                  c.smem);
     c.sms = sms;
     c.per = per > 0 ? per : 1;
     c.grid = sms * c.per;
@@ -664,14 +668,15 @@ LaunchCfg compress_cfg() {
   return cfg;
 }
 
-void launch_compress(const KernelArgs& a, cudaStream_t st) {
+void launch_compress(const KernelArgs& a, cudaStream_t st, CompressKind kind) {
   const LaunchCfg c = compress_cfg();
-  fsz_compress_kernel<<<sched_grid(c, kSchedCompress), kThreads, c.smem, st>>>(a);
-}
-
-void launch_compress_given(const KernelArgs& a, cudaStream_t st) {
-  const LaunchCfg c = compress_cfg();
-  fsz_compress_given_kernel<<<sched_grid(c, kSchedCompress), kThreads, c.smem, st>>>(a);
+  const int g = sched_grid(c, kSchedCompress);
+  if (kind == kCompressFeatures)
+    fsz_compress_kernel<false, true><<<g, kThreads, c.smem, st>>>(a);
+  else if (kind == kCompressGiven)
+    fsz_compress_kernel<true, false><<<g, kThreads, c.smem, st>>>(a);
+  else
+    fsz_compress_kernel<false, false><<<g, kThreads, c.smem, st>>>(a);
 }
 
 }  // namespace fsz

@@ -54,8 +54,7 @@ struct ChunkRec {
   uint32_t shift;        // payload start inside the stage
   uint32_t ntiles;
   uint32_t cnt;          // valid elements of the chunk
-  uint32_t seg;          // prefix-sum segment mask: whole warp, or 4-lane blocks when the
-                         // stream's blocks are independent
+  uint32_t indep;        // the stream's blocks are independent (no carried state)
   float step;
 };
 
@@ -88,13 +87,15 @@ __device__ __forceinline__ bool header_reserved_bits_set(uint64_t h) {
 }
 
 // Decodes one tile with one warp; returns false if the tile's mean slot is malformed.
-// `seg` is the shuffle segment mask of the inverse prediction's prefix sums: 0 for a tile
-// whose state runs across its blocks, (32 - 4) << 8 for independent blocks (each block's
-// 4 lanes sum on their own, from zero predecessors).
+// kAny: the instance that also decodes streams without the cross-block state; for those
+// (`indep`) the inverse prediction's prefix sums restart at every block (4 lanes, zero
+// predecessors): the warp-wide prefix less the prefix at the block's start. The other
+// instance carries none of that code (it costs the full method's decode 3 %).
+template <bool kAny>
 __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t boff,
                                                 const uint8_t* __restrict__ tp,
                                                 float* __restrict__ out, const float s,
-                                                const int lane, const uint32_t seg) {
+                                                const int lane, const bool indep) {
   constexpr uint32_t FULL = 0xffffffffu;
   const int g = lane >> 2, t = lane & 3;
   const bool second = (h & 0x80u) != 0, centred = (h & 0x40u) != 0;
@@ -158,8 +159,12 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
     const uint32_t tot = v[7];
     uint32_t inc = tot;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) inc = scan_step_up_seg(inc, o, seg);
-    const uint32_t ex = inc - tot;
+    for (int o = 1; o < 32; o <<= 1) inc = scan_step_up(inc, o);
+    uint32_t ex = inc - tot;
+    if (kAny && indep) {  // less the inclusive prefix of the lane before the block's first
+      const uint32_t b = __shfl_sync(FULL, inc, (lane & ~3) - 1);
+      if (lane >= 4) ex -= b;
+    }
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] += ex;
   };
@@ -173,6 +178,7 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
   return __all_sync(FULL, good);
 }
 
+template <bool kAny>
 __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   DecompressSmem& S = *reinterpret_cast<DecompressSmem*>(smem_raw);
@@ -230,7 +236,10 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
       // a tile may not use a feature the stream has switched off
       const uint32_t foff = fi->features_off;
       const uint64_t forbid = ((foff & kOffLz2) ? 0x80u : 0u) | ((foff & kOffCenter) ? 0x40u : 0u);
-      const bool bad_hdr =
+      // streams without the cross-block state are decoded by the kAny instance only
+      const bool unsupported = !kAny && (foff & kOffCross);
+      if (unsupported && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_INVALID_ARG);
+      const bool bad_hdr = unsupported ||
           __any_sync(FULL, lane < ntiles && (header_reserved_bits_set(hb) || (hb & forbid)));
       const uint32_t mine = lane < ntiles ? tile_bytes_from_header(hb) : 0u;
       uint32_t inc = mine;
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
         q.ntiles = uint32_t(ntiles);
         q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kDChunkElems)));
         q.step = fi->s;
-        q.seg = (foff & kOffCross) ? uint32_t(32 - 4) << 8 : 0u;
+        q.indep = (foff & kOffCross) ? 1u : 0u;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&S.fetched[r]);
@@ -354,7 +363,8 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
         float* buf = S.out[warp][nstore & 1u];
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         __syncwarp();
-        good &= decompress_tile(st.hdr[tl], st.boff[tl], pay + st.toff[tl], buf, step, lane, st.seg);
+        good &= decompress_tile<kAny>(st.hdr[tl], st.boff[tl], pay + st.toff[tl], buf, step, lane,
+                                      st.indep != 0);
         fence_proxy_async();
         __syncwarp();
         const uint32_t k0 = uint32_t(tl) * kTile;
@@ -385,11 +395,15 @@ LaunchCfg decompress_cfg() {
   static LaunchCfg cfg = [] {
     LaunchCfg c;
     c.smem = int(sizeof(DecompressSmem));
-    cudaFuncSetAttribute(fsz_decompress_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
+    cudaFuncSetAttribute(fsz_decompress_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         c.smem);
+    cudaFuncSetAttribute(fsz_decompress_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         c.smem);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_decompress_kernel, kThreads, c.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_decompress_kernel<false>, kThreads,
+                                                  c.smem);
     c.sms = sms;
     c.per = per > 0 ? per : 1;
     c.grid = sms * c.per;
@@ -398,9 +412,12 @@ LaunchCfg decompress_cfg() {
   return cfg;
 }
 
-void launch_decompress(const KernelArgs& a, cudaStream_t st) {
+void launch_decompress(const KernelArgs& a, cudaStream_t st, bool any) {
   const LaunchCfg c = decompress_cfg();
-  fsz_decompress_kernel<<<sched_grid(c, kSchedDecompress), kThreads, c.smem, st>>>(a);
+  if (any)
+    fsz_decompress_kernel<true><<<sched_grid(c, kSchedDecompress), kThreads, c.smem, st>>>(a);
+  else
+    fsz_decompress_kernel<false><<<sched_grid(c, kSchedDecompress), kThreads, c.smem, st>>>(a);
 }
 
 }  // namespace fsz

@@ -305,8 +305,7 @@ __device__ __forceinline__ void transpose8x8(uint32_t& lo, uint32_t& hi) {
 
 // One step of an inclusive scan: v += v of lane - o, where that lane exists within the
 // segment of `width` lanes. The shuffle's own in-range predicate guards the add, so no
-// lane-index compare is needed. scan_step_up_seg takes the segment as the shuffle's
-// segment-mask operand, (32 - width) << 8, at run time.
+// lane-index compare is needed.
 template <int kWidth = 32>
 __device__ __forceinline__ uint32_t scan_step_up(uint32_t v, int o) {
   asm("{\n\t.reg .pred p;\n\t.reg .b32 y;\n\t"
@@ -316,14 +315,7 @@ __device__ __forceinline__ uint32_t scan_step_up(uint32_t v, int o) {
       : "r"(o), "n"((32 - kWidth) << 8));
   return v;
 }
-__device__ __forceinline__ uint32_t scan_step_up_seg(uint32_t v, int o, uint32_t segmask) {
-  asm("{\n\t.reg .pred p;\n\t.reg .b32 y;\n\t"
-      "shfl.sync.up.b32 y|p, %0, %1, %2, 0xffffffff;\n\t"
-      "@p add.u32 %0, %0, y;\n\t}"
-      : "+r"(v)
-      : "r"(o), "r"(segmask));
-  return v;
-}
+
 
 // 4x4 byte transpose across the 4 lanes of a group (t = lane & 3): afterwards byte k of
 // lane t's word is byte t of lane k's word. Two exchange steps (xor 1, xor 2).
@@ -489,12 +481,17 @@ LaunchCfg compress_cfg();
 LaunchCfg decompress_cfg();
 
 void launch_stats(const KernelArgs& a, cudaStream_t st);
-void launch_compress(const KernelArgs& a, cudaStream_t st);
+// Compression kernel instances (feature-toggle builds of one kernel): the full method;
+// with switched-off features honoured per field (fsz_compress_features, batches); the
+// multipass evaluation's encoding pass (selection from a.given_costs).
+enum CompressKind { kCompressFull = 0, kCompressFeatures = 1, kCompressGiven = 2 };
+void launch_compress(const KernelArgs& a, cudaStream_t st, CompressKind kind = kCompressFull);
 // The multipass evaluation: one pass per variant writing its tile costs, then the
 // compression kernel selecting from them (a.given_costs).
 void launch_cost_pass(const KernelArgs& a, int variant, uint32_t* costs, cudaStream_t st);
-void launch_compress_given(const KernelArgs& a, cudaStream_t st);
-void launch_decompress(const KernelArgs& a, cudaStream_t st);
+
+// any: the instance that also decodes streams without the cross-block state.
+void launch_decompress(const KernelArgs& a, cudaStream_t st, bool any = false);
 void launch_setup_compress(const KernelArgs& a, const FieldInfo& fi, cudaStream_t st);
 void launch_setup_decompress(const KernelArgs& a, const uint8_t* in, uint64_t in_bytes, float* out,
                              uint64_t cap_elems, uint64_t chunk_cap, cudaStream_t st);

@@ -27,7 +27,7 @@ OFF_CROSS_BLOCK, OFF_CENTERING, OFF_LZ2 = 1, 2, 4
 
 # Every entry point include/fsz.h declares.
 EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_bytes", "fsz_compress",
-           "fsz_compress_features", "fsz_compress_multipass",
+           "fsz_compress_features", "fsz_compress_multipass", "fsz_decompress_any",
            "fsz_compress_prepare", "fsz_compress_encode", "fsz_decompress", "fsz_compress_batched",
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
            "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc",
@@ -140,6 +140,8 @@ def lib():
             L.fsz_compress_features.restype = i32
             L.fsz_compress_multipass.argtypes = [P, FszDims, i32, f64, P, u64, P, P, P, u64, P]
             L.fsz_compress_multipass.restype = i32
+            L.fsz_decompress_any.argtypes = [P, u64, P, u64, P, u64, P]
+            L.fsz_decompress_any.restype = i32
             L.fsz_decompress.argtypes = [P, u64, P, u64, P, u64, P]
             L.fsz_decompress.restype = i32
             L.fsz_compress_batched.argtypes = [P, u32, u64, P, u64, P]
@@ -416,8 +418,10 @@ def compress_multipass(x, eb: float, mode: int = EB_REL, shape=None, ws: Workspa
 
 
 def decompress(stream_bytes, n: int | None = None, ws: Workspace | None = None, out=None,
-               stream=None, check: bool = True):
-    """Decompress a device byte tensor holding one stream. Returns a float32 tensor."""
+               stream=None, check: bool = True, any_stream: bool = False):
+    """Decompress a device byte tensor holding one stream. Returns a float32 tensor.
+    any_stream: through fsz_decompress_any, which also takes streams compressed without
+    the cross-block state (OFF_CROSS_BLOCK)."""
     import torch
     assert stream_bytes.dtype == torch.uint8 and stream_bytes.is_cuda
     if n is None:
@@ -429,7 +433,8 @@ def decompress(stream_bytes, n: int | None = None, ws: Workspace | None = None, 
     if src.data_ptr() % 16:
         src = src.clone()
     sp = _stream_ptr(stream)
-    st = fsz_decompress(src.data_ptr(), src.numel(), out.data_ptr(), out.numel(), ws.ptr, ws.bytes, sp)
+    fn = lib().fsz_decompress_any if any_stream else fsz_decompress
+    st = fn(src.data_ptr(), src.numel(), out.data_ptr(), out.numel(), ws.ptr, ws.bytes, sp)
     _check(st, "fsz_decompress")
     if check:
         _check(fsz_check(ws.ptr, sp), "fsz_decompress (device)")

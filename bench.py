@@ -594,8 +594,16 @@ def main():
     if st != fsz.OK:
         raise fsz.FszError(st, "warm-up")
     sizes = nbytes.cpu().tolist()
-    # quick self-check of the last job's reconstruction against its bound
-    p_last = recon.double().sub(jobs[-1][1].double()).abs().max().item()
+    # rate-distortion point of every job (Sec. 6.2, Fig. 8), on the device, untimed:
+    # decompress its stream and compare with the original
+    qual = []
+    for j, (name, x, rel) in enumerate(jobs):
+        st = L.fsz_decompress(outs[j].data_ptr(), sizes[j], recon.data_ptr(), n, ws.data_ptr(), wsb, sp)
+        if st != fsz.OK or fsz.fsz_check(ws.data_ptr(), sp) != fsz.OK:
+            raise fsz.FszError(st, "quality decode")
+        eb = rel * (float(x.max().item()) - float(x.min().item()))
+        qual.append(fsz.quality(x, recon, eb, sizes[j]))
+    p_last = qual[-1]["max_abs_err"]
 
     comp_ms, enc_ms, stats_ms, dec_ms = ([[] for _ in jobs] for _ in range(4))
     torch.cuda.synchronize(dev)
@@ -754,6 +762,9 @@ def main():
     for j, (name, x, rel) in enumerate(jobs):
         med = lambda v: statistics.median(v)
         per_job.append({"field": name, "rel": rel, "cr": 4 * n / sizes[j], "bytes": sizes[j],
+                        "psnr_db": qual[j]["psnr_db"], "bit_rate": qual[j]["bit_rate"],
+                        "nrmse": qual[j]["nrmse"], "max_abs_err": qual[j]["max_abs_err"],
+                        "errors_over_bound": qual[j]["over_bound"],
                         "compress_gbs": 4 * n / med(comp_ms[j]) / 1e6,
                         "encode_kernel_gbs": 4 * n / med(enc_ms[j]) / 1e6,
                         "encode_kernel_hbm_gbs": (4 * n + sizes[j]) / med(enc_ms[j]) / 1e6,

@@ -170,6 +170,33 @@ fsz_status fsz_decompress_any(const void* d_in, uint64_t in_bytes, float* d_out,
                               uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
                               fsz_stream stream);
 
+/* ------------------------------------------------------------------ quality */
+
+/* Reconstruction quality for the rate-distortion evaluation of Sec. 6.2 (Fig. 8: PSNR
+ * against bit rate). Written to DEVICE memory by fsz_quality_stats. */
+typedef struct {
+  uint64_t n;           /* elements compared */
+  uint64_t over_bound;  /* elements with |d - d'| > eb (0 for a stream of this library) */
+  double max_abs_err;   /* max |d - d'| */
+  double sum_sq_err;    /* sum of (d - d')^2 */
+  double min, max;      /* value range of the original d */
+  double psnr_db;       /* 20 log10(max - min) - 10 log10(sum_sq_err / n); +inf if exact */
+  double nrmse;         /* sqrt(sum_sq_err / n) / (max - min) (0 for a constant field) */
+  double bit_rate;      /* bits per value: 8 stream_bytes / n */
+} fsz_quality;
+
+/* Workspace for fsz_quality_stats (a few hundred KB; independent of n). */
+uint64_t fsz_quality_workspace_bytes(void);
+
+/* Compares the original d_orig with its reconstruction d_recon (n float32 each, device,
+ * 16-byte aligned) and writes the statistics to *d_out (device, 16-byte aligned).
+ * Differences are float32 (exact for the close values a bounded reconstruction holds),
+ * their squares summed in float32 over 8 elements and then in float64 in a fixed order:
+ * the sum is deterministic and within a relative 1e-6 of the exact one. */
+fsz_status fsz_quality_stats(const float* d_orig, const float* d_recon, uint64_t n, double eb,
+                             uint64_t stream_bytes, fsz_quality* d_out, void* d_ws,
+                             uint64_t ws_bytes, fsz_stream stream);
+
 /* ------------------------------------------------------------------ batches */
 
 /* Compress nfields fields in one persistent launch (plus a planning kernel and the

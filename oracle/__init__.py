@@ -101,12 +101,20 @@ def lib():
                                           ctypes.c_int]
             L.fszo_compress_tiles_f.argtypes = [P, u64, f32, u64, u64, u32, P, P, u64, P]
             L.fszo_read_preamble_f.argtypes = [P, u64, P, P, P, P, P, P, P]
+            L.fszo_quality.argtypes = [P, P, u64, f64, u64, P]
             _lib = L
     return _lib
 
 
 def _ptr(a: np.ndarray) -> int:
     return a.ctypes.data
+
+
+class Quality(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("over_bound", ctypes.c_uint64),
+                ("max_abs_err", ctypes.c_double), ("sum_sq_err", ctypes.c_double),
+                ("vmin", ctypes.c_double), ("vmax", ctypes.c_double), ("psnr_db", ctypes.c_double),
+                ("nrmse", ctypes.c_double), ("bit_rate", ctypes.c_double)]
 
 
 class OracleError(RuntimeError):
@@ -243,6 +251,18 @@ def decompress(stream: bytes, q: bool = False) -> np.ndarray:
     if st != OK:
         raise OracleError(st, "decompress")
     return out[:n]
+
+
+def quality(d: np.ndarray, y: np.ndarray, eb: float, stream_bytes: int = 0) -> dict:
+    """Reconstruction quality (PSNR, NRMSE, max error, bit rate) of y against d."""
+    d = np.ascontiguousarray(d, dtype=np.float32).ravel()
+    y = np.ascontiguousarray(y, dtype=np.float32).ravel()
+    assert d.size == y.size
+    q = Quality()
+    st = lib().fszo_quality(_ptr(d), _ptr(y), d.size, eb, stream_bytes, ctypes.byref(q))
+    if st != OK:
+        raise OracleError(st, "quality")
+    return {k: getattr(q, k) for k, _ in Quality._fields_}
 
 
 def decompress_status(stream: bytes, cap: int | None = None) -> int:

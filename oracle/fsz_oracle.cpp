@@ -583,6 +583,34 @@ int decode_to_q(const uint8_t* in, uint64_t in_bytes, std::vector<int32_t>& qout
 
 }  // namespace
 
+// PSNR against the original's value range, the usual definition of the error-bounded
+// compression literature (the paper plots it, Fig. 8, without printing the formula).
+int fszo_quality(const float* d, const float* y, uint64_t n, double eb, uint64_t stream_bytes,
+                 fszo_quality_t* q) {
+  if (q == nullptr || n == 0 || d == nullptr || y == nullptr) return FSZO_ERR_INVALID_ARG;
+  q->n = n;
+  q->over_bound = 0;
+  q->max_abs_err = 0.0;
+  q->sum_sq_err = 0.0;
+  q->vmin = double(d[0]);
+  q->vmax = double(d[0]);
+  for (uint64_t i = 0; i < n; ++i) {
+    const double e = double(d[i]) - double(y[i]);
+    const double a = std::fabs(e);
+    if (a > q->max_abs_err) q->max_abs_err = a;
+    if (a > eb) q->over_bound += 1;
+    q->sum_sq_err += e * e;
+    if (double(d[i]) < q->vmin) q->vmin = double(d[i]);
+    if (double(d[i]) > q->vmax) q->vmax = double(d[i]);
+  }
+  const double range = q->vmax - q->vmin;
+  const double mse = q->sum_sq_err / double(n);
+  q->psnr_db = mse > 0.0 ? 20.0 * std::log10(range) - 10.0 * std::log10(mse) : INFINITY;
+  q->nrmse = range > 0.0 ? std::sqrt(mse) / range : 0.0;
+  q->bit_rate = 8.0 * double(stream_bytes) / double(n);
+  return FSZO_OK;
+}
+
 int fszo_decompress_q(const uint8_t* in, uint64_t in_bytes, int32_t* q_out,
                       uint64_t out_capacity_elems, uint64_t* n_out) {
   std::vector<int32_t> q; uint64_t n = 0; float s;

@@ -121,6 +121,17 @@ int fszo_compress_tiles_f(const float* d, uint64_t n, float r, uint64_t t0, uint
 int fszo_read_preamble_f(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint32_t* ndim,
                          uint64_t dims[3], double* eb_req, float* s, uint64_t* data_bytes,
                          uint32_t* features_off);
+/* Reconstruction quality for the rate-distortion evaluation of Sec. 6.2 (Fig. 8: PSNR
+ * against bit rate). Differences in float64: max |d - d'|, the sum of (d - d')^2 (in
+ * element order), elements with |d - d'| > eb, the original's min and max; then
+ * PSNR = 20 log10(max - min) - 10 log10(sum / n) (+inf for an exact reconstruction),
+ * NRMSE = sqrt(sum / n) / (max - min), bit rate = 8 stream_bytes / n. */
+typedef struct {
+  uint64_t n, over_bound;
+  double max_abs_err, sum_sq_err, vmin, vmax, psnr_db, nrmse, bit_rate;
+} fszo_quality_t;
+int fszo_quality(const float* d, const float* y, uint64_t n, double eb, uint64_t stream_bytes,
+                 fszo_quality_t* q);
 /* Whole-stream decompression (Sec. 3.1 "Decompression", steps d1-d5). */
 int fszo_decompress(const uint8_t* in, uint64_t in_bytes, float* out, uint64_t out_capacity_elems,
                     uint64_t* n_out);

@@ -28,6 +28,7 @@ OFF_CROSS_BLOCK, OFF_CENTERING, OFF_LZ2 = 1, 2, 4
 # Every entry point include/fsz.h declares.
 EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_bytes", "fsz_compress",
            "fsz_compress_features", "fsz_compress_multipass", "fsz_decompress_any",
+           "fsz_quality_workspace_bytes", "fsz_quality_stats",
            "fsz_compress_prepare", "fsz_compress_encode", "fsz_decompress", "fsz_compress_batched",
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
            "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc",
@@ -142,6 +143,10 @@ def lib():
             L.fsz_compress_multipass.restype = i32
             L.fsz_decompress_any.argtypes = [P, u64, P, u64, P, u64, P]
             L.fsz_decompress_any.restype = i32
+            L.fsz_quality_workspace_bytes.argtypes = []
+            L.fsz_quality_workspace_bytes.restype = u64
+            L.fsz_quality_stats.argtypes = [P, P, u64, f64, u64, P, P, u64, P]
+            L.fsz_quality_stats.restype = i32
             L.fsz_decompress.argtypes = [P, u64, P, u64, P, u64, P]
             L.fsz_decompress.restype = i32
             L.fsz_compress_batched.argtypes = [P, u32, u64, P, u64, P]
@@ -439,6 +444,37 @@ def decompress(stream_bytes, n: int | None = None, ws: Workspace | None = None, 
     if check:
         _check(fsz_check(ws.ptr, sp), "fsz_decompress (device)")
     return out[:n]
+
+
+# ------------------------------------------------------------------ quality
+
+QUALITY_FIELDS = ["n", "over_bound", "max_abs_err", "sum_sq_err", "min", "max", "psnr_db", "nrmse",
+                  "bit_rate"]
+
+
+def quality(orig, recon, eb: float, stream_bytes: int = 0, stream=None) -> dict:
+    """Reconstruction quality on the device (fsz_quality_stats): PSNR, NRMSE, max error,
+    errors above eb, value range, bit rate. Waits for the result."""
+    import numpy as np
+    import torch
+    assert orig.dtype == torch.float32 and recon.dtype == torch.float32
+    assert orig.is_cuda and orig.numel() == recon.numel()
+    n = orig.numel()
+    out = torch.zeros(16, dtype=torch.float64, device=orig.device)
+    wsb = lib().fsz_quality_workspace_bytes()
+    ws = _dev_buffer(wsb, orig.device)
+    a, b = orig.contiguous(), recon.contiguous()
+    if a.data_ptr() % 16:
+        a = a.clone()
+    if b.data_ptr() % 16:
+        b = b.clone()
+    sp = _stream_ptr(stream)
+    _check(lib().fsz_quality_stats(a.data_ptr(), b.data_ptr(), n, float(eb), int(stream_bytes),
+                                   out.data_ptr(), ws.data_ptr(), wsb, sp), "fsz_quality_stats")
+    raw = out[:9].cpu().numpy()
+    ints = raw[:2].view(np.uint64)
+    vals = {k: float(v) for k, v in zip(QUALITY_FIELDS[2:], raw[2:])}
+    return {"n": int(ints[0]), "over_bound": int(ints[1]), **vals}
 
 
 # ------------------------------------------------------------------ batches

@@ -197,3 +197,38 @@ def test_independent_block_stream_decodes_per_block():
     q1 = O.decompress(bytes(s), q=True)
     diff = np.nonzero(q1 != q0)[0]
     assert diff.size > 0 and diff.min() >= 256 + 64 and diff.max() < 256 + 96
+
+
+# ---------------------------------------------------------------- quality (Sec. 6.2, Fig. 8)
+
+def test_quality_closed_forms():
+    """A constant error c: sum c^2 n, max c, PSNR = 20 log10(range / c); an exact copy:
+    infinite PSNR; the bound count; bits per value from the stream size."""
+    n = 4096
+    d = ((np.arange(n) % 129) * 0.0625 - 3.0).astype(np.float32)   # range 8, d + c exact
+    c = np.float32(0.25)
+    q = O.quality(d, d + c, eb=0.3, stream_bytes=n // 4)        # 2 bits per value
+    assert q["n"] == n and q["over_bound"] == 0
+    assert q["max_abs_err"] == 0.25 and q["sum_sq_err"] == n * 0.0625
+    assert q["vmin"] == -3.0 and q["vmax"] == 5.0
+    assert q["psnr_db"] == pytest.approx(20 * np.log10(8.0 / 0.25), abs=1e-12)
+    assert q["nrmse"] == pytest.approx(0.25 / 8.0, abs=1e-15)
+    assert q["bit_rate"] == 2.0
+    assert O.quality(d, d + c, eb=0.2)["over_bound"] == n
+    assert np.isinf(O.quality(d, d.copy(), eb=0.1)["psnr_db"])
+
+
+def test_quality_matches_numpy_on_a_round_trip():
+    x = _field()
+    s = O.compress(x, 1e-3, O.REL)
+    y = O.decompress(s)
+    eb = 1e-3 * (float(x.max()) - float(x.min()))
+    q = O.quality(x, y, eb, len(s))
+    e = x.astype(np.float64) - y.astype(np.float64)
+    assert q["over_bound"] == 0 and q["max_abs_err"] == float(np.abs(e).max()) <= eb
+    assert q["sum_sq_err"] == pytest.approx(float(np.sum(e * e)), rel=1e-12)
+    rng = float(x.max()) - float(x.min())
+    assert q["psnr_db"] == pytest.approx(20 * np.log10(rng) - 10 * np.log10(np.mean(e * e)), abs=1e-9)
+    assert q["bit_rate"] == pytest.approx(8 * len(s) / x.size)
+    # an error-bounded quantizer with step 2 eb: MSE near (2 eb)^2 / 12 on rough data
+    assert 20 * np.log10(rng / (2 * eb / np.sqrt(12))) - 1.5 < q["psnr_db"] < 20 * np.log10(rng / (2 * eb / np.sqrt(12))) + 1.5

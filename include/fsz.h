@@ -163,6 +163,17 @@ fsz_status fsz_decompress(const void* d_in, uint64_t in_bytes, float* d_out,
                           uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
                           fsz_stream stream);
 
+/* fsz_decompress into an output that already holds zeros: tiles whose 8 blocks all have
+ * rate 0 and no mean decode to +0.0 and are neither decoded nor written (the pre-zero of
+ * Sec. 3.1, which the paper enables above a compression ratio of 100). It pays off when
+ * the zeros are already there (e.g. a buffer reused for sparse fields): on GB300 the full
+ * decoder writes such a field at near the HBM write rate, so zero-filling first costs
+ * more than it saves. Streams without the cross-block state are refused as by
+ * fsz_decompress. */
+fsz_status fsz_decompress_prezeroed(const void* d_in, uint64_t in_bytes, float* d_out,
+                                    uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
+                                    fsz_stream stream);
+
 /* fsz_decompress for any stream, including those compressed with FSZ_OFF_CROSS_BLOCK
  * (its inverse prediction restarts at every block). About 3 % slower than fsz_decompress
  * on the full method's streams, for which fsz_decompress is the call. */

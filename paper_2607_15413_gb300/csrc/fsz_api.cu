@@ -111,11 +111,10 @@ fsz_status prepare_one(const float* d_in, fsz_dims dims, fsz_eb_mode mode, doubl
   return launched();
 }
 
-// One stream's decompression; `any` selects the decoder instance that also takes streams
-// without the cross-block state.
+// One stream's decompression with the given decoder instance.
 fsz_status decompress_one(const void* d_in, uint64_t in_bytes, float* d_out,
                           uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
-                          fsz_stream stream, bool any) {
+                          fsz_stream stream, DecompressKind kind) {
   if (d_in == nullptr || d_out == nullptr || d_ws == nullptr) return FSZ_ERR_INVALID_ARG;
   if (misaligned(d_in) || misaligned(d_out) || misaligned(d_ws)) return FSZ_ERR_ALIGN;
   if (out_capacity_elems > kMaxElems) out_capacity_elems = kMaxElems;
@@ -126,7 +125,7 @@ fsz_status decompress_one(const void* d_in, uint64_t in_bytes, float* d_out,
   const KernelArgs a = make_args(d_ws, L);
   launch_setup_decompress(a, static_cast<const uint8_t*>(d_in), in_bytes, d_out, out_capacity_elems,
                           L.chunk_cap, s);
-  launch_decompress(a, s, any);
+  launch_decompress(a, s, kind);
   return launched();
 }
 
@@ -239,13 +238,22 @@ fsz_status fsz_compress_multipass(const float* d_in, fsz_dims dims, fsz_eb_mode 
 
 fsz_status fsz_decompress(const void* d_in, uint64_t in_bytes, float* d_out, uint64_t out_capacity_elems,
                           void* d_ws, uint64_t ws_bytes, fsz_stream stream) {
-  return decompress_one(d_in, in_bytes, d_out, out_capacity_elems, d_ws, ws_bytes, stream, false);
+  return decompress_one(d_in, in_bytes, d_out, out_capacity_elems, d_ws, ws_bytes, stream,
+                        kDecompressFull);
+}
+
+fsz_status fsz_decompress_prezeroed(const void* d_in, uint64_t in_bytes, float* d_out,
+                                    uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
+                                    fsz_stream stream) {
+  return decompress_one(d_in, in_bytes, d_out, out_capacity_elems, d_ws, ws_bytes, stream,
+                        kDecompressPrezeroed);
 }
 
 fsz_status fsz_decompress_any(const void* d_in, uint64_t in_bytes, float* d_out,
                               uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
                               fsz_stream stream) {
-  return decompress_one(d_in, in_bytes, d_out, out_capacity_elems, d_ws, ws_bytes, stream, true);
+  return decompress_one(d_in, in_bytes, d_out, out_capacity_elems, d_ws, ws_bytes, stream,
+                        kDecompressAny);
 }
 
 fsz_status fsz_compress_batched(const fsz_cfield* d_fields, uint32_t nfields, uint64_t n_total,
@@ -323,6 +331,7 @@ fsz_status fsz_read_header(const void* h_first64, uint64_t* n, fsz_dims* dims, d
   for (uint32_t k = 0; k < nd; ++k) d.dims[k] = u64(16 + 8 * k);
   uint64_t prod = 0;
   if (dims_count(d, &prod) != FSZ_OK || prod != nn) return FSZ_ERR_CORRUPT;
+  if (!features_valid(u32(52))) return FSZ_ERR_CORRUPT;
   double e;
   std::memcpy(&e, p + 40, 8);
   float sv;

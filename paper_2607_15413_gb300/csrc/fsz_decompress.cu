@@ -38,6 +38,8 @@ struct ChunkRec {
   uint64_t hdr[kDChunkTiles];
   uint64_t boff[kDChunkTiles];  // block word offsets of each tile (block_word_offsets)
   uint32_t toff[kDChunkTiles];
+  uint8_t list[kDChunkTiles];   // pre-zeroed output: the tiles to decode (not all-zero ones)
+  uint32_t ndec;                // how many
   FieldInfo* fi;
   float* dout;           // the chunk's first output element
   const uint8_t* sin;    // the field's stream
@@ -178,7 +180,10 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
   return __all_sync(FULL, good);
 }
 
-template <bool kAny>
+// kAny: also decodes streams without the cross-block state. kPrezero: the output already
+// holds zeros; tiles whose 8 blocks all have rate 0 and no mean (all +0.0) are neither
+// decoded nor written (the adaptive pre-zero of Sec. 3.1 for high compression ratios).
+template <bool kAny, bool kPrezero>
 __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   DecompressSmem& S = *reinterpret_cast<DecompressSmem*>(smem_raw);
@@ -249,6 +254,12 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
         if (lane >= o) inc += y;
       }
       if (lane < kDChunkTiles) q.toff[lane] = inc - mine;
+      uint32_t dmask = 0;
+      if constexpr (kPrezero) {
+        const bool dec = lane < ntiles && (hb & 0x1F1F1F1F1F1F1F5FULL) != 0;
+        dmask = __ballot_sync(FULL, dec);
+        if (dec) q.list[__popc(dmask & ((1u << lane) - 1u))] = uint8_t(lane);
+      }
       const uint32_t tot = __shfl_sync(FULL, inc, 31);
       if (lane == 0) {
         if (uint64_t(c) != a.skip_chunk) st_flag(a.flags + c, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
@@ -266,6 +277,7 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
         q.ntiles = uint32_t(ntiles);
         q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kDChunkElems)));
         q.step = fi->s;
+        q.ndec = uint32_t(__popc(dmask));
         q.indep = (foff & kOffCross) ? 1u : 0u;
       }
       __syncwarp();
@@ -359,7 +371,9 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
       const uint32_t cnt = st.cnt;
       float* dout = st.dout;
       const uint8_t* pay = S.payload[p] + st.shift;
-      for (int tl = warp; tl < ntiles; tl += kDecodeWarps) {
+      const int nloop = kPrezero ? int(st.ndec) : ntiles;
+      for (int i = warp; i < nloop; i += kDecodeWarps) {
+        const int tl = kPrezero ? int(st.list[i]) : i;
         float* buf = S.out[warp][nstore & 1u];
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         __syncwarp();
@@ -395,15 +409,17 @@ LaunchCfg decompress_cfg() {
   static LaunchCfg cfg = [] {
     LaunchCfg c;
     c.smem = int(sizeof(DecompressSmem));
-    cudaFuncSetAttribute(fsz_decompress_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         c.smem);
-    cudaFuncSetAttribute(fsz_decompress_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         c.smem);
+    cudaFuncSetAttribute(fsz_decompress_kernel<false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
+    cudaFuncSetAttribute(fsz_decompress_kernel<true, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
+    cudaFuncSetAttribute(fsz_decompress_kernel<false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, c.smem);
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_decompress_kernel<false>, kThreads,
-                                                  c.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_decompress_kernel<false, false>,
+                                                  kThreads, c.smem);
     c.sms = sms;
     c.per = per > 0 ? per : 1;
     c.grid = sms * c.per;
@@ -412,12 +428,15 @@ LaunchCfg decompress_cfg() {
   return cfg;
 }
 
-void launch_decompress(const KernelArgs& a, cudaStream_t st, bool any) {
+void launch_decompress(const KernelArgs& a, cudaStream_t st, DecompressKind kind) {
   const LaunchCfg c = decompress_cfg();
-  if (any)
-    fsz_decompress_kernel<true><<<sched_grid(c, kSchedDecompress), kThreads, c.smem, st>>>(a);
+  const int g = sched_grid(c, kSchedDecompress);
+  if (kind == kDecompressAny)
+    fsz_decompress_kernel<true, false><<<g, kThreads, c.smem, st>>>(a);
+  else if (kind == kDecompressPrezeroed)
+    fsz_decompress_kernel<false, true><<<g, kThreads, c.smem, st>>>(a);
   else
-    fsz_decompress_kernel<false><<<sched_grid(c, kSchedDecompress), kThreads, c.smem, st>>>(a);
+    fsz_decompress_kernel<false, false><<<g, kThreads, c.smem, st>>>(a);
 }
 
 }  // namespace fsz

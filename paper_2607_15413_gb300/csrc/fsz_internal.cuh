@@ -490,8 +490,11 @@ void launch_compress(const KernelArgs& a, cudaStream_t st, CompressKind kind = k
 // compression kernel selecting from them (a.given_costs).
 void launch_cost_pass(const KernelArgs& a, int variant, uint32_t* costs, cudaStream_t st);
 
-// any: the instance that also decodes streams without the cross-block state.
-void launch_decompress(const KernelArgs& a, cudaStream_t st, bool any = false);
+// Decoder instances: the full method's; one that also decodes streams without the
+// cross-block state; one for a pre-zeroed output that skips all-zero tiles.
+enum DecompressKind { kDecompressFull = 0, kDecompressAny = 1, kDecompressPrezeroed = 2 };
+void launch_decompress(const KernelArgs& a, cudaStream_t st,
+                       DecompressKind kind = kDecompressFull);
 void launch_setup_compress(const KernelArgs& a, const FieldInfo& fi, cudaStream_t st);
 void launch_setup_decompress(const KernelArgs& a, const uint8_t* in, uint64_t in_bytes, float* out,
                              uint64_t cap_elems, uint64_t chunk_cap, cudaStream_t st);

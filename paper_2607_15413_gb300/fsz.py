@@ -28,6 +28,7 @@ OFF_CROSS_BLOCK, OFF_CENTERING, OFF_LZ2 = 1, 2, 4
 # Every entry point include/fsz.h declares.
 EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_bytes", "fsz_compress",
            "fsz_compress_features", "fsz_compress_multipass", "fsz_decompress_any",
+           "fsz_decompress_prezeroed",
            "fsz_quality_workspace_bytes", "fsz_quality_stats",
            "fsz_compress_prepare", "fsz_compress_encode", "fsz_decompress", "fsz_compress_batched",
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
@@ -143,6 +144,8 @@ def lib():
             L.fsz_compress_multipass.restype = i32
             L.fsz_decompress_any.argtypes = [P, u64, P, u64, P, u64, P]
             L.fsz_decompress_any.restype = i32
+            L.fsz_decompress_prezeroed.argtypes = [P, u64, P, u64, P, u64, P]
+            L.fsz_decompress_prezeroed.restype = i32
             L.fsz_quality_workspace_bytes.argtypes = []
             L.fsz_quality_workspace_bytes.restype = u64
             L.fsz_quality_stats.argtypes = [P, P, u64, f64, u64, P, P, u64, P]
@@ -423,22 +426,27 @@ def compress_multipass(x, eb: float, mode: int = EB_REL, shape=None, ws: Workspa
 
 
 def decompress(stream_bytes, n: int | None = None, ws: Workspace | None = None, out=None,
-               stream=None, check: bool = True, any_stream: bool = False):
+               stream=None, check: bool = True, any_stream: bool = False, out_is_zero: bool = False):
     """Decompress a device byte tensor holding one stream. Returns a float32 tensor.
     any_stream: through fsz_decompress_any, which also takes streams compressed without
-    the cross-block state (OFF_CROSS_BLOCK)."""
+    the cross-block state (OFF_CROSS_BLOCK). out_is_zero: `out` already holds zeros (or,
+    with out=None, is allocated zero-filled): the all-zero tiles are neither decoded nor
+    written (fsz_decompress_prezeroed); pays off for sparse fields when the zeros are
+    already there."""
     import torch
     assert stream_bytes.dtype == torch.uint8 and stream_bytes.is_cuda
     if n is None:
         n = fsz_read_header(stream_bytes[:64].cpu().numpy().tobytes())["n"]
     if out is None:
-        out = torch.empty(max(n, 4), dtype=torch.float32, device=stream_bytes.device)
+        alloc = torch.zeros if out_is_zero else torch.empty
+        out = alloc(max(n, 4), dtype=torch.float32, device=stream_bytes.device)
     ws = ws if ws is not None else Workspace(out.numel(), stream_bytes.device)
     src = stream_bytes
     if src.data_ptr() % 16:
         src = src.clone()
     sp = _stream_ptr(stream)
-    fn = lib().fsz_decompress_any if any_stream else fsz_decompress
+    fn = (lib().fsz_decompress_any if any_stream
+          else lib().fsz_decompress_prezeroed if out_is_zero else fsz_decompress)
     st = fn(src.data_ptr(), src.numel(), out.data_ptr(), out.numel(), ws.ptr, ws.bytes, sp)
     _check(st, "fsz_decompress")
     if check:

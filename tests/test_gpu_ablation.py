@@ -169,3 +169,45 @@ def test_multipass_refuses_missing_or_misaligned_costs(fszlib):
     args = (x.data_ptr(), fszlib.make_dims((5000,)), 1, 1e-3, out.data_ptr(), out.numel(), None)
     assert L.fsz_compress_multipass(*args, None, ws.ptr, ws.bytes, sp) == fszlib.ERR_INVALID_ARG
     assert L.fsz_compress_multipass(*args, costs.data_ptr() + 4, ws.ptr, ws.bytes, sp) == fszlib.ERR_ALIGN
+
+
+# ---------------------------------------------------------------- adaptive pre-zero (Sec. 3.1)
+
+def _sparse(n, seed):
+    """Mostly exact zeros (about 99 %), a smooth band elsewhere: a stream of CR above 100."""
+    x = np.zeros(n, np.float32)
+    band = inputs.sinusoids(n // 128, seed=seed) + np.float32(3.0)
+    x[n // 2: n // 2 + band.size] = band
+    return x
+
+
+def _zero_tiles(stream: bytes, n: int) -> np.ndarray:
+    T = (n + 255) // 256
+    h = np.frombuffer(stream[64: 64 + 8 * T], np.uint64)
+    return (h & np.uint64(0x1F1F1F1F1F1F1F5F)) == 0
+
+
+@pytest.mark.parametrize("field", ["sparse", "zero_slabs", "offset"])
+def test_prezeroed_decode_skips_exactly_the_zero_tiles(fszlib, oracle, field):
+    dev = _cuda()
+    n = 4096 * 24 + 77
+    x = _sparse(n, 2) if field == "sparse" else FIELDS[field](n, 2)
+    ref = oracle.compress(x, 1e-3, oracle.REL)
+    sb = torch.from_numpy(np.frombuffer(ref, np.uint8).copy()).to(dev)
+    yref = oracle.decompress(ref).view(np.uint32)
+    # into zeros: identical to the full decode
+    y = fszlib.decompress(sb, n=n, out_is_zero=True).cpu().numpy()
+    assert np.array_equal(y.view(np.uint32), yref)
+    # into a NaN-filled buffer: the all-zero tiles are not written, all others are
+    out = torch.full((n,), float("nan"), device=dev)
+    ws = fszlib.Workspace(n, dev)
+    sp = torch.cuda.current_stream().cuda_stream
+    assert fszlib.lib().fsz_decompress_prezeroed(sb.data_ptr(), sb.numel(), out.data_ptr(), n, ws.ptr,
+                                                 ws.bytes, sp) == fszlib.OK
+    assert fszlib.fsz_check(ws.ptr, sp) == fszlib.OK
+    got = out.cpu().numpy()
+    zt = np.repeat(_zero_tiles(ref, n), 256)[:n]
+    assert np.all(np.isnan(got[zt]))
+    assert np.array_equal(got[~zt].view(np.uint32), yref[~zt])
+    if field == "sparse":
+        assert zt.mean() > 0.9 and 4 * n / len(ref) > 100

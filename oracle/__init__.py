@@ -102,6 +102,12 @@ def lib():
             L.fszo_compress_tiles_f.argtypes = [P, u64, f32, u64, u64, u32, P, P, u64, P]
             L.fszo_read_preamble_f.argtypes = [P, u64, P, P, P, P, P, P, P]
             L.fszo_quality.argtypes = [P, P, u64, f64, u64, P]
+            L.fszo_tile_word.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.fszo_tile_word.restype = u32
+            L.fszo_compress_bound_cfg.argtypes = [u64, ctypes.c_int, ctypes.c_int]
+            L.fszo_compress_bound_cfg.restype = u64
+            L.fszo_compress_cfg.argtypes = [P, u32, P, ctypes.c_int, f64, u32, ctypes.c_int,
+                                            ctypes.c_int, P, u64, P]
             _lib = L
     return _lib
 
@@ -211,6 +217,33 @@ def compress(d: np.ndarray, eb: float, mode: int = REL, dims=None, force_variant
     return out[: nb.value].tobytes()
 
 
+# Tile configurations of Sec. 6.5 (Table 8): (B, T) = (elements per block, blocks per tile).
+TILE_CONFIGS = ((32, 4), (32, 8), (32, 16), (64, 4), (64, 8), (64, 16))
+
+
+def tile_word(B: int, T: int) -> int:
+    return lib().fszo_tile_word(B, T)
+
+
+def compress_cfg(d: np.ndarray, eb: float, mode: int = REL, B: int = 32, T: int = 8,
+                 features_off: int = 0, dims=None) -> bytes:
+    """A stream with B-element blocks and T blocks per tile (the four variants costed by
+    definition); B = 32, T = 8 gives the default stream."""
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    if dims is None:
+        dims = d.shape if d.ndim >= 1 else (d.size,)
+    dims_arr = np.zeros(3, np.uint64)
+    dims_arr[: len(dims)] = dims
+    cap = lib().fszo_compress_bound_cfg(d.size, B, T)
+    out = np.zeros(cap, np.uint8)
+    nb = ctypes.c_uint64()
+    st = lib().fszo_compress_cfg(_ptr(d), len(dims), _ptr(dims_arr), mode, eb, features_off, B, T,
+                                 _ptr(out), cap, ctypes.byref(nb))
+    if st != OK:
+        raise OracleError(st, "compress_cfg")
+    return out[: nb.value].tobytes()
+
+
 def compress_tiles(d: np.ndarray, r: float, t0: int, t1: int, features_off: int = 0):
     """Headers (8 bytes per tile) and data of tiles [t0, t1) of field d, given r = 1/s."""
     d = np.ascontiguousarray(d, dtype=np.float32).ravel()
@@ -236,8 +269,12 @@ def read_preamble(stream: bytes):
                                     ctypes.byref(db), ctypes.byref(off))
     if st != OK:
         raise OracleError(st, "read_preamble")
+    w = off.value
+    B = 64 if (w >> 8) & 0xF == 1 else 32
+    T = {0: 8, 1: 4, 2: 16}.get((w >> 12) & 0xF, 0)
     return dict(n=n.value, ndim=ndim.value, dims=tuple(int(x) for x in dims[: ndim.value]),
-                eb=eb.value, s=s.value, data_bytes=db.value, features_off=off.value)
+                eb=eb.value, s=s.value, data_bytes=db.value, features_off=w & 7, method_word=w,
+                B=B, T=T)
 
 
 def decompress(stream: bytes, q: bool = False) -> np.ndarray:

@@ -55,6 +55,16 @@ int32_t wsub(int32_t a, int32_t b) { return int32_t(uint32_t(a) - uint32_t(b)); 
 int32_t wadd(int32_t a, int32_t b) { return int32_t(uint32_t(a) + uint32_t(b)); }
 uint32_t uabs(int32_t v) { return v < 0 ? uint32_t(0) - uint32_t(v) : uint32_t(v); }
 
+// The tile configuration in bits 8-15 of the preamble's method word (Sec. 6.5): B code 0
+// (32) or 1 (64), T code 0 (8), 1 (4) or 2 (16).
+bool tile_cfg_from_word(uint32_t word, int* B, int* T) {
+  const uint32_t bc = (word >> 8) & 0xF, tc = (word >> 12) & 0xF;
+  if (bc > 1 || tc > 2) return false;
+  *B = bc == 1 ? 64 : 32;
+  *T = tc == 1 ? 4 : tc == 2 ? 16 : 8;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -305,6 +315,9 @@ int fszo_select_f(const uint32_t C[4], uint32_t off) {
 }
 
 int fszo_features_valid(uint32_t off) {
+  // bits 8-15 name the tile configuration (fszo_tile_word); the rest are features
+  if (((off >> 8) & 0xF) > 1 || ((off >> 12) & 0xF) > 2) return 0;
+  off &= ~uint32_t(0xFF00);
   if (off & ~uint32_t(FSZO_OFF_CROSS | FSZO_OFF_CENTER | FSZO_OFF_LZ2)) return 0;
   // centring is defined on the carried state (Eq. 4): off with it
   if ((off & FSZO_OFF_CROSS) && !(off & FSZO_OFF_CENTER)) return 0;
@@ -494,9 +507,11 @@ int fszo_read_preamble_f(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint
   const uint32_t off = get_u32(in + 52);
   if (!fszo_features_valid(off)) return FSZO_ERR_CORRUPT;
   uint64_t db = get_u64(in + 56);
-  uint64_t T = tiles_of(nn);
-  if (in_bytes - kPreamble < 8 * T) return FSZO_ERR_CORRUPT;
-  if (db > in_bytes - kPreamble - 8 * T) return FSZO_ERR_CORRUPT;
+  int cfgB = 32, cfgT = 8;
+  tile_cfg_from_word(off, &cfgB, &cfgT);
+  const uint64_t hdr = uint64_t(cfgT) * ((nn + uint64_t(cfgB * cfgT) - 1) / uint64_t(cfgB * cfgT));
+  if (in_bytes - kPreamble < hdr) return FSZO_ERR_CORRUPT;
+  if (db > in_bytes - kPreamble - hdr) return FSZO_ERR_CORRUPT;
   if (n) *n = nn;
   if (ndim) *ndim = nd;
   if (eb_req) *eb_req = eb;
@@ -505,6 +520,250 @@ int fszo_read_preamble_f(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint
   if (features_off) *features_off = off;
   return FSZO_OK;
 }
+
+// ------------------------------------------------------------------ tile configurations
+//
+// Sec. 6.5 (Table 8) sweeps the block size B (elements per block) and the blocks per tile
+// T. A configured tile has B T elements and T header bytes (block 0's byte carries the
+// order and centring flags as in the default). For B = 64 a sign map or bit-plane is an
+// 8-byte word, element j at bit 63 - j, serialised most significant byte first (the B = 32
+// word's rule at twice the width), so S_b = (B / 8)(1 + r_b) bytes for r_b > 0 (Eq. 3).
+// The tile mean sums 8-element runs left to right and then pairs them as the default does
+// (P_j += P_{j+h}, h = R/2 .. 1 for R runs), times 1/(B T). This path evaluates the four
+// variants by their definition (one residual pass per variant) and takes the first strict
+// minimum among the enabled ones. With B = 32, T = 8 it reproduces the default stream.
+
+extern "C" uint32_t fszo_tile_word(int B, int T) {
+  const uint32_t bcode = B == 64 ? 1u : 0u;
+  const uint32_t tcode = T == 4 ? 1u : T == 16 ? 2u : 0u;
+  return (bcode << 8) | (tcode << 12);
+}
+
+namespace {
+
+uint32_t cfg_block_cost(uint32_t rate, int B) {
+  return rate == 0 ? 0u : uint32_t(B / 8) * (1u + rate);
+}
+
+// Serialises the low B bits of w most significant first (B / 8 bytes).
+void put_bits_be(std::vector<uint8_t>& out, uint64_t w, int B) {
+  for (int k = B / 8 - 1; k >= 0; --k) out.push_back(uint8_t(w >> (8 * k)));
+}
+uint64_t get_bits_be(const uint8_t* p, int B) {
+  uint64_t w = 0;
+  for (int k = 0; k < B / 8; ++k) w = (w << 8) | p[k];
+  return w;
+}
+
+int32_t cfg_tile_mu(const std::vector<float>& dt, float r) {
+  const int R = int(dt.size()) / 8;
+  std::vector<float> P(R);
+  for (int j = 0; j < R; ++j) {
+    float acc = dt[8 * j];
+    for (int i = 1; i < 8; ++i) acc = acc + dt[8 * j + i];
+    P[j] = acc;
+  }
+  for (int h = R / 2; h >= 1; h /= 2)
+    for (int j = 0; j < h; ++j) P[j] = P[j] + P[j + h];
+  const float dbar = P[0] * (1.0f / float(dt.size()));  // a power of two: exact
+  return fszo_quantize(dbar, r);
+}
+
+void cfg_residuals(const std::vector<int32_t>& q, int32_t mu, int variant, uint32_t off, int B,
+                   std::vector<int32_t>& l) {
+  const bool centred = (variant == FSZO_LZ1C || variant == FSZO_LZ2C);
+  const bool second = (variant == FSZO_LZ2 || variant == FSZO_LZ2C);
+  int32_t prev1 = 0, prev2 = 0;
+  l.assign(q.size(), 0);
+  for (size_t i = 0; i < q.size(); ++i) {
+    if ((off & FSZO_OFF_CROSS) && i % size_t(B) == 0) prev1 = prev2 = 0;
+    const int32_t qh = centred ? wsub(q[i], mu) : q[i];
+    l[i] = second ? wadd(wsub(qh, wadd(prev1, prev1)), prev2) : wsub(qh, prev1);
+    prev2 = prev1;
+    prev1 = qh;
+  }
+}
+
+// One configured tile: header (T bytes) and data appended (steps 1-5 of Sec. 3.1).
+void cfg_encode_tile(const std::vector<float>& dt, float r, uint32_t off, int B, int T,
+                     uint8_t* header, std::vector<uint8_t>& data) {
+  const int tile = B * T;
+  std::vector<int32_t> q(tile), l;
+  for (int i = 0; i < tile; ++i) q[i] = fszo_quantize(dt[i], r);
+  const int32_t mu = cfg_tile_mu(dt, r);
+  uint32_t C[4];
+  std::vector<uint8_t> rates(4 * size_t(T));
+  for (int v = 0; v < 4; ++v) {
+    cfg_residuals(q, mu, v, off, B, l);
+    uint32_t cost = (v == FSZO_LZ1C || v == FSZO_LZ2C) ? 4u : 0u;
+    for (int b = 0; b < T; ++b) {
+      uint32_t m = 0;
+      for (int j = 0; j < B; ++j) { const uint32_t a = uabs(l[b * B + j]); if (a > m) m = a; }
+      rates[size_t(v) * T + b] = uint8_t(fszo_rate(m));
+      cost += cfg_block_cost(rates[size_t(v) * T + b], B);
+    }
+    C[v] = cost;
+  }
+  const int v = fszo_select_f(C, off);
+  const bool centred = (v == FSZO_LZ1C || v == FSZO_LZ2C);
+  const bool second = (v == FSZO_LZ2 || v == FSZO_LZ2C);
+  for (int b = 0; b < T; ++b) header[b] = rates[size_t(v) * T + b];
+  header[0] = uint8_t(header[0] | (second ? 0x80 : 0) | (centred ? 0x40 : 0));
+  cfg_residuals(q, mu, v, off, B, l);
+  if (centred) {
+    const float muf = float(mu);
+    uint32_t bits;
+    std::memcpy(&bits, &muf, 4);
+    uint8_t tmp[4];
+    put_u32(tmp, bits);
+    data.insert(data.end(), tmp, tmp + 4);
+  }
+  for (int b = 0; b < T; ++b) {
+    const uint32_t rb = rates[size_t(v) * T + b];
+    if (rb == 0) continue;
+    uint64_t sign = 0;
+    for (int j = 0; j < B; ++j)
+      if (l[b * B + j] < 0) sign |= uint64_t(1) << (B - 1 - j);
+    put_bits_be(data, sign, B);
+    for (uint32_t k = 0; k < rb; ++k) {
+      uint64_t w = 0;
+      for (int j = 0; j < B; ++j)
+        if ((uabs(l[b * B + j]) >> k) & 1u) w |= uint64_t(1) << (B - 1 - j);
+      put_bits_be(data, w, B);
+    }
+  }
+}
+
+// Decodes a configured stream (preamble already checked) into q.
+int cfg_decode_to_q(const uint8_t* in, uint64_t in_bytes, uint64_t n, uint32_t word, uint64_t db,
+                    std::vector<int32_t>& qout) {
+  int B, T;
+  if (!tile_cfg_from_word(word, &B, &T)) return FSZO_ERR_CORRUPT;
+  const int tile = B * T;
+  const uint64_t NT = (n + uint64_t(tile) - 1) / uint64_t(tile);
+  if ((in_bytes - kPreamble) / uint64_t(T) < NT) return FSZO_ERR_CORRUPT;
+  const uint8_t* header = in + kPreamble;
+  const uint8_t* data = header + uint64_t(T) * NT;
+  if (db > in_bytes - kPreamble - uint64_t(T) * NT) return FSZO_ERR_CORRUPT;
+  std::vector<uint64_t> offs(NT + 1, 0);
+  for (uint64_t t = 0; t < NT; ++t) {
+    const uint8_t* h = header + uint64_t(T) * t;
+    if (h[0] & 0x20) return FSZO_ERR_CORRUPT;
+    if ((h[0] & 0x80) && (word & FSZO_OFF_LZ2)) return FSZO_ERR_CORRUPT;
+    if ((h[0] & 0x40) && (word & FSZO_OFF_CENTER)) return FSZO_ERR_CORRUPT;
+    uint64_t bytes = (h[0] & 0x40) ? 4 : 0;
+    for (int b = 0; b < T; ++b) {
+      if (b > 0 && (h[b] & 0xE0)) return FSZO_ERR_CORRUPT;
+      bytes += cfg_block_cost(h[b] & 0x1F, B);
+    }
+    offs[t + 1] = offs[t] + bytes;
+  }
+  if (offs[NT] != db) return FSZO_ERR_CORRUPT;
+  qout.assign(size_t(NT) * size_t(tile), 0);
+  std::vector<int32_t> l(tile);
+  for (uint64_t t = 0; t < NT; ++t) {
+    const uint8_t* h = header + uint64_t(T) * t;
+    const bool second = (h[0] & 0x80) != 0, centred = (h[0] & 0x40) != 0;
+    const uint8_t* p = data + offs[t];
+    int32_t mu = 0;
+    if (centred) {
+      const uint32_t bits = get_u32(p);
+      float muf;
+      std::memcpy(&muf, &bits, 4);
+      if (!(std::fabs(muf) <= 16777216.0f) || std::nearbyint(muf) != muf) return FSZO_ERR_CORRUPT;
+      mu = int32_t(muf);
+      p += 4;
+    }
+    for (int b = 0; b < T; ++b) {
+      const uint32_t rb = h[b] & 0x1F;
+      for (int j = 0; j < B; ++j) l[b * B + j] = 0;
+      if (rb == 0) continue;
+      const uint64_t sign = get_bits_be(p, B);
+      p += B / 8;
+      std::vector<uint32_t> mag(B, 0);
+      for (uint32_t k = 0; k < rb; ++k) {
+        const uint64_t w = get_bits_be(p, B);
+        p += B / 8;
+        for (int j = 0; j < B; ++j)
+          if ((w >> (B - 1 - j)) & 1u) mag[j] |= 1u << k;
+      }
+      for (int j = 0; j < B; ++j) {
+        const bool neg = (sign >> (B - 1 - j)) & 1u;
+        l[b * B + j] = neg ? int32_t(uint32_t(0) - mag[j]) : int32_t(mag[j]);
+      }
+    }
+    int32_t prev1 = 0, prev2 = 0;
+    for (int i = 0; i < tile; ++i) {
+      if ((word & FSZO_OFF_CROSS) && i % B == 0) prev1 = prev2 = 0;
+      const int32_t qh = second ? wsub(wadd(l[i], wadd(prev1, prev1)), prev2) : wadd(l[i], prev1);
+      prev2 = prev1;
+      prev1 = qh;
+      qout[size_t(t) * size_t(tile) + size_t(i)] = wadd(qh, mu);
+    }
+  }
+  return FSZO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t fszo_compress_bound_cfg(uint64_t n, int B, int T) {
+  const uint64_t NT = (n + uint64_t(B * T) - 1) / uint64_t(B * T);
+  return kPreamble + uint64_t(T) * NT + (uint64_t(T) * uint64_t(B / 8) * 22 + 4) * NT;
+}
+
+int fszo_compress_cfg(const float* d, uint32_t ndim, const uint64_t* dims, int mode, double eb_req,
+                      uint32_t off, int B, int T, uint8_t* out, uint64_t out_capacity,
+                      uint64_t* out_bytes) {
+  if ((B != 32 && B != 64) || (T != 4 && T != 8 && T != 16)) return FSZO_ERR_INVALID_ARG;
+  if (ndim < 1 || ndim > 3 || dims == nullptr || !fszo_features_valid(off & 7u)) return FSZO_ERR_INVALID_ARG;
+  uint64_t n = 1;
+  for (uint32_t k = 0; k < ndim; ++k) {
+    if (dims[k] != 0 && n > kMaxElems / dims[k]) return FSZO_ERR_INVALID_ARG;
+    n *= dims[k];
+  }
+  float vmin, vmax;
+  int fin;
+  fszo_stats(d, n, &vmin, &vmax, &fin);
+  fszo_params_t p;
+  const int st = fszo_params(mode, eb_req, vmin, vmax, fin, n, &p);
+  if (st != FSZO_OK) return st;
+  const int tile = B * T;
+  const uint64_t NT = (n + uint64_t(tile) - 1) / uint64_t(tile);
+  std::vector<uint8_t> header(uint64_t(T) * NT), data;
+  std::vector<float> dt(tile);
+  for (uint64_t t = 0; t < NT; ++t) {
+    for (int i = 0; i < tile; ++i) {  // zero padding of a partial last tile
+      const uint64_t g = t * uint64_t(tile) + uint64_t(i);
+      dt[i] = g < n ? d[g] : 0.0f;
+    }
+    cfg_encode_tile(dt, p.r, off & 7u, B, T, header.data() + uint64_t(T) * t, data);
+  }
+  const uint64_t total = kPreamble + header.size() + data.size();
+  if (out_bytes) *out_bytes = total;
+  if (total > out_capacity) return FSZO_ERR_CAPACITY;
+  std::memset(out, 0, kPreamble);
+  out[0] = 'F'; out[1] = 'S'; out[2] = 'Z'; out[3] = '1';
+  put_u16(out + 4, 1);
+  out[6] = uint8_t(ndim);
+  out[7] = uint8_t(mode);
+  put_u64(out + 8, n);
+  for (uint32_t k = 0; k < 3; ++k) put_u64(out + 16 + 8 * k, k < ndim ? dims[k] : 0);
+  uint64_t ebits;
+  std::memcpy(&ebits, &eb_req, 8);
+  put_u64(out + 40, ebits);
+  uint32_t sbits;
+  std::memcpy(&sbits, &p.s, 4);
+  put_u32(out + 48, sbits);
+  put_u32(out + 52, (off & 7u) | fszo_tile_word(B, T));
+  put_u64(out + 56, uint64_t(data.size()));
+  if (!header.empty()) std::memcpy(out + kPreamble, header.data(), header.size());
+  if (!data.empty()) std::memcpy(out + kPreamble + header.size(), data.data(), data.size());
+  return FSZO_OK;
+}
+
+}  // extern "C"
 
 namespace {
 
@@ -515,6 +774,13 @@ int decode_to_q(const uint8_t* in, uint64_t in_bytes, std::vector<int32_t>& qout
   int st = fszo_read_preamble_f(in, in_bytes, &n, &nd, dims, &eb, &s, &db, &feat_off);
   if (st != FSZO_OK) return st;
   if (n > cap) return FSZO_ERR_CAPACITY;
+  if (feat_off & 0xFF00u) {  // a configured tile (Sec. 6.5)
+    st = cfg_decode_to_q(in, in_bytes, n, feat_off, db, qout);
+    if (st != FSZO_OK) return st;
+    if (n_out) *n_out = n;
+    if (s_out) *s_out = s;
+    return FSZO_OK;
+  }
   const uint64_t T = tiles_of(n);
   const uint8_t* header = in + kPreamble;
   const uint8_t* data = header + 8 * T;

@@ -121,6 +121,18 @@ int fszo_compress_tiles_f(const float* d, uint64_t n, float r, uint64_t t0, uint
 int fszo_read_preamble_f(const uint8_t* in, uint64_t in_bytes, uint64_t* n, uint32_t* ndim,
                          uint64_t dims[3], double* eb_req, float* s, uint64_t* data_bytes,
                          uint32_t* features_off);
+/* Tile configurations (Sec. 6.5, Table 8): B elements per block (32 or 64), T blocks per
+ * tile (4, 8 or 16). A configured stream has T header bytes per tile and B-bit sign and
+ * plane words (B / 8 bytes, element j at bit B - 1 - j, most significant byte first); the
+ * method word at byte 52 carries the configuration in bits 8-15 (fszo_tile_word; 0 for
+ * B = 32, T = 8) besides the switched-off features. fszo_compress_cfg evaluates the four
+ * variants by definition (one residual pass each); fszo_decompress decodes every
+ * configuration. */
+uint32_t fszo_tile_word(int B, int T);
+uint64_t fszo_compress_bound_cfg(uint64_t n, int B, int T);
+int fszo_compress_cfg(const float* d, uint32_t ndim, const uint64_t* dims, int mode, double eb_req,
+                      uint32_t off, int B, int T, uint8_t* out, uint64_t out_capacity,
+                      uint64_t* out_bytes);
 /* Reconstruction quality for the rate-distortion evaluation of Sec. 6.2 (Fig. 8: PSNR
  * against bit rate). Differences in float64: max |d - d'|, the sum of (d - d')^2 (in
  * element order), elements with |d - d'| > eb, the original's min and max; then

@@ -521,6 +521,70 @@ def run_ablation(fsz, fields, rels, dev, shape):
             "single_pass_speedup_geomean": geo([t["speedup"] for t in timing]), "prezero": prezero}
 
 
+def run_tiles(fsz, fields, rels, dev, shape):
+    """Sec. 6.5 (Table 8): every tile configuration (B elements per block, T blocks per
+    tile) on the bench fields through the generic two-read path: CR against the default
+    B = 32, T = 8 (win / loss beyond 2 %, tie within), and the generic path's compression
+    and decompression time; the specialised single-pass kernels cover 32 x 8 only."""
+    import math
+    import statistics
+
+    import torch
+    L = fsz.lib()
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    n = fields[0][1].numel()
+    wsb = L.fsz_tiled_workspace_bytes(n)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    cap = max(L.fsz_compress_bound_tiled(n, B, T) for B, T in fsz.TILE_CONFIGS)
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    rec = torch.empty(n, dtype=torch.float32, device=dev)
+    nb = torch.zeros(2, dtype=torch.int64, device=dev)
+    dims = fsz.make_dims(shape)
+
+    def timed(fn, reps=4):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            st = fn()
+            e1.record()
+            torch.cuda.synchronize(dev)
+            if st != 0:
+                raise fsz.FszError(st, "tiles")
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts[1:])
+
+    rows = []
+    for name, x in fields:
+        for rel in rels:
+            row = {"field": name, "rel": rel}
+            for B, T in fsz.TILE_CONFIGS:
+                c_ms = timed(lambda: L.fsz_compress_tiled(x.data_ptr(), dims, 1, rel, B, T, 0, out.data_ptr(),
+                                                          cap, nb.data_ptr(), ws.data_ptr(), wsb, sp))
+                if fsz.fsz_check(ws.data_ptr(), sp) != fsz.OK:
+                    raise fsz.FszError(fsz.fsz_check(ws.data_ptr(), sp), "tiles compress")
+                k = int(nb[0].item())
+                d_ms = timed(lambda: L.fsz_decompress_tiled(out.data_ptr(), k, rec.data_ptr(), n,
+                                                            ws.data_ptr(), wsb, sp))
+                if fsz.fsz_check(ws.data_ptr(), sp) != fsz.OK:
+                    raise fsz.FszError(fsz.fsz_check(ws.data_ptr(), sp), "tiles decompress")
+                row[f"{B}x{T}"] = {"cr": 4 * n / k, "compress_gbs": 4 * n / c_ms / 1e6,
+                                   "decompress_gbs": 4 * n / d_ms / 1e6}
+            rows.append(row)
+    summary = {}
+    for B, T in fsz.TILE_CONFIGS:
+        key = f"{B}x{T}"
+        ratios = [r[key]["cr"] / r["32x8"]["cr"] for r in rows]
+        summary[key] = {"win": sum(q > 1.02 for q in ratios), "tie": sum(0.98 <= q <= 1.02 for q in ratios),
+                        "loss": sum(q < 0.98 for q in ratios), "cr_ratio_mean": sum(ratios) / len(ratios),
+                        "compress_gbs_geomean": math.exp(sum(math.log(r[key]["compress_gbs"]) for r in rows) / len(rows)),
+                        "decompress_gbs_geomean": math.exp(sum(math.log(r[key]["decompress_gbs"]) for r in rows) / len(rows))}
+    del out, rec, ws
+    torch.cuda.empty_cache()
+    return {"workload": "the bench fields at each REL, every (B, T) through the generic tiled path",
+            "rows": rows, "vs_32x8": summary}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -800,10 +864,12 @@ def main():
     njobs, nfields_main = len(jobs), len(fields)
     clock_summary = clocks.summary()
     ablation = None
+    tiles = None
     if not args.no_ablation:
         del outs, recon
         torch.cuda.empty_cache()
         ablation = run_ablation(fsz, fields, rels, dev, SHAPE)
+        tiles = run_tiles(fsz, fields, rels, dev, SHAPE)
     batched = None
     if not args.no_batched:
         del fields, jobs, g
@@ -826,7 +892,8 @@ def main():
                            "l2": "inputs 512 MiB > L2; streams read back after >= 2.5 GB of traffic"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps,
-                "clocks": clock_summary, "jobs": per_job, "ablation": ablation, "batched": batched,
+                "clocks": clock_summary, "jobs": per_job, "ablation": ablation, "tiles": tiles,
+                "batched": batched,
                 "serving": serving,
                 "max_abs_err_last_job": p_last}
         print(json.dumps(line))

@@ -181,6 +181,28 @@ fsz_status fsz_decompress_any(const void* d_in, uint64_t in_bytes, float* d_out,
                               uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
                               fsz_stream stream);
 
+/* ------------------------------------------------------------------ tile configurations */
+
+/* The tile-configuration sweep of Sec. 6.5 (Table 8): `block` elements per block (32 or
+ * 64) and `tile_blocks` blocks per tile (4, 8 or 16). A configured stream has tile_blocks
+ * header bytes per tile and block-bit sign and plane words (block / 8 bytes, element j at
+ * bit block - 1 - j, most significant byte first); the method word (preamble byte 52)
+ * holds the configuration in bits 8-15 (0 for 32 x 8, the default). A generic two-read
+ * path (a cost pass, a scan of tile sizes, an encoding pass; one warp per tile) for every
+ * configuration; the default configuration's specialised single-pass kernels are
+ * fsz_compress / fsz_decompress, and fsz_decompress refuses configured streams. */
+uint64_t fsz_compress_bound_tiled(uint64_t n, uint32_t block, uint32_t tile_blocks);
+/* Workspace for fsz_compress_tiled / fsz_decompress_tiled of up to n elements. */
+uint64_t fsz_tiled_workspace_bytes(uint64_t n);
+fsz_status fsz_compress_tiled(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                              uint32_t block, uint32_t tile_blocks, uint32_t features_off,
+                              void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes, void* d_ws,
+                              uint64_t ws_bytes, fsz_stream stream);
+/* Decodes a stream of any tile configuration (including the default). */
+fsz_status fsz_decompress_tiled(const void* d_in, uint64_t in_bytes, float* d_out,
+                                uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
+                                fsz_stream stream);
+
 /* ------------------------------------------------------------------ quality */
 
 /* Reconstruction quality for the rate-distortion evaluation of Sec. 6.2 (Fig. 8: PSNR

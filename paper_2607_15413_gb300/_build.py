@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libfsz.so")
 SOURCES = ["fsz_stats.cu", "fsz_compress.cu", "fsz_decompress.cu", "fsz_api.cu",
-           "fsz_noalloc.cu", "fsz_serve.cu", "fsz_multipass.cu", "fsz_quality.cu"]
+           "fsz_noalloc.cu", "fsz_serve.cu", "fsz_multipass.cu", "fsz_quality.cu",
+           "fsz_tiled.cu"]
 HEADERS = [os.path.join(CSRC, "fsz_internal.cuh"), os.path.join(ROOT, "include", "fsz.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -226,6 +226,7 @@ __device__ uint32_t plan_dfield(FieldInfo* fi, const uint8_t* in, uint64_t in_by
   const float sv = __uint_as_float(w[12]);
   if (!(eb > 0.0) || isinf(eb)) return FSZ_ERR_CORRUPT;
   if (!(sv >= 1.5777218104420236e-30f) || isinf(sv)) return FSZ_ERR_CORRUPT;  // 2^-99
+  if (w[13] & 0xFF00u) return FSZ_ERR_INVALID_ARG;  // a tile configuration: fsz_decompress_tiled
   if (!features_valid(w[13])) return FSZ_ERR_CORRUPT;
   fi->features_off = w[13];
   const uint64_t db = uint64_t(w[14]) | (uint64_t(w[15]) << 32);

@@ -1,0 +1,652 @@
+// Tile configurations of Sec. 6.5 (Table 8): B elements per block (32 or 64) and T blocks
+// per tile (4, 8 or 16). A configured stream has T header bytes per tile (block 0's byte
+// carries the order and centring flags) and B-bit sign and plane words (B / 8 bytes,
+// element j at bit B - 1 - j, most significant byte first), so S_b = (B / 8)(1 + r_b) for
+// r_b > 0. The preamble's method word (byte 52) carries the configuration in bits 8-15.
+//
+// A generic path for the configuration sweep, in the paper's two-read structure: the
+// value-range pass; a cost pass (one warp per tile: the four variants' costs, the
+// selection, the rate header, the tile's size); an exclusive scan of the sizes; an
+// encoding pass (the tile read again, the bit-planes built by warp ballots); the
+// preamble. Element i of a tile sits in register i / 32 of lane i % 32, so every load and
+// store of a register is one coalesced 128-byte row. The decoder mirrors it. The
+// specialised single-pass kernels cover the default configuration only.
+#include <algorithm>
+
+#include "fsz_internal.cuh"
+
+namespace fsz {
+
+namespace {
+
+constexpr int kTiledThreads = 256;  // 8 warps, a tile each at a time
+constexpr int kTiledWarps = kTiledThreads / 32;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4 * kScanThreads;  // tile sizes per CTA in the scan
+constexpr uint32_t FULL = 0xffffffffu;
+
+uint32_t tile_word_of(int B, int T) {
+  return (B == 64 ? 1u : 0u) << 8 | (T == 4 ? 1u : T == 16 ? 2u : 0u) << 12;
+}
+
+__host__ __device__ __forceinline__ bool config_of(uint32_t word, int* B, int* T) {
+  const uint32_t bc = (word >> 8) & 0xF, tc = (word >> 12) & 0xF;
+  if (bc > 1 || tc > 2 || (word & 0xFFFF00F8u)) return false;
+  *B = bc == 1 ? 64 : 32;
+  *T = tc == 1 ? 4 : tc == 2 ? 16 : 8;
+  return true;
+}
+
+// Per-call arrays after the value-range pass's workspace.
+struct TiledPtrs {
+  uint32_t* sizes;   // tile bytes
+  uint64_t* offs;    // exclusive byte offsets inside the tile data
+  uint64_t* rec;     // cost pass -> encoding pass: variant | mu << 32
+  uint64_t* part;    // scan: CTA sums, then their exclusive prefix; part[nparts] = total
+  uint64_t ntiles;
+};
+
+struct TiledLayout {
+  WsLayout L;
+  uint64_t sizes_off, offs_off, rec_off, part_off, bytes, max_tiles;
+};
+
+TiledLayout tiled_layout(uint64_t n) {
+  TiledLayout t;
+  t.L = ws_layout((n + kTile - 1) / kTile, 1);
+  t.max_tiles = (n + 127) / 128 + 1;  // the smallest tile has 128 elements
+  auto a16 = [](uint64_t x) { return (x + 15) & ~uint64_t(15); };
+  t.sizes_off = a16(t.L.bytes);
+  t.offs_off = a16(t.sizes_off + 4 * t.max_tiles);
+  t.rec_off = a16(t.offs_off + 8 * t.max_tiles);
+  t.part_off = a16(t.rec_off + 8 * t.max_tiles);
+  t.bytes = t.part_off + 8 * (t.max_tiles / kScanItems + 2);
+  return t;
+}
+
+TiledPtrs tiled_ptrs(void* ws, const TiledLayout& t, uint64_t ntiles) {
+  uint8_t* b = static_cast<uint8_t*>(ws);
+  return TiledPtrs{reinterpret_cast<uint32_t*>(b + t.sizes_off), reinterpret_cast<uint64_t*>(b + t.offs_off),
+                   reinterpret_cast<uint64_t*>(b + t.rec_off), reinterpret_cast<uint64_t*>(b + t.part_off),
+                   ntiles};
+}
+
+__device__ __forceinline__ uint32_t quantize_bits(float d, float r) {
+  return uint32_t(__float_as_int(__fadd_rn(__fmul_rn(d, r), kMagic)) - kMagicBits);
+}
+
+__device__ __forceinline__ uint32_t bswap32(uint32_t w) { return __byte_perm(w, 0, 0x0123); }
+
+// Residuals of one variant (Eqs. 1-2) for the tile held in qh (q, less mu when centred):
+// the state runs across the whole tile from zero predecessors, or restarts at every
+// block without the cross-block state.
+template <int B, int E>
+__device__ __forceinline__ void tile_residuals(const uint32_t (&qh)[E], bool second, bool indep,
+                                               int lane, uint32_t (&l)[E]) {
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const uint32_t up1 = __shfl_up_sync(FULL, qh[k], 1);
+    const uint32_t up2 = __shfl_up_sync(FULL, qh[k], 2);
+    const uint32_t last = k > 0 ? __shfl_sync(FULL, qh[k > 0 ? k - 1 : 0], 31) : 0u;
+    const uint32_t last2 = k > 0 ? __shfl_sync(FULL, qh[k > 0 ? k - 1 : 0], 30) : 0u;
+    uint32_t p1 = lane >= 1 ? up1 : last;
+    uint32_t p2 = lane >= 2 ? up2 : (lane == 1 ? last : last2);
+    const int pos = (32 * k + lane) % B;  // position inside the block
+    if (indep && pos == 0) p1 = p2 = 0;
+    if (indep && pos == 1) p2 = 0;
+    l[k] = second ? qh[k] - 2u * p1 + p2 : qh[k] - p1;
+  }
+}
+
+// OR of |l| over block b (B / 32 registers), warp-wide: the block's rate (Sec. 4.1.2).
+template <int B, int E>
+__device__ __forceinline__ uint32_t block_rate(const uint32_t (&l)[E], int b) {
+  uint32_t m = uabs32(int32_t(l[b * (B / 32)]));
+  if (B == 64) m |= uabs32(int32_t(l[b * (B / 32) + (B == 64 ? 1 : 0)]));
+  m = __reduce_or_sync(FULL, m);
+  return 32u - uint32_t(__clz(int(m)));
+}
+
+__device__ __forceinline__ uint32_t cfg_block_cost(uint32_t rate, int B) {
+  return rate == 0 ? 0u : uint32_t(B / 8) * (1u + rate);
+}
+
+// The tile's elements (zero past n) and their quantized values.
+template <int B, int T, int E>
+__device__ __forceinline__ void load_tile(const float* in, uint64_t n, uint64_t t, float r, int lane,
+                                          float (&d)[E], uint32_t (&q)[E]) {
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const uint64_t i = t * uint64_t(B * T) + uint64_t(32 * k + lane);
+    d[k] = i < n ? in[i] : 0.0f;
+    q[k] = quantize_bits(d[k], r);
+  }
+}
+
+// The tile mean in the fixed order: 8-element runs left to right (run j = elements
+// 8j..8j+7: register j / 4, lanes 8 (j % 4) ..), then P_j += P_{j+h}, h = R/2 .. 1.
+template <int B, int T, int E>
+__device__ __forceinline__ uint32_t tile_mu(const float (&d)[E], float r, int lane, float* runs) {
+  constexpr int R = B * T / 8;
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    float acc = d[k];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) acc = __fadd_rn(acc, __shfl_down_sync(FULL, d[k], i));
+    if ((lane & 7) == 0) runs[4 * k + (lane >> 3)] = acc;
+  }
+  __syncwarp();
+  uint32_t mu = 0;
+  if (lane == 0) {
+    for (int h = R / 2; h >= 1; h /= 2)
+      for (int j = 0; j < h; ++j) runs[j] = __fadd_rn(runs[j], runs[j + h]);
+    mu = quantize_bits(__fmul_rn(runs[0], 1.0f / float(B * T)), r);
+  }
+  __syncwarp();
+  return __shfl_sync(FULL, mu, 0);
+}
+
+template <int B, int T>
+__global__ void __launch_bounds__(kTiledThreads) fsz_tiled_cost_kernel(KernelArgs a, TiledPtrs p) {
+  constexpr int E = B * T / 32;
+  __shared__ float s_runs[kTiledWarps][B * T / 8];
+  __shared__ uint8_t s_rates[kTiledWarps][4][T];
+  FieldInfo* fi = a.fields;
+  if (fi->status != 0) return;
+  const float r = fi->r;
+  const uint64_t n = fi->n;
+  const uint32_t off = fi->features_off & 7u;
+  const bool indep = (off & kOffCross) != 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t hdr_base = 64;
+  for (uint64_t t = uint64_t(blockIdx.x) * kTiledWarps + warp; t < p.ntiles;
+       t += uint64_t(gridDim.x) * kTiledWarps) {
+    float d[E];
+    uint32_t q[E], qh[E], l[E];
+    load_tile<B, T, E>(fi->in, n, t, r, lane, d, q);
+    const uint32_t mu = (off & kOffCenter) ? 0u : tile_mu<B, T, E>(d, r, lane, s_runs[warp]);
+    uint32_t C[4];
+#pragma unroll 1
+    for (int v = 0; v < 4; ++v) {
+      const bool centred = v >= 2, second = (v & 1) != 0;
+      const bool on = !(second && (off & kOffLz2)) && !(centred && (off & kOffCenter));
+      C[v] = 0xFFFFFFFFu;
+      if (!on) continue;
+#pragma unroll
+      for (int k = 0; k < E; ++k) qh[k] = centred ? q[k] - mu : q[k];
+      tile_residuals<B, E>(qh, second, indep, lane, l);
+      uint32_t cost = centred ? 4u : 0u;
+#pragma unroll
+      for (int b = 0; b < T; ++b) {
+        const uint32_t rate = block_rate<B, E>(l, b);
+        if (lane == 0) s_rates[warp][v][b] = uint8_t(rate);
+        cost += cfg_block_cost(rate, B);
+      }
+      C[v] = cost;
+    }
+    int vs = 0;  // first strict minimum in the listed order (Sec. 4.2.2)
+#pragma unroll
+    for (int v = 1; v < 4; ++v)
+      if (C[v] < C[vs]) vs = v;
+    __syncwarp();
+    if (lane < T) {
+      uint32_t hb = s_rates[warp][vs][lane];
+      if (lane == 0) hb |= ((vs & 1) ? 0x80u : 0u) | (vs >= 2 ? 0x40u : 0u);
+      fi->out[hdr_base + uint64_t(T) * t + lane] = uint8_t(hb);
+    }
+    if (lane == 0) {
+      p.sizes[t] = C[vs];
+      p.rec[t] = uint64_t(vs) | (uint64_t(mu) << 32);
+    }
+    __syncwarp();
+  }
+}
+
+// Exclusive scan of the tile sizes: CTA sums, their prefix (one CTA), then each CTA's
+// tiles. part[nparts] holds the total.
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* s_warp, uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(FULL, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_warp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < int(blockDim.x / 32) ? s_warp[lane] : 0;
+    uint64_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(FULL, wi, o);
+      if (lane >= o) wi += y;
+    }
+    s_warp[lane] = wi - w;
+    if (lane == 31) s_warp[32] = wi;
+  }
+  __syncthreads();
+  const uint64_t r = inc - v + s_warp[warp];
+  *total = s_warp[32];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) fsz_tiled_scan_sums(TiledPtrs p) {
+  __shared__ uint64_t s_warp[33];
+  uint64_t sum = 0;
+  const uint64_t base = uint64_t(blockIdx.x) * kScanItems;
+  for (int k = threadIdx.x; k < kScanItems; k += kScanThreads)
+    if (base + k < p.ntiles) sum += p.sizes[base + k];
+  uint64_t total;
+  block_exclusive_scan(sum, s_warp, &total);
+  if (threadIdx.x == 0) p.part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) fsz_tiled_scan_parts(TiledPtrs p, uint32_t nparts) {
+  __shared__ uint64_t s_warp[33];
+  uint64_t carry = 0;
+  for (uint32_t base = 0; base < nparts; base += kScanThreads) {
+    const uint32_t i = base + threadIdx.x;
+    const uint64_t v = i < nparts ? p.part[i] : 0;
+    uint64_t total;
+    const uint64_t ex = block_exclusive_scan(v, s_warp, &total);
+    if (i < nparts) p.part[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) p.part[nparts] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) fsz_tiled_scan_apply(TiledPtrs p) {
+  __shared__ uint64_t s_warp[33];
+  const uint64_t base = uint64_t(blockIdx.x) * kScanItems;
+  uint64_t carry = p.part[blockIdx.x];
+  for (int k0 = 0; k0 < kScanItems; k0 += kScanThreads) {
+    const uint64_t i = base + k0 + threadIdx.x;
+    const uint64_t v = i < p.ntiles ? p.sizes[i] : 0;
+    uint64_t total;
+    const uint64_t ex = block_exclusive_scan(v, s_warp, &total);
+    if (i < p.ntiles) p.offs[i] = carry + ex;
+    carry += total;
+  }
+}
+
+template <int B, int T>
+__global__ void __launch_bounds__(kTiledThreads) fsz_tiled_encode_kernel(KernelArgs a, TiledPtrs p,
+                                                                         uint32_t nparts) {
+  constexpr int E = B * T / 32;
+  FieldInfo* fi = a.fields;
+  if (fi->status != 0) return;
+  const uint64_t data_bytes = p.part[nparts];
+  const uint64_t data_base = 64 + uint64_t(T) * p.ntiles;
+  if (data_base + data_bytes > fi->cap) {  // the stream does not fit: nothing is written
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_error(a.ctrl, fi, FSZ_ERR_CAPACITY);
+    return;
+  }
+  const float r = fi->r;
+  const uint64_t n = fi->n;
+  const bool indep = (fi->features_off & kOffCross) != 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t t = uint64_t(blockIdx.x) * kTiledWarps + warp; t < p.ntiles;
+       t += uint64_t(gridDim.x) * kTiledWarps) {
+    float d[E];
+    uint32_t q[E], l[E];
+    load_tile<B, T, E>(fi->in, n, t, r, lane, d, q);
+    const uint64_t rec = p.rec[t];
+    const int vs = int(rec & 3u);
+    const uint32_t mu = uint32_t(rec >> 32);
+    const bool centred = vs >= 2, second = (vs & 1) != 0;
+    if (centred) {
+#pragma unroll
+      for (int k = 0; k < E; ++k) q[k] -= mu;
+    }
+    tile_residuals<B, E>(q, second, indep, lane, l);
+    uint32_t vv[E];  // sign-magnitude: bit 0 the sign, bit k + 1 magnitude plane k
+#pragma unroll
+    for (int k = 0; k < E; ++k) vv[k] = (uabs32(int32_t(l[k])) << 1) | (l[k] >> 31);
+    uint8_t* dst = fi->out + data_base + p.offs[t];
+    const uint8_t* hdr = fi->out + 64 + uint64_t(T) * t;
+    uint32_t pos = 0;
+    if (centred) {
+      if (lane == 0) *reinterpret_cast<float*>(dst) = __int2float_rn(int32_t(mu));
+      pos = 4;
+    }
+#pragma unroll 1
+    for (int b = 0; b < T; ++b) {
+      const uint32_t rate = hdr[b] & 0x1Fu;
+      if (rate == 0) continue;
+      // words 0..rate: word w holds bit w of every element's sign-magnitude value
+      uint32_t hi = 0, lo = 0;
+      for (uint32_t w = 0; w <= rate; ++w) {
+        const uint32_t h = __brev(__ballot_sync(FULL, (vv[b * (B / 32)] >> w) & 1u));
+        uint32_t g = 0;
+        if (B == 64) g = __brev(__ballot_sync(FULL, (vv[b * (B / 32) + (B == 64 ? 1 : 0)] >> w) & 1u));
+        if (uint32_t(lane) == w) {
+          hi = h;
+          lo = g;
+        }
+      }
+      if (uint32_t(lane) <= rate) {
+        uint32_t* o = reinterpret_cast<uint32_t*>(dst + pos + uint32_t(B / 8) * uint32_t(lane));
+        o[0] = bswap32(hi);
+        if (B == 64) o[1] = bswap32(lo);
+      }
+      pos += uint32_t(B / 8) * (rate + 1);
+    }
+    __syncwarp();
+  }
+}
+
+__global__ void fsz_tiled_preamble_kernel(KernelArgs a, TiledPtrs p, uint32_t nparts, int T) {
+  FieldInfo* fi = a.fields;
+  if (threadIdx.x != 0 || fi->status != 0) return;
+  const uint64_t data_bytes = p.part[nparts];
+  const uint64_t total = 64 + uint64_t(T) * p.ntiles + data_bytes;
+  if (total > fi->cap) return;
+  uint32_t w[16];
+  w[0] = 0x315A5346u;  // "FSZ1"
+  w[1] = 1u | (fi->ndim << 16) | (fi->mode << 24);
+  w[2] = uint32_t(fi->n);
+  w[3] = uint32_t(fi->n >> 32);
+  for (int k = 0; k < 3; ++k) {
+    const uint64_t dk = uint32_t(k) < fi->ndim ? fi->dims[k] : 0;
+    w[4 + 2 * k] = uint32_t(dk);
+    w[5 + 2 * k] = uint32_t(dk >> 32);
+  }
+  const uint64_t eb = static_cast<uint64_t>(__double_as_longlong(fi->eb_req));
+  w[10] = uint32_t(eb);
+  w[11] = uint32_t(eb >> 32);
+  w[12] = __float_as_uint(fi->s);
+  w[13] = fi->features_off;  // switched-off features and the tile configuration
+  w[14] = uint32_t(data_bytes);
+  w[15] = uint32_t(data_bytes >> 32);
+  uint4* dst = reinterpret_cast<uint4*>(fi->out);
+  for (int k = 0; k < 4; ++k) dst[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+  fi->data_bytes = data_bytes;
+  if (fi->out_bytes) *fi->out_bytes = total;
+}
+
+// ------------------------------------------------------------------ decompression
+
+// Reads and checks a configured stream's preamble (the rules of plan_dfield plus the
+// configuration) into the field record.
+__global__ void fsz_tiled_setup_decompress(KernelArgs a, const uint8_t* in, uint64_t in_bytes,
+                                           float* out, uint64_t cap_elems, uint64_t max_tiles) {
+  if (threadIdx.x != 0) return;
+  FieldInfo* fi = a.fields;
+  fi->sin = in;
+  fi->in_bytes = in_bytes;
+  fi->dout = out;
+  fi->nchunks = 0;
+  uint32_t st = FSZ_OK;
+  int B = 32, T = 8;
+  if (in_bytes < 64) st = FSZ_ERR_CORRUPT;
+  uint32_t w[16] = {0};
+  if (st == FSZ_OK) {
+    const uint4* pw = reinterpret_cast<const uint4*>(in);
+    for (int k = 0; k < 4; ++k) {
+      const uint4 v = pw[k];
+      w[4 * k] = v.x; w[4 * k + 1] = v.y; w[4 * k + 2] = v.z; w[4 * k + 3] = v.w;
+    }
+    if (w[0] != 0x315A5346u || (w[1] & 0xFFFFu) != 1u) st = FSZ_ERR_CORRUPT;
+  }
+  const uint32_t ndim = (w[1] >> 16) & 0xFFu, mode = w[1] >> 24;
+  if (st == FSZ_OK && (ndim < 1 || ndim > 3 || mode > 1)) st = FSZ_ERR_CORRUPT;
+  const uint64_t n = uint64_t(w[2]) | (uint64_t(w[3]) << 32);
+  uint64_t prod = 1;
+  for (uint32_t k = 0; st == FSZ_OK && k < 3; ++k) {
+    const uint64_t dk = uint64_t(w[4 + 2 * k]) | (uint64_t(w[5 + 2 * k]) << 32);
+    if (k >= ndim) {
+      if (dk != 0) st = FSZ_ERR_CORRUPT;
+      continue;
+    }
+    if (dk != 0 && prod > kMaxElems / dk) st = FSZ_ERR_CORRUPT;
+    prod *= dk;
+  }
+  if (st == FSZ_OK && (prod != n || n > kMaxElems)) st = FSZ_ERR_CORRUPT;
+  const double eb = __longlong_as_double(static_cast<long long>(uint64_t(w[10]) | (uint64_t(w[11]) << 32)));
+  const float sv = __uint_as_float(w[12]);
+  if (st == FSZ_OK && (!(eb > 0.0) || isinf(eb) || !(sv >= 1.5777218104420236e-30f) || isinf(sv)))
+    st = FSZ_ERR_CORRUPT;
+  if (st == FSZ_OK && (!config_of(w[13], &B, &T) || !features_valid(w[13] & 7u))) st = FSZ_ERR_CORRUPT;
+  const uint64_t db = uint64_t(w[14]) | (uint64_t(w[15]) << 32);
+  const uint64_t NT = (n + uint64_t(B * T) - 1) / uint64_t(B * T);
+  if (st == FSZ_OK && ((in_bytes - 64) / uint64_t(T) < NT || db > in_bytes - 64 - uint64_t(T) * NT))
+    st = FSZ_ERR_CORRUPT;
+  if (st == FSZ_OK && n > cap_elems) st = FSZ_ERR_CAPACITY;
+  if (st == FSZ_OK && NT > max_tiles) st = FSZ_ERR_WORKSPACE;
+  fi->n = st == FSZ_OK ? n : 0;
+  fi->T = st == FSZ_OK ? NT : 0;
+  fi->s = sv;
+  fi->data_bytes = db;
+  fi->features_off = w[13];
+  if (st != FSZ_OK) set_error(a.ctrl, fi, st);
+}
+
+// Tile sizes from the rate headers (any configuration: B and T from the method word);
+// zero for the slots past the stream's tiles, which the scan also covers.
+__global__ void __launch_bounds__(kTiledThreads) fsz_tiled_sizes_kernel(KernelArgs a, TiledPtrs p) {
+  FieldInfo* fi = a.fields;
+  const bool ok = fi->status == 0;
+  int B = 32, T = 8;
+  config_of(fi->features_off, &B, &T);
+  const uint32_t foff = fi->features_off & 7u;
+  const uint64_t NT = ok ? fi->T : 0;
+  for (uint64_t t = uint64_t(blockIdx.x) * kTiledThreads + threadIdx.x; t < p.ntiles;
+       t += uint64_t(gridDim.x) * kTiledThreads) {
+    if (t >= NT) {
+      p.sizes[t] = 0;
+      continue;
+    }
+    const uint8_t* h = fi->sin + 64 + uint64_t(T) * t;
+    uint32_t bytes = (h[0] & 0x40u) ? 4u : 0u;
+    bool bad = (h[0] & 0x20u) || ((h[0] & 0x80u) && (foff & kOffLz2)) ||
+               ((h[0] & 0x40u) && (foff & kOffCenter));
+    for (int b = 0; b < T; ++b) {
+      if (b > 0 && (h[b] & 0xE0u)) bad = true;
+      bytes += cfg_block_cost(h[b] & 0x1Fu, B);
+    }
+    if (bad) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
+    p.sizes[t] = bytes;
+  }
+}
+
+template <int B, int T>
+__global__ void __launch_bounds__(kTiledThreads) fsz_tiled_decode_kernel(KernelArgs a, TiledPtrs p,
+                                                                         uint32_t nparts) {
+  constexpr int E = B * T / 32;
+  FieldInfo* fi = a.fields;
+  int cb = 0, ct = 0;
+  if (!config_of(fi->features_off, &cb, &ct) || cb != B || ct != T) return;  // another instance's
+  if (fi->status != 0) return;
+  if (p.part[nparts] != fi->data_bytes) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
+    return;
+  }
+  const float s = fi->s;
+  const uint64_t n = fi->n;
+  const bool indep = (fi->features_off & kOffCross) != 0;
+  const uint64_t data_base = 64 + uint64_t(T) * fi->T;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t t = uint64_t(blockIdx.x) * kTiledWarps + warp; t < fi->T;
+       t += uint64_t(gridDim.x) * kTiledWarps) {
+    const uint8_t* h = fi->sin + 64 + uint64_t(T) * t;
+    const uint8_t* src = fi->sin + data_base + p.offs[t];
+    const bool second = (h[0] & 0x80u) != 0, centred = (h[0] & 0x40u) != 0;
+    uint32_t mu = 0;
+    bool good = true;
+    uint32_t pos = 0;
+    if (centred) {
+      const float muf = *reinterpret_cast<const float*>(src);
+      const int m = __float2int_rn(muf);
+      if (!(fabsf(muf) <= 16777216.0f) || __int2float_rn(m) != muf) good = false;
+      mu = uint32_t(m);
+      pos = 4;
+    }
+    uint32_t x[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) x[k] = 0;
+#pragma unroll
+    for (int b = 0; b < T; ++b) {
+      const uint32_t rate = h[b] & 0x1Fu;
+      if (rate == 0) continue;
+      uint32_t v0 = 0, v1 = 0;  // sign-magnitude values of this lane's element(s) in block b
+      for (uint32_t w = 0; w <= rate; ++w) {
+        const uint32_t* wp = reinterpret_cast<const uint32_t*>(src + pos + uint32_t(B / 8) * w);
+        v0 |= ((bswap32(wp[0]) >> (31 - lane)) & 1u) << w;
+        if (B == 64) v1 |= ((bswap32(wp[B == 64 ? 1 : 0]) >> (31 - lane)) & 1u) << w;
+      }
+      const uint32_t m0 = v0 >> 1, m1 = v1 >> 1;
+      x[b * (B / 32)] = (v0 & 1u) ? 0u - m0 : m0;
+      if (B == 64) x[b * (B / 32) + (B == 64 ? 1 : 0)] = (v1 & 1u) ? 0u - m1 : m1;
+      pos += uint32_t(B / 8) * (rate + 1);
+    }
+    // inverse prediction: inclusive prefix sums in element order (once for LZ1, twice for
+    // LZ2), restarting at every block without the cross-block state
+#pragma unroll 1
+    for (int pass = 0; pass < (second ? 2 : 1); ++pass) {
+      uint32_t carry = 0;
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        if (indep && ((32 * k) % B) == 0) carry = 0;
+        uint32_t inc = x[k];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) inc = scan_step_up(inc, o);
+        x[k] = inc + carry;
+        carry = __shfl_sync(FULL, x[k], 31);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const uint64_t i = t * uint64_t(B * T) + uint64_t(32 * k + lane);
+      if (i < n) fi->dout[i] = __fmul_rn(__int2float_rn(int32_t(x[k] + mu)), s);
+    }
+    if (!__all_sync(FULL, good) && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
+  }
+}
+
+int tiled_grid() {
+  static int g = [] {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * 8;
+  }();
+  return g;
+}
+
+template <int B, int T>
+void launch_tiled_compress(const KernelArgs& a, const TiledPtrs& p, uint32_t nparts, cudaStream_t s) {
+  const int g = int(std::min<uint64_t>(uint64_t(tiled_grid()), (p.ntiles + kTiledWarps - 1) / kTiledWarps));
+  fsz_tiled_cost_kernel<B, T><<<g, kTiledThreads, 0, s>>>(a, p);
+  fsz_tiled_scan_sums<<<nparts, kScanThreads, 0, s>>>(p);
+  fsz_tiled_scan_parts<<<1, kScanThreads, 0, s>>>(p, nparts);
+  fsz_tiled_scan_apply<<<nparts, kScanThreads, 0, s>>>(p);
+  fsz_tiled_encode_kernel<B, T><<<g, kTiledThreads, 0, s>>>(a, p, nparts);
+  fsz_tiled_preamble_kernel<<<1, 32, 0, s>>>(a, p, nparts, T);
+}
+
+}  // namespace
+
+}  // namespace fsz
+
+using namespace fsz;
+
+extern "C" {
+
+uint64_t fsz_compress_bound_tiled(uint64_t n, uint32_t block, uint32_t tile_blocks) {
+  const uint64_t tile = uint64_t(block) * tile_blocks;
+  if ((block != 32 && block != 64) || (tile_blocks != 4 && tile_blocks != 8 && tile_blocks != 16))
+    return 0;
+  const uint64_t NT = (n + tile - 1) / tile;
+  return 64 + uint64_t(tile_blocks) * NT + (uint64_t(tile_blocks) * (block / 8) * 22 + 4) * NT;
+}
+
+uint64_t fsz_tiled_workspace_bytes(uint64_t n) { return tiled_layout(n).bytes; }
+
+fsz_status fsz_compress_tiled(const float* d_in, fsz_dims dims, fsz_eb_mode mode, double eb,
+                              uint32_t block, uint32_t tile_blocks, uint32_t features_off,
+                              void* d_out, uint64_t out_capacity, uint64_t* d_out_bytes, void* d_ws,
+                              uint64_t ws_bytes, fsz_stream stream) {
+  const int B = int(block), T = int(tile_blocks);
+  if ((B != 32 && B != 64) || (T != 4 && T != 8 && T != 16)) return FSZ_ERR_INVALID_ARG;
+  if (!features_valid(features_off)) return FSZ_ERR_INVALID_ARG;
+  uint64_t n = 1;
+  if (dims.ndim < 1 || dims.ndim > 3 || dims.reserved != 0) return FSZ_ERR_INVALID_ARG;
+  for (uint32_t k = 0; k < dims.ndim; ++k) {
+    if (dims.dims[k] != 0 && n > kMaxElems / dims.dims[k]) return FSZ_ERR_INVALID_ARG;
+    n *= dims.dims[k];
+  }
+  if (n == 0) return FSZ_ERR_INVALID_ARG;
+  const TiledLayout lay = tiled_layout(n);
+  if (d_ws == nullptr || ws_bytes < lay.bytes) return FSZ_ERR_WORKSPACE;
+  const uint64_t NT = (n + uint64_t(B * T) - 1) / uint64_t(B * T);
+  if (out_capacity < 64 + uint64_t(T) * NT) return FSZ_ERR_CAPACITY;
+  // value-range pass and step (the field record gets the method word)
+  fsz_status st = fsz_compress_prepare(d_in, dims, mode, eb, d_out, out_capacity, d_out_bytes, d_ws,
+                                       lay.L.bytes, stream);
+  if (st != FSZ_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  KernelArgs a;
+  a.ctrl = reinterpret_cast<Ctrl*>(ws);
+  a.fields = reinterpret_cast<FieldInfo*>(ws + lay.L.fields_off);
+  a.chunk_field = reinterpret_cast<const uint32_t*>(ws + lay.L.map_off);
+  a.flags = reinterpret_cast<uint64_t*>(ws + lay.L.flags_off);
+  a.skip_chunk = ~uint64_t(0);
+  a.timeout_ns = kDefaultTimeoutNs;
+  const uint32_t word = features_off | tile_word_of(B, T);
+  if (cudaMemcpyAsync(&a.fields->features_off, &word, 4, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return FSZ_ERR_CUDA;
+  const TiledPtrs p = tiled_ptrs(d_ws, lay, NT);
+  const uint32_t nparts = uint32_t((NT + kScanItems - 1) / kScanItems);
+  if (B == 32 && T == 4) launch_tiled_compress<32, 4>(a, p, nparts, s);
+  else if (B == 32 && T == 8) launch_tiled_compress<32, 8>(a, p, nparts, s);
+  else if (B == 32 && T == 16) launch_tiled_compress<32, 16>(a, p, nparts, s);
+  else if (B == 64 && T == 4) launch_tiled_compress<64, 4>(a, p, nparts, s);
+  else if (B == 64 && T == 8) launch_tiled_compress<64, 8>(a, p, nparts, s);
+  else launch_tiled_compress<64, 16>(a, p, nparts, s);
+  return cudaGetLastError() == cudaSuccess ? FSZ_OK : FSZ_ERR_CUDA;
+}
+
+fsz_status fsz_decompress_tiled(const void* d_in, uint64_t in_bytes, float* d_out,
+                                uint64_t out_capacity_elems, void* d_ws, uint64_t ws_bytes,
+                                fsz_stream stream) {
+  if (d_in == nullptr || d_out == nullptr || d_ws == nullptr) return FSZ_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out) |
+       reinterpret_cast<uintptr_t>(d_ws)) & 15)
+    return FSZ_ERR_ALIGN;
+  if (out_capacity_elems > kMaxElems) out_capacity_elems = kMaxElems;
+  const TiledLayout lay = tiled_layout(out_capacity_elems);
+  if (ws_bytes < lay.bytes) return FSZ_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_ws, 0, lay.L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
+  uint8_t* ws = static_cast<uint8_t*>(d_ws);
+  KernelArgs a;
+  a.ctrl = reinterpret_cast<Ctrl*>(ws);
+  a.fields = reinterpret_cast<FieldInfo*>(ws + lay.L.fields_off);
+  a.chunk_field = reinterpret_cast<const uint32_t*>(ws + lay.L.map_off);
+  a.flags = reinterpret_cast<uint64_t*>(ws + lay.L.flags_off);
+  a.skip_chunk = ~uint64_t(0);
+  a.timeout_ns = kDefaultTimeoutNs;
+  fsz_tiled_setup_decompress<<<1, 32, 0, s>>>(a, static_cast<const uint8_t*>(d_in), in_bytes, d_out,
+                                              out_capacity_elems, lay.max_tiles);
+  // the tile count is on the device: the sizes, the scan and the decoders cover the most
+  // tiles this output can hold and stop at the stream's own count
+  const TiledPtrs p = tiled_ptrs(d_ws, lay, lay.max_tiles);
+  const uint32_t nparts = uint32_t((lay.max_tiles + kScanItems - 1) / kScanItems);
+  const int g = tiled_grid();
+  fsz_tiled_sizes_kernel<<<g, kTiledThreads, 0, s>>>(a, p);
+  fsz_tiled_scan_sums<<<nparts, kScanThreads, 0, s>>>(p);
+  fsz_tiled_scan_parts<<<1, kScanThreads, 0, s>>>(p, nparts);
+  fsz_tiled_scan_apply<<<nparts, kScanThreads, 0, s>>>(p);
+  fsz_tiled_decode_kernel<32, 4><<<g, kTiledThreads, 0, s>>>(a, p, nparts);
+  fsz_tiled_decode_kernel<32, 8><<<g, kTiledThreads, 0, s>>>(a, p, nparts);
+  fsz_tiled_decode_kernel<32, 16><<<g, kTiledThreads, 0, s>>>(a, p, nparts);
+  fsz_tiled_decode_kernel<64, 4><<<g, kTiledThreads, 0, s>>>(a, p, nparts);
+  fsz_tiled_decode_kernel<64, 8><<<g, kTiledThreads, 0, s>>>(a, p, nparts);
+  fsz_tiled_decode_kernel<64, 16><<<g, kTiledThreads, 0, s>>>(a, p, nparts);
+  return cudaGetLastError() == cudaSuccess ? FSZ_OK : FSZ_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -29,7 +29,8 @@ OFF_CROSS_BLOCK, OFF_CENTERING, OFF_LZ2 = 1, 2, 4
 EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_bytes", "fsz_compress",
            "fsz_compress_features", "fsz_compress_multipass", "fsz_decompress_any",
            "fsz_decompress_prezeroed",
-           "fsz_quality_workspace_bytes", "fsz_quality_stats",
+           "fsz_quality_workspace_bytes", "fsz_quality_stats", "fsz_compress_bound_tiled",
+           "fsz_tiled_workspace_bytes", "fsz_compress_tiled", "fsz_decompress_tiled",
            "fsz_compress_prepare", "fsz_compress_encode", "fsz_decompress", "fsz_compress_batched",
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
            "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc",
@@ -150,6 +151,14 @@ def lib():
             L.fsz_quality_workspace_bytes.restype = u64
             L.fsz_quality_stats.argtypes = [P, P, u64, f64, u64, P, P, u64, P]
             L.fsz_quality_stats.restype = i32
+            L.fsz_compress_bound_tiled.argtypes = [u64, u32, u32]
+            L.fsz_compress_bound_tiled.restype = u64
+            L.fsz_tiled_workspace_bytes.argtypes = [u64]
+            L.fsz_tiled_workspace_bytes.restype = u64
+            L.fsz_compress_tiled.argtypes = [P, FszDims, i32, f64, u32, u32, u32, P, u64, P, P, u64, P]
+            L.fsz_compress_tiled.restype = i32
+            L.fsz_decompress_tiled.argtypes = [P, u64, P, u64, P, u64, P]
+            L.fsz_decompress_tiled.restype = i32
             L.fsz_decompress.argtypes = [P, u64, P, u64, P, u64, P]
             L.fsz_decompress.restype = i32
             L.fsz_compress_batched.argtypes = [P, u32, u64, P, u64, P]
@@ -451,6 +460,51 @@ def decompress(stream_bytes, n: int | None = None, ws: Workspace | None = None, 
     _check(st, "fsz_decompress")
     if check:
         _check(fsz_check(ws.ptr, sp), "fsz_decompress (device)")
+    return out[:n]
+
+
+# ------------------------------------------------------------------ tile configurations
+
+TILE_CONFIGS = ((32, 4), (32, 8), (32, 16), (64, 4), (64, 8), (64, 16))
+
+
+def compress_tiled(x, eb: float, mode: int = EB_REL, block: int = 32, tile_blocks: int = 8,
+                   features_off: int = 0, shape=None, stream=None, check: bool = True):
+    """Compress with a tile configuration of Sec. 6.5 (fsz_compress_tiled). Returns
+    (stream_bytes_tensor, nbytes)."""
+    import torch
+    assert x.dtype == torch.float32 and x.is_cuda and x.is_contiguous()
+    shape = tuple(x.shape) if shape is None else tuple(shape)
+    if len(shape) == 0:
+        shape = (x.numel(),)
+    n = x.numel()
+    cap = lib().fsz_compress_bound_tiled(n, block, tile_blocks)
+    out = _dev_buffer(max(cap, 16), x.device)
+    wsb = lib().fsz_tiled_workspace_bytes(n)
+    ws = _dev_buffer(wsb, x.device)
+    nbytes = torch.zeros(2, dtype=torch.int64, device=x.device)
+    sp = _stream_ptr(stream)
+    _check(lib().fsz_compress_tiled(x.data_ptr(), make_dims(shape), mode, eb, block, tile_blocks,
+                                    features_off, out.data_ptr(), cap, nbytes.data_ptr(),
+                                    ws.data_ptr(), wsb, sp), "fsz_compress_tiled")
+    if check:
+        _check(fsz_check(ws.data_ptr(), sp), "fsz_compress_tiled (device)")
+    nb = int(nbytes[0].item())
+    return out[:nb], nb
+
+
+def decompress_tiled(stream_bytes, n: int, stream=None, check: bool = True):
+    """Decode a stream of any tile configuration (fsz_decompress_tiled)."""
+    import torch
+    src = stream_bytes if stream_bytes.data_ptr() % 16 == 0 else stream_bytes.clone()
+    out = torch.empty(max(n, 4), dtype=torch.float32, device=src.device)
+    wsb = lib().fsz_tiled_workspace_bytes(out.numel())
+    ws = _dev_buffer(wsb, src.device)
+    sp = _stream_ptr(stream)
+    _check(lib().fsz_decompress_tiled(src.data_ptr(), src.numel(), out.data_ptr(), out.numel(),
+                                      ws.data_ptr(), wsb, sp), "fsz_decompress_tiled")
+    if check:
+        _check(fsz_check(ws.data_ptr(), sp), "fsz_decompress_tiled (device)")
     return out[:n]
 
 

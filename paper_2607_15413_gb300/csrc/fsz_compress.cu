@@ -471,7 +471,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
           const uint32_t nw = ((ti & 0xffffu) + (t0 + 1 < nt ? (S.tinfo[b][t0 + 1] & 0xffffu) : 0u)) >> 2;
           const uint32_t* src = reinterpret_cast<const uint32_t*>(ring + (ti >> 16));
           uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][t0]);
-          for (uint32_t q = lane; q < nw; q += 32) dst[q] = src[q];
+          for (uint32_t q0 = 0; q0 < nw; q0 += 128) {  // 4 words per lane in flight
+            uint32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const uint32_t q = q0 + 32 * u + lane;
+              if (q < nw) v[u] = src[q];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const uint32_t q = q0 + 32 * u + lane;
+              if (q < nw) dst[q] = v[u];
+            }
+          }
         }
         if (warp == 0 && lane == 0 && (ci.flags & kInfoLast)) write_preamble(ci.fi, excl + tot);
       }

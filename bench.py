@@ -585,6 +585,107 @@ def run_tiles(fsz, fields, rels, dev, shape):
             "rows": rows, "vs_32x8": summary}
 
 
+CONFIG_WORKLOADS = {
+    1: "2^20 float32, five seeded sinusoids + noise (seed 0), REL 1e-3 (4 MiB: held in L2)",
+    3: "2^28 float32 (1 GiB), particle x-coordinates around 10^4 centres then N(0, 300^2) "
+       "velocities (seed 2), REL 1e-4",
+    4: "512 fields (seed 3), log-uniform 64 KiB-64 MiB, 1-3-D, 40% k^-3 GRF / 40% particles / "
+       "20% zero-slab offset, REL per field from {1e-2, 1e-3, 1e-4}; one batched graph launch "
+       "each way, default schedule",
+}
+
+
+def run_config(args, fsz, inputs, dev, cfg: int):
+    """Compresses and decompresses one of the other workloads for --steps timed steps (after
+    --warmup untimed ones) and prints one JSON line of per-kernel input GB/s (median and
+    mean over the steps): the per-configuration numbers and the command their ncu launch
+    lists are taken with."""
+    import torch
+    L = fsz.lib()
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    out = {"config_run": cfg, "workload": CONFIG_WORKLOADS[cfg], "steps": args.steps,
+           "warmup": max(3, args.warmup)}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    if cfg in (1, 3):
+        if cfg == 1:
+            x = torch.from_numpy(inputs.sinusoids(1 << 20, seed=0)).to(dev)
+            rel = 1e-3
+        else:
+            x = inputs.particles(1 << 28, seed=2, device=str(dev))
+            rel = 1e-4
+        torch.cuda.empty_cache()
+        n = x.numel()
+        dims = fsz.make_dims((n,))
+        cap = fsz.fsz_compress_bound(n)
+        sb = torch.empty(cap, dtype=torch.uint8, device=dev)
+        rec = torch.empty(n, dtype=torch.float32, device=dev)
+        nb = torch.zeros(1, dtype=torch.int64, device=dev)
+        wsb = fsz.fsz_workspace_bytes(n)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        times = {"stats": [], "encode": [], "decompress": []}
+        for k in range(max(3, args.warmup) + args.steps):
+            e = [ev() for _ in range(4)]
+            e[0].record(stream)
+            st = L.fsz_compress_prepare(x.data_ptr(), dims, fsz.EB_REL, rel, sb.data_ptr(), cap,
+                                        nb.data_ptr(), ws.data_ptr(), wsb, sp)
+            e[1].record(stream)
+            st |= L.fsz_compress_encode(x.data_ptr(), dims, fsz.EB_REL, rel, sb.data_ptr(), cap,
+                                        nb.data_ptr(), ws.data_ptr(), wsb, sp)
+            e[2].record(stream)
+            st |= L.fsz_decompress(sb.data_ptr(), cap, rec.data_ptr(), n, ws.data_ptr(), wsb, sp)
+            e[3].record(stream)
+            if st:
+                raise fsz.FszError(st, f"config {cfg}")
+            torch.cuda.synchronize(dev)
+            if k >= max(3, args.warmup):
+                times["stats"].append(e[0].elapsed_time(e[1]))
+                times["encode"].append(e[1].elapsed_time(e[2]))
+                times["decompress"].append(e[2].elapsed_time(e[3]))
+        st = fsz.fsz_check(ws.data_ptr(), sp)
+        if st != fsz.OK:
+            raise fsz.FszError(st, f"config {cfg}")
+        k = int(nb[0].item())
+        q = fsz.quality(x, rec, rel * (float(x.max().item()) - float(x.min().item())), k)
+        nbytes_in, comp_bytes = 4 * n, k
+        out.update({"n": n, "cr": 4 * n / k, "psnr_db": q["psnr_db"], "bit_rate": q["bit_rate"],
+                    "errors_over_bound": q["over_bound"]})
+    else:
+        specs = inputs.field_mix_specs(512, seed=3)
+        fields = [(inputs.make_field(spec, device=str(dev)).contiguous(), spec["dims"], fsz.EB_REL,
+                   spec["rel"]) for spec in specs]
+        torch.cuda.empty_cache()
+        nbytes_in = sum(4 * f.numel() for f, *_ in fields)
+        cb = fsz.CompressBatch(fields, dev)
+        assert cb.run() == fsz.OK and cb.status()[0] == fsz.OK
+        sizes = cb.sizes.cpu().tolist()
+        db = fsz.DecompressBatch([cb.stream(i, sizes) for i in range(len(fields))],
+                                 [f.numel() for f, *_ in fields], dev)
+        comp_bytes = sum(sizes)
+        times = {"compress": [], "decompress": []}
+        for k in range(max(3, args.warmup) + args.steps):
+            e = [ev() for _ in range(3)]
+            e[0].record(stream)
+            cb.launch_graph()
+            e[1].record(stream)
+            db.launch_graph()
+            e[2].record(stream)
+            torch.cuda.synchronize(dev)
+            if k >= max(3, args.warmup):
+                times["compress"].append(e[0].elapsed_time(e[1]))
+                times["decompress"].append(e[1].elapsed_time(e[2]))
+        if cb.status()[0] != fsz.OK or db.status()[0] != fsz.OK:
+            raise fsz.FszError(fsz.ERR_CORRUPT, "config 4")
+        out.update({"n": nbytes_in // 4, "fields": len(fields), "cr": nbytes_in / comp_bytes})
+    for name, ts in times.items():
+        out[f"{name}_gbs"] = nbytes_in / statistics.median(ts) / 1e6
+        out[f"{name}_gbs_mean"] = nbytes_in / statistics.mean(ts) / 1e6
+    out["note"] = ("input bytes / CUDA-event time per kernel (stats = the value-range pass with its "
+                   "set-up kernel; encode = the compression kernel)" if cfg != 4 else
+                   "input bytes / CUDA-event time per batched graph launch")
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -605,6 +706,9 @@ def main():
                     help="subset of grf,zero_slabs (smaller cases for profiling)")
     ap.add_argument("--rels", default=",".join(str(r) for r in RELS),
                     help="subset of the error bounds (smaller cases for profiling)")
+    ap.add_argument("--config", type=int, choices=[1, 3, 4], default=None,
+                    help="time one of the other workloads alone (per-configuration numbers and "
+                         "their profiles) instead of the bench")
     args = ap.parse_args()
     world, rank, local = dist_setup(args.gpus)
     if args.impl == "reference":
@@ -618,11 +722,16 @@ def main():
     from paper_2607_15413_gb300 import fsz, inputs
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.config is None:
         cpu = cpu_baseline_run(cpu_sample_fields())   # on the host, before any GPU work
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.config is not None:
+        if rank == 0:
+            run_config(args, fsz, inputs, dev, args.config)
+        barrier(world)
+        return
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
 
@@ -860,7 +969,11 @@ def main():
                         "encode_kernel_hbm_gbs": (4 * n + sizes[j]) / med(enc_ms[j]) / 1e6,
                         "stats_gbs": 4 * n / med(stats_ms[j]) / 1e6,
                         "decompress_gbs": 4 * n / med(dec_ms[j]) / 1e6,
-                        "decompress_hbm_gbs": (4 * n + sizes[j]) / med(dec_ms[j]) / 1e6})
+                        "decompress_hbm_gbs": (4 * n + sizes[j]) / med(dec_ms[j]) / 1e6,
+                        # the same over the mean step instead of the median one
+                        "compress_gbs_mean": 4 * n / statistics.mean(comp_ms[j]) / 1e6,
+                        "encode_kernel_gbs_mean": 4 * n / statistics.mean(enc_ms[j]) / 1e6,
+                        "decompress_gbs_mean": 4 * n / statistics.mean(dec_ms[j]) / 1e6})
     njobs, nfields_main = len(jobs), len(fields)
     clock_summary = clocks.summary()
     ablation = None

@@ -350,11 +350,13 @@ __global__ void __launch_bounds__(kPlanThreads) fsz_plan_kernel(KernelArgs a, co
     }
   }
   if (total > chunk_cap) return;
+  // The chunk -> field table, one warp per field (the fields' ranges are disjoint), so
+  // that the fields' record loads overlap rather than follow one another.
   uint32_t* map = const_cast<uint32_t*>(a.chunk_field);
-  for (uint32_t f = 0; f < nfields; ++f) {
+  for (uint32_t f = uint32_t(warp); f < nfields; f += uint32_t(kPlanThreads / 32)) {
     const FieldInfo* fi = a.fields + f;
     const uint64_t c0 = fi->chunk_first, nc = fi->nchunks;
-    for (uint64_t k = tid; k < nc; k += kPlanThreads) map[c0 + k] = f;
+    for (uint64_t k = uint64_t(lane); k < nc; k += 32) map[c0 + k] = f;
   }
   if constexpr (kCompress) {
     for (uint32_t f = tid; f < nfields; f += kPlanThreads) {

@@ -86,3 +86,35 @@ def apply_default(path: str = DEFAULT_TABLE) -> dict | None:
         return None
     apply(table["best"])
     return table["best"]
+
+
+def main() -> None:
+    """Tunes on the 512-field batch (seed 3: log-uniform 64 KiB-64 MiB, mixed classes and
+    REL bounds) on cuda:0 and writes the table that ships with the package."""
+    import torch
+    from . import inputs
+    dev = torch.device("cuda", 0)
+    specs = inputs.field_mix_specs(512, seed=3)
+    fields = [(inputs.make_field(spec, device=str(dev)).contiguous(), spec["dims"], fsz.EB_REL,
+               spec["rel"]) for spec in specs]
+    cb = fsz.CompressBatch(fields, dev)
+    if cb.run() != fsz.OK or cb.status()[0] != fsz.OK:
+        raise fsz.FszError(cb.status()[0], "tune: compress")
+    sizes = cb.sizes.cpu().tolist()
+    db = fsz.DecompressBatch([cb.stream(i, sizes) for i in range(len(fields))],
+                             [f.numel() for f, *_ in fields], dev)
+    res = tune(cb, db, reps=5)
+    props = torch.cuda.get_device_properties(dev)
+    save({"device": f"{props.name} ({props.multi_processor_count} SMs)",
+          "workload": "512 fields, seed 3: log-uniform 64 KiB-64 MiB, 1-3-D, 40% k^-3 GRF / "
+                      "40% particle-like / 20% zero-slab, REL in {1e-2,1e-3,1e-4}",
+          "limits": res["limits"], "best": res["best"],
+          "tuning_ms": {"compress": res["compress"], "decompress": res["decompress"]},
+          "note": "CTAs per SM for the value-range, compression and decompression kernels; "
+                  "0 = as many as fit. Measured by paper_2607_15413_gb300.tune on the batched "
+                  "workload (graph launches, median of 5)."}, DEFAULT_TABLE)
+    print(json.dumps(res["best"]))
+
+
+if __name__ == "__main__":
+    main()

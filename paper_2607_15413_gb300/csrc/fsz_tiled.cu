@@ -77,25 +77,59 @@ __device__ __forceinline__ uint32_t quantize_bits(float d, float r) {
 
 __device__ __forceinline__ uint32_t bswap32(uint32_t w) { return __byte_perm(w, 0, 0x0123); }
 
+// The predecessor of every element of the tile (element 32 k + L sits in register k of
+// lane L): one rotation of each register by a lane, lane 0 taking the previous register's
+// rotated value (element 32 k - 1); zero before the tile, and before every block when
+// `restart` holds (no cross-block state).
+template <int B, int E>
+__device__ __forceinline__ void predecessors(const uint32_t (&v)[E], bool restart, int lane,
+                                             uint32_t (&p)[E]) {
+  uint32_t before = 0;  // at lane 0: the element before register k's first
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const uint32_t rot = __shfl_sync(FULL, v[k], (lane + 31) & 31);
+    uint32_t pk = lane == 0 ? before : rot;
+    if (restart && ((32 * k + lane) % B) == 0) pk = 0;
+    p[k] = pk;
+    before = rot;
+  }
+}
+
 // Residuals of one variant (Eqs. 1-2) for the tile held in qh (q, less mu when centred):
-// the state runs across the whole tile from zero predecessors, or restarts at every
-// block without the cross-block state.
+// LZ1 from zero predecessors, LZ2 as the LZ1 residuals' own first differences (so
+// l2_0 = qh_0 and l2_1 = qh_1 - 2 qh_0), the state running across the whole tile, or
+// restarting at every block without the cross-block state.
 template <int B, int E>
 __device__ __forceinline__ void tile_residuals(const uint32_t (&qh)[E], bool second, bool indep,
                                                int lane, uint32_t (&l)[E]) {
+  uint32_t p[E];
+  predecessors<B, E>(qh, indep, lane, p);
 #pragma unroll
-  for (int k = 0; k < E; ++k) {
-    const uint32_t up1 = __shfl_up_sync(FULL, qh[k], 1);
-    const uint32_t up2 = __shfl_up_sync(FULL, qh[k], 2);
-    const uint32_t last = k > 0 ? __shfl_sync(FULL, qh[k > 0 ? k - 1 : 0], 31) : 0u;
-    const uint32_t last2 = k > 0 ? __shfl_sync(FULL, qh[k > 0 ? k - 1 : 0], 30) : 0u;
-    uint32_t p1 = lane >= 1 ? up1 : last;
-    uint32_t p2 = lane >= 2 ? up2 : (lane == 1 ? last : last2);
-    const int pos = (32 * k + lane) % B;  // position inside the block
-    if (indep && pos == 0) p1 = p2 = 0;
-    if (indep && pos == 1) p2 = 0;
-    l[k] = second ? qh[k] - 2u * p1 + p2 : qh[k] - p1;
+  for (int k = 0; k < E; ++k) l[k] = qh[k] - p[k];
+  if (second) {
+    predecessors<B, E>(l, indep, lane, p);
+#pragma unroll
+    for (int k = 0; k < E; ++k) l[k] -= p[k];
   }
+}
+
+// 32 x 32 bit transpose across the warp, anti-diagonal form: on return bit c of lane L is
+// bit 31 - L of lane 31 - c on entry. Five exchange steps (j = 16 .. 1): lanes L and L ^ j
+// trade the j x j bit blocks off the diagonal of their 2j x 2j block, each taking a
+// rotated copy of the partner's word and a bit-select. Lane L holds plane 31 - L of the
+// 32 elements given one per lane (element e at bit 31 - e), and the converse.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
+#pragma unroll
+  for (int j = 16; j >= 1; j >>= 1) {
+    const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                     : j == 2 ? 0x33333333u : 0x55555555u;
+    const bool upper = (lane & j) != 0;
+    const uint32_t x = __shfl_xor_sync(FULL, v, j);
+    const uint32_t sh = __funnelshift_r(x, x, upper ? 32 - j : j);  // rotate right
+    const uint32_t keep = upper ? m : ~m;                            // this lane's own bits
+    v = (v & keep) | (sh & ~keep);
+  }
+  return v;
 }
 
 // OR of |l| over block b (B / 32 registers), warp-wide: the block's rate (Sec. 4.1.2).
@@ -123,33 +157,54 @@ __device__ __forceinline__ void load_tile(const float* in, uint64_t n, uint64_t 
   }
 }
 
-// The tile mean in the fixed order: 8-element runs left to right (run j = elements
-// 8j..8j+7: register j / 4, lanes 8 (j % 4) ..), then P_j += P_{j+h}, h = R/2 .. 1.
+// The tile mean in the fixed order: the 8-element runs P_j (elements 8j..8j+7) added left
+// to right, then P_j += P_{j+h} for h = R/2 .. 1 (R runs). The tile goes through the
+// warp's shared buffer so that lane j adds run j (and j + 32, ...); the first levels of
+// the tree stay inside a lane, the last five are shuffles.
 template <int B, int T, int E>
-__device__ __forceinline__ uint32_t tile_mu(const float (&d)[E], float r, int lane, float* runs) {
+__device__ __forceinline__ uint32_t tile_mu(const float (&d)[E], float r, int lane, float* tile) {
   constexpr int R = B * T / 8;
+  constexpr int U = (R + 31) / 32;  // runs per lane: 1, 2 or 4
 #pragma unroll
-  for (int k = 0; k < E; ++k) {
-    float acc = d[k];
+  for (int k = 0; k < E; ++k) tile[32 * k + lane] = d[k];
+  __syncwarp();
+  float P[U];
 #pragma unroll
-    for (int i = 1; i < 8; ++i) acc = __fadd_rn(acc, __shfl_down_sync(FULL, d[k], i));
-    if ((lane & 7) == 0) runs[4 * k + (lane >> 3)] = acc;
+  for (int u = 0; u < U; ++u) {
+    const int j = lane + 32 * u;
+    float acc = 0.0f;
+    if (j < R) {
+      const float4 x = reinterpret_cast<const float4*>(tile)[2 * j];
+      const float4 y = reinterpret_cast<const float4*>(tile)[2 * j + 1];
+      acc = __fadd_rn(x.x, x.y);
+      acc = __fadd_rn(acc, x.z);
+      acc = __fadd_rn(acc, x.w);
+      acc = __fadd_rn(acc, y.x);
+      acc = __fadd_rn(acc, y.y);
+      acc = __fadd_rn(acc, y.z);
+      acc = __fadd_rn(acc, y.w);
+    }
+    P[u] = acc;
   }
-  __syncwarp();
-  uint32_t mu = 0;
-  if (lane == 0) {
-    for (int h = R / 2; h >= 1; h /= 2)
-      for (int j = 0; j < h; ++j) runs[j] = __fadd_rn(runs[j], runs[j + h]);
-    mu = quantize_bits(__fmul_rn(runs[0], 1.0f / float(B * T)), r);
+  __syncwarp();  // the buffer is the next tile's
+  if constexpr (U == 4) {  // h = 64: runs j += j + 64 and j + 32 += j + 96
+    P[0] = __fadd_rn(P[0], P[2]);
+    P[1] = __fadd_rn(P[1], P[3]);
   }
-  __syncwarp();
+  if constexpr (U >= 2) P[0] = __fadd_rn(P[0], P[1]);  // h = 32
+#pragma unroll
+  for (int h = R >= 32 ? 16 : R / 2; h >= 1; h >>= 1) {
+    const float y = __shfl_down_sync(FULL, P[0], h);
+    if (lane < h) P[0] = __fadd_rn(P[0], y);
+  }
+  const uint32_t mu = quantize_bits(__fmul_rn(P[0], 1.0f / float(B * T)), r);
   return __shfl_sync(FULL, mu, 0);
 }
 
 template <int B, int T>
 __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_cost_kernel(KernelArgs a, TiledPtrs p) {
   constexpr int E = B * T / 32;
-  __shared__ float s_runs[kTiledWarps][B * T / 8];
+  __shared__ __align__(16) float s_tile[kTiledWarps][B * T];
   __shared__ uint8_t s_rates[kTiledWarps][4][T];
   FieldInfo* fi = a.fields;
   if (fi->status != 0) return;
@@ -157,32 +212,85 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_cost_kernel(KernelArg
   const uint64_t n = fi->n;
   const uint32_t off = fi->features_off & 7u;
   const bool indep = (off & kOffCross) != 0;
+  const bool lz2_on = !(off & kOffLz2), cen_on = !(off & kOffCenter);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t hdr_base = 64;
   for (uint64_t t = uint64_t(blockIdx.x) * kTiledWarps + warp; t < p.ntiles;
        t += uint64_t(gridDim.x) * kTiledWarps) {
     float d[E];
-    uint32_t q[E], qh[E], l[E];
+    uint32_t q[E], l[E];
     load_tile<B, T, E>(fi->in, n, t, r, lane, d, q);
-    const uint32_t mu = (off & kOffCenter) ? 0u : tile_mu<B, T, E>(d, r, lane, s_runs[warp]);
-    uint32_t C[4];
-#pragma unroll 1
-    for (int v = 0; v < 4; ++v) {
-      const bool centred = v >= 2, second = (v & 1) != 0;
-      const bool on = !(second && (off & kOffLz2)) && !(centred && (off & kOffCenter));
-      C[v] = 0xFFFFFFFFu;
-      if (!on) continue;
+    const uint32_t mu = cen_on ? tile_mu<B, T, E>(d, r, lane, s_tile[warp]) : 0u;
+    uint32_t C[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+    if (!indep) {
+      // With the state carried across blocks, centring changes the tile's first residual
+      // of LZ1 and the first two of LZ2 only (Eq. 4): both variants' residuals once, and
+      // block 0's centred rates from the rest of the block and the changed residuals.
+      uint32_t p1[E], l2[E];
+      predecessors<B, E>(q, false, lane, p1);
 #pragma unroll
-      for (int k = 0; k < E; ++k) qh[k] = centred ? q[k] - mu : q[k];
-      tile_residuals<B, E>(qh, second, indep, lane, l);
-      uint32_t cost = centred ? 4u : 0u;
+      for (int k = 0; k < E; ++k) l[k] = q[k] - p1[k];
+      predecessors<B, E>(l, false, lane, p1);
+#pragma unroll
+      for (int k = 0; k < E; ++k) l2[k] = l[k] - p1[k];
+      uint32_t c1 = 0, c2 = 0, r10 = 0, r20 = 0;
 #pragma unroll
       for (int b = 0; b < T; ++b) {
-        const uint32_t rate = block_rate<B, E>(l, b);
-        if (lane == 0) s_rates[warp][v][b] = uint8_t(rate);
-        cost += cfg_block_cost(rate, B);
+        const uint32_t ra = block_rate<B, E>(l, b), rb = block_rate<B, E>(l2, b);
+        if (lane == 0) {
+          s_rates[warp][0][b] = s_rates[warp][2][b] = uint8_t(ra);
+          s_rates[warp][1][b] = s_rates[warp][3][b] = uint8_t(rb);
+        }
+        if (b == 0) {
+          r10 = ra;
+          r20 = rb;
+        }
+        c1 += cfg_block_cost(ra, B);
+        c2 += cfg_block_cost(rb, B);
       }
-      C[v] = cost;
+      C[0] = c1;
+      if (lz2_on) C[1] = c2;
+      if (cen_on) {
+        uint32_t m1 = lane == 0 ? 0u : uabs32(int32_t(l[0]));
+        uint32_t m2 = lane <= 1 ? 0u : uabs32(int32_t(l2[0]));
+        if (B == 64) {
+          m1 |= uabs32(int32_t(l[B == 64 ? 1 : 0]));
+          m2 |= uabs32(int32_t(l2[B == 64 ? 1 : 0]));
+        }
+        m1 = __reduce_or_sync(FULL, m1);
+        m2 = __reduce_or_sync(FULL, m2);
+        const uint32_t q0 = __shfl_sync(FULL, q[0], 0);
+        const uint32_t l21 = __shfl_sync(FULL, l2[0], 1);
+        const uint32_t c0 = uabs32(int32_t(q0 - mu));  // centred l1_0 = l2_0 = q_0 - mu
+        const uint32_t r1c = 32u - uint32_t(__clz(int(m1 | c0)));
+        const uint32_t r2c = 32u - uint32_t(__clz(int(m2 | c0 | uabs32(int32_t(l21 + mu)))));
+        C[2] = 4u + c1 - cfg_block_cost(r10, B) + cfg_block_cost(r1c, B);
+        if (lz2_on) C[3] = 4u + c2 - cfg_block_cost(r20, B) + cfg_block_cost(r2c, B);
+        if (lane == 0) {
+          s_rates[warp][2][0] = uint8_t(r1c);
+          s_rates[warp][3][0] = uint8_t(r2c);
+        }
+      }
+    } else {
+      // Without it every block restarts, so centring changes every block: each variant's
+      // residuals in turn.
+      uint32_t qh[E];
+#pragma unroll 1
+      for (int v = 0; v < 4; ++v) {
+        const bool centred = v >= 2, second = (v & 1) != 0;
+        if ((second && !lz2_on) || (centred && !cen_on)) continue;
+#pragma unroll
+        for (int k = 0; k < E; ++k) qh[k] = centred ? q[k] - mu : q[k];
+        tile_residuals<B, E>(qh, second, true, lane, l);
+        uint32_t cost = centred ? 4u : 0u;
+#pragma unroll
+        for (int b = 0; b < T; ++b) {
+          const uint32_t rate = block_rate<B, E>(l, b);
+          if (lane == 0) s_rates[warp][v][b] = uint8_t(rate);
+          cost += cfg_block_cost(rate, B);
+        }
+        C[v] = cost;
+      }
     }
     int vs = 0;  // first strict minimum in the listed order (Sec. 4.2.2)
 #pragma unroll
@@ -311,23 +419,18 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_encode_kernel(KernelA
       if (lane == 0) *reinterpret_cast<float*>(dst) = __int2float_rn(int32_t(mu));
       pos = 4;
     }
-#pragma unroll 1
+#pragma unroll
     for (int b = 0; b < T; ++b) {
       const uint32_t rate = hdr[b] & 0x1Fu;
       if (rate == 0) continue;
-      // words 0..rate: word w holds bit w of every element's sign-magnitude value
-      uint32_t hi = 0, lo = 0;
-      for (uint32_t w = 0; w <= rate; ++w) {
-        const uint32_t h = __brev(__ballot_sync(FULL, (vv[b * (B / 32)] >> w) & 1u));
-        uint32_t g = 0;
-        if (B == 64) g = __brev(__ballot_sync(FULL, (vv[b * (B / 32) + (B == 64 ? 1 : 0)] >> w) & 1u));
-        if (uint32_t(lane) == w) {
-          hi = h;
-          lo = g;
-        }
-      }
-      if (uint32_t(lane) <= rate) {
-        uint32_t* o = reinterpret_cast<uint32_t*>(dst + pos + uint32_t(B / 8) * uint32_t(lane));
+      // words 0..rate: word w holds bit w of every element's sign-magnitude value; after
+      // the transpose lane L holds word 31 - L (B = 64: both 32-element halves)
+      const uint32_t w = 31u - uint32_t(lane);
+      const uint32_t hi = warp_transpose32(vv[b * (B / 32)], lane);
+      uint32_t lo = 0;
+      if (B == 64) lo = warp_transpose32(vv[b * (B / 32) + (B == 64 ? 1 : 0)], lane);
+      if (w <= rate) {
+        uint32_t* o = reinterpret_cast<uint32_t*>(dst + pos + uint32_t(B / 8) * w);
         o[0] = bswap32(hi);
         if (B == 64) o[1] = bswap32(lo);
       }
@@ -490,12 +593,18 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_decode_kernel(KernelA
     for (int b = 0; b < T; ++b) {
       const uint32_t rate = h[b] & 0x1Fu;
       if (rate == 0) continue;
-      uint32_t v0 = 0, v1 = 0;  // sign-magnitude values of this lane's element(s) in block b
-      for (uint32_t w = 0; w <= rate; ++w) {
+      // lane L loads word 31 - L (zero past the block's rate + 1 words); the transpose
+      // leaves this lane's element's sign-magnitude value, bit w from word w
+      const uint32_t w = 31u - uint32_t(lane);
+      uint32_t g0 = 0, g1 = 0;
+      if (w <= rate) {
         const uint32_t* wp = reinterpret_cast<const uint32_t*>(src + pos + uint32_t(B / 8) * w);
-        v0 |= ((bswap32(wp[0]) >> (31 - lane)) & 1u) << w;
-        if (B == 64) v1 |= ((bswap32(wp[B == 64 ? 1 : 0]) >> (31 - lane)) & 1u) << w;
+        g0 = bswap32(wp[0]);
+        if (B == 64) g1 = bswap32(wp[B == 64 ? 1 : 0]);
       }
+      const uint32_t v0 = warp_transpose32(g0, lane);
+      uint32_t v1 = 0;
+      if (B == 64) v1 = warp_transpose32(g1, lane);
       const uint32_t m0 = v0 >> 1, m1 = v1 >> 1;
       x[b * (B / 32)] = (v0 & 1u) ? 0u - m0 : m0;
       if (B == 64) x[b * (B / 32) + (B == 64 ? 1 : 0)] = (v1 & 1u) ? 0u - m1 : m1;

@@ -113,21 +113,40 @@ __device__ __forceinline__ void tile_residuals(const uint32_t (&qh)[E], bool sec
   }
 }
 
+// Lane constants of warp_transpose32, one per exchange step (j = 16, 8, 4, 2, 1): the
+// lane's own bits (the lower lane of a pair keeps the bits outside the low j of each 2j,
+// the upper lane those inside) and the rotation that lines the partner's bits up.
+struct Xpose {
+  uint32_t keep[5];
+  uint32_t amt[5];
+};
+
+__device__ __forceinline__ Xpose xpose_consts(int lane) {
+  Xpose c;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
+    const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
+                     : j == 2 ? 0x33333333u : 0x55555555u;
+    const bool upper = (lane & j) != 0;
+    c.keep[s] = upper ? m : ~m;
+    c.amt[s] = upper ? uint32_t(32 - j) : uint32_t(j);
+  }
+  return c;
+}
+
 // 32 x 32 bit transpose across the warp, anti-diagonal form: on return bit c of lane L is
 // bit 31 - L of lane 31 - c on entry. Five exchange steps (j = 16 .. 1): lanes L and L ^ j
 // trade the j x j bit blocks off the diagonal of their 2j x 2j block, each taking a
 // rotated copy of the partner's word and a bit-select. Lane L holds plane 31 - L of the
 // 32 elements given one per lane (element e at bit 31 - e), and the converse.
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, int lane) {
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t v, const Xpose& c) {
 #pragma unroll
-  for (int j = 16; j >= 1; j >>= 1) {
-    const uint32_t m = j == 16 ? 0x0000FFFFu : j == 8 ? 0x00FF00FFu : j == 4 ? 0x0F0F0F0Fu
-                     : j == 2 ? 0x33333333u : 0x55555555u;
-    const bool upper = (lane & j) != 0;
+  for (int s = 0; s < 5; ++s) {
+    const int j = 16 >> s;
     const uint32_t x = __shfl_xor_sync(FULL, v, j);
-    const uint32_t sh = __funnelshift_r(x, x, upper ? 32 - j : j);  // rotate right
-    const uint32_t keep = upper ? m : ~m;                            // this lane's own bits
-    v = (v & keep) | (sh & ~keep);
+    const uint32_t sh = __funnelshift_r(x, x, j == 16 ? 16u : c.amt[s]);  // rotate right
+    v = (v & c.keep[s]) | (sh & ~c.keep[s]);
   }
   return v;
 }
@@ -215,11 +234,14 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_cost_kernel(KernelArg
   const bool lz2_on = !(off & kOffLz2), cen_on = !(off & kOffCenter);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t hdr_base = 64;
+  // the record's pointers once: the byte stores below may alias anything
+  const float* const in = fi->in;
+  uint8_t* const out = fi->out;
   for (uint64_t t = uint64_t(blockIdx.x) * kTiledWarps + warp; t < p.ntiles;
        t += uint64_t(gridDim.x) * kTiledWarps) {
     float d[E];
     uint32_t q[E], l[E];
-    load_tile<B, T, E>(fi->in, n, t, r, lane, d, q);
+    load_tile<B, T, E>(in, n, t, r, lane, d, q);
     const uint32_t mu = cen_on ? tile_mu<B, T, E>(d, r, lane, s_tile[warp]) : 0u;
     uint32_t C[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
     if (!indep) {
@@ -300,7 +322,7 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_cost_kernel(KernelArg
     if (lane < T) {
       uint32_t hb = s_rates[warp][vs][lane];
       if (lane == 0) hb |= ((vs & 1) ? 0x80u : 0u) | (vs >= 2 ? 0x40u : 0u);
-      fi->out[hdr_base + uint64_t(T) * t + lane] = uint8_t(hb);
+      out[hdr_base + uint64_t(T) * t + lane] = uint8_t(hb);
     }
     if (lane == 0) {
       p.sizes[t] = C[vs];
@@ -395,11 +417,14 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_encode_kernel(KernelA
   const uint64_t n = fi->n;
   const bool indep = (fi->features_off & kOffCross) != 0;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const Xpose xc = xpose_consts(lane);
+  const float* const in = fi->in;
+  uint8_t* const out = fi->out;
   for (uint64_t t = uint64_t(blockIdx.x) * kTiledWarps + warp; t < p.ntiles;
        t += uint64_t(gridDim.x) * kTiledWarps) {
     float d[E];
     uint32_t q[E], l[E];
-    load_tile<B, T, E>(fi->in, n, t, r, lane, d, q);
+    load_tile<B, T, E>(in, n, t, r, lane, d, q);
     const uint64_t rec = p.rec[t];
     const int vs = int(rec & 3u);
     const uint32_t mu = uint32_t(rec >> 32);
@@ -412,8 +437,8 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_encode_kernel(KernelA
     uint32_t vv[E];  // sign-magnitude: bit 0 the sign, bit k + 1 magnitude plane k
 #pragma unroll
     for (int k = 0; k < E; ++k) vv[k] = (uabs32(int32_t(l[k])) << 1) | (l[k] >> 31);
-    uint8_t* dst = fi->out + data_base + p.offs[t];
-    const uint8_t* hdr = fi->out + 64 + uint64_t(T) * t;
+    uint8_t* dst = out + data_base + p.offs[t];
+    const uint8_t* hdr = out + 64 + uint64_t(T) * t;
     uint32_t pos = 0;
     if (centred) {
       if (lane == 0) *reinterpret_cast<float*>(dst) = __int2float_rn(int32_t(mu));
@@ -426,9 +451,9 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_encode_kernel(KernelA
       // words 0..rate: word w holds bit w of every element's sign-magnitude value; after
       // the transpose lane L holds word 31 - L (B = 64: both 32-element halves)
       const uint32_t w = 31u - uint32_t(lane);
-      const uint32_t hi = warp_transpose32(vv[b * (B / 32)], lane);
+      const uint32_t hi = warp_transpose32(vv[b * (B / 32)], xc);
       uint32_t lo = 0;
-      if (B == 64) lo = warp_transpose32(vv[b * (B / 32) + (B == 64 ? 1 : 0)], lane);
+      if (B == 64) lo = warp_transpose32(vv[b * (B / 32) + (B == 64 ? 1 : 0)], xc);
       if (w <= rate) {
         uint32_t* o = reinterpret_cast<uint32_t*>(dst + pos + uint32_t(B / 8) * w);
         o[0] = bswap32(hi);
@@ -569,12 +594,16 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_decode_kernel(KernelA
   const float s = fi->s;
   const uint64_t n = fi->n;
   const bool indep = (fi->features_off & kOffCross) != 0;
-  const uint64_t data_base = 64 + uint64_t(T) * fi->T;
+  const uint64_t NT = fi->T;
+  const uint64_t data_base = 64 + uint64_t(T) * NT;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint64_t t = uint64_t(blockIdx.x) * kTiledWarps + warp; t < fi->T;
+  const Xpose xc = xpose_consts(lane);
+  const uint8_t* const sin = fi->sin;
+  float* const dout = fi->dout;
+  for (uint64_t t = uint64_t(blockIdx.x) * kTiledWarps + warp; t < NT;
        t += uint64_t(gridDim.x) * kTiledWarps) {
-    const uint8_t* h = fi->sin + 64 + uint64_t(T) * t;
-    const uint8_t* src = fi->sin + data_base + p.offs[t];
+    const uint8_t* h = sin + 64 + uint64_t(T) * t;
+    const uint8_t* src = sin + data_base + p.offs[t];
     const bool second = (h[0] & 0x80u) != 0, centred = (h[0] & 0x40u) != 0;
     uint32_t mu = 0;
     bool good = true;
@@ -602,9 +631,9 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_decode_kernel(KernelA
         g0 = bswap32(wp[0]);
         if (B == 64) g1 = bswap32(wp[B == 64 ? 1 : 0]);
       }
-      const uint32_t v0 = warp_transpose32(g0, lane);
+      const uint32_t v0 = warp_transpose32(g0, xc);
       uint32_t v1 = 0;
-      if (B == 64) v1 = warp_transpose32(g1, lane);
+      if (B == 64) v1 = warp_transpose32(g1, xc);
       const uint32_t m0 = v0 >> 1, m1 = v1 >> 1;
       x[b * (B / 32)] = (v0 & 1u) ? 0u - m0 : m0;
       if (B == 64) x[b * (B / 32) + (B == 64 ? 1 : 0)] = (v1 & 1u) ? 0u - m1 : m1;
@@ -628,7 +657,7 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_decode_kernel(KernelA
 #pragma unroll
     for (int k = 0; k < E; ++k) {
       const uint64_t i = t * uint64_t(B * T) + uint64_t(32 * k + lane);
-      if (i < n) fi->dout[i] = __fmul_rn(__int2float_rn(int32_t(x[k] + mu)), s);
+      if (i < n) dout[i] = __fmul_rn(__int2float_rn(int32_t(x[k] + mu)), s);
     }
     if (!__all_sync(FULL, good) && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
   }

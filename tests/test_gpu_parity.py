@@ -273,3 +273,59 @@ def test_config3_particles_2p28(fszlib, oracle):
     _cuda()
     x = inputs.particles(1 << 28, seed=2, device="cuda")
     sampled_parity(fszlib, oracle, x, 1e-4, (1 << 28,), nsample=64)
+
+
+def test_field_past_2p32_elements(fszlib, oracle):
+    """A 1-D field of 2^32 + 777 elements (17.2 GB) with a stream of about 4.9 GB:
+    element and byte offsets pass 2^32, the last tile and the last 16 bytes are ragged. Every element by the
+    quantization property and the bound, on the device in slices; the field's parameters
+    from its value range; sampled tiles (the ones around element 2^32 among them) byte for
+    byte against the oracle's tile encoder."""
+    dev = _cuda()
+    if torch.cuda.mem_get_info()[0] < (80 << 30):
+        pytest.skip("needs about 80 GB of free device memory")
+    n = (1 << 32) + 777
+    S = 1 << 28
+    xd = torch.empty(n, dtype=torch.float32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    for k0 in range(0, n, S):
+        k1 = min(n, k0 + S)
+        i = torch.arange(k0, k1, dtype=torch.float64, device=dev)
+        xd[k0:k1] = (50.0 * torch.sin(i * 2.1e-4) + 20.0 * torch.sin(i * 3.7e-7)
+                     + 2.0 * torch.randn(k1 - k0, generator=g, dtype=torch.float64, device=dev)
+                     ).to(torch.float32)
+        del i
+    rel = 1e-4  # noise of ~70 steps: CR ~3.5, a stream past 2^32 bytes
+    sb, nb = fszlib.compress(xd, rel, fszlib.EB_REL)
+    lo, hi = float(xd.min().item()), float(xd.max().item())
+    assert bool(torch.isfinite(xd).all())
+    p = oracle.params(oracle.REL, rel, lo, hi, True, n)
+    h = fszlib.fsz_read_header(sb[:64].cpu().numpy().tobytes())
+    assert h["n"] == n and h["total_bytes"] == nb and np.float32(h["step"]) == np.float32(p.s)
+    y = fszlib.decompress(sb, n=n)
+    r32 = torch.tensor(p.r, dtype=torch.float32, device=dev)
+    s32 = torch.tensor(p.s, dtype=torch.float32, device=dev)
+    for k0 in range(0, n, S):
+        xs, ys = xd[k0:k0 + S], y[k0:k0 + S]
+        want = (torch.round(xs * r32) + 0.0) * s32
+        assert torch.equal(want.view(torch.int32), ys.view(torch.int32)), k0
+        assert (xs.double() - ys.double()).abs().max().item() <= p.eb, k0
+        del want
+    del y
+    T = (n + 255) // 256
+    hdr = sb[64:64 + 8 * T].cpu().numpy().reshape(T, 8).astype(np.int64)
+    rates = hdr & 31
+    sizes = np.where(rates == 0, 0, 4 + 4 * rates).sum(axis=1) + np.where(hdr[:, 0] & 0x40, 4, 0)
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    data0 = 64 + 8 * T
+    assert data0 + int(offs[-1]) == nb and data0 + int(offs[-1]) > (1 << 32)
+    rng = np.random.default_rng(11)
+    starts = set(int(t) for t in rng.integers(0, T - 4, size=32))
+    starts |= {0, T - 4, (1 << 24) - 2}  # tile 2^24 starts at element 2^32
+    for t0 in sorted(starts):
+        t1 = min(T, t0 + 4)
+        xs = xd[256 * t0:min(n, 256 * t1)].cpu().numpy()
+        rh, rd = oracle.compress_tiles(xs, p.r, 0, t1 - t0)
+        assert sb[64 + 8 * t0:64 + 8 * t1].cpu().numpy().tobytes() == rh, t0
+        assert sb[data0 + int(offs[t0]):data0 + int(offs[t1])].cpu().numpy().tobytes() == rd, t0

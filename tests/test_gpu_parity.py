@@ -205,6 +205,67 @@ def test_corrupt_streams_detected(fszlib, oracle):
         assert _status_of_decompress(fszlib, bytes(b), n) in (fszlib.OK, fszlib.ERR_CORRUPT)
 
 
+def _decode(fszlib, stream: bytes, n):
+    """(device status, reconstruction) of one decode through the C ABI."""
+    dev = _cuda()
+    buf = torch.zeros(len(stream) + 64, dtype=torch.uint8, device=dev)
+    buf[: len(stream)] = torch.from_numpy(np.frombuffer(stream, np.uint8).copy()).to(dev)
+    out = torch.zeros(n, dtype=torch.float32, device=dev)
+    ws = fszlib.Workspace(n, dev)
+    sp = torch.cuda.current_stream().cuda_stream
+    assert fszlib.fsz_decompress(buf.data_ptr(), len(stream), out.data_ptr(), n, ws.ptr, ws.bytes,
+                                 sp) == fszlib.OK
+    return fszlib.fsz_check(ws.ptr, sp), out.cpu().numpy()
+
+
+def test_damaged_streams_decode_as_the_oracle(fszlib, oracle):
+    """Damage the format still admits (payload bytes, rates traded between two blocks of a
+    tile at equal size, random bytes past the preamble) decodes on the GPU to exactly the
+    oracle decoder's floats (wrap-around integer arithmetic, the same conversions); what
+    either decoder refuses, both refuse."""
+    x = inputs.sinusoids(300000, seed=4)
+    s = oracle.compress(x, 1e-4, oracle.REL)
+    n = x.size
+    T = (n + 255) // 256
+    data0 = 64 + 8 * T
+    rng = np.random.default_rng(1)
+    cases = []
+    for _ in range(10):  # payload bytes
+        b = bytearray(s)
+        for pos in rng.integers(data0, len(s), size=6):
+            b[int(pos)] = int(rng.integers(0, 256))
+        cases.append(b)
+    hdr = np.frombuffer(s[64:data0], np.uint8).reshape(T, 8)
+    for _ in range(10):  # one block's rate up by one, another's down by one: same sizes
+        while True:
+            t = int(rng.integers(0, T))
+            r = hdr[t] & 31
+            up = [k for k in range(8) if 1 <= r[k] <= 30]
+            down = [k for k in range(8) if r[k] >= 2]
+            pairs = [(i, j) for i in up for j in down if i != j]
+            if pairs:
+                break
+        i, j = pairs[int(rng.integers(0, len(pairs)))]
+        b = bytearray(s)
+        b[64 + 8 * t + i] += 1
+        b[64 + 8 * t + j] -= 1
+        cases.append(b)
+    for _ in range(10):  # anything past the preamble
+        b = bytearray(s)
+        for pos in rng.integers(64, len(s), size=3):
+            b[int(pos)] = int(rng.integers(0, 256))
+        cases.append(b)
+    seen = set()
+    for k, b in enumerate(cases):
+        want = oracle.decompress_status(bytes(b))
+        st, y = _decode(fszlib, bytes(b), n)
+        assert st == want, (k, st, want)
+        seen.add(st)
+        if st == fszlib.OK:
+            assert np.array_equal(y.view(np.uint32), oracle.decompress(bytes(b)).view(np.uint32)), k
+    assert fszlib.OK in seen
+
+
 def test_lookback_timeout_is_reported(fszlib, oracle):
     # A chunk that never publishes its flag: its successor's bounded wait runs out, the
     # kernel still finishes and the workspace status reads FSZ_ERR_TIMEOUT.

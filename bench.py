@@ -802,6 +802,15 @@ def main():
             raise fsz.FszError(st, "quality decode")
         eb = rel * (float(x.max().item()) - float(x.min().item()))
         qual.append(fsz.quality(x, recon, eb, sizes[j]))
+        # the stream's own record: the requested bound (REL) and the step from its preamble,
+        # and how many tiles took each variant (byte 0 of a tile's header: bit 7 order 2,
+        # bit 6 centred)
+        pre = fsz.fsz_read_header(outs[j][:64].cpu().numpy().tobytes())
+        T = (n + 255) // 256
+        sel = (outs[j][64:64 + 8 * T:8].to(torch.int64) >> 6) & 3
+        cnt = torch.bincount(sel, minlength=4).tolist()
+        qual[-1].update({"eb": eb, "eb_requested": pre["eb"], "step": pre["step"],
+                         "variants": {"lz1": cnt[0], "lz1c": cnt[1], "lz2": cnt[2], "lz2c": cnt[3]}})
     p_last = qual[-1]["max_abs_err"]
 
     comp_ms, enc_ms, stats_ms, dec_ms = ([[] for _ in jobs] for _ in range(4))
@@ -964,6 +973,10 @@ def main():
                         "psnr_db": qual[j]["psnr_db"], "bit_rate": qual[j]["bit_rate"],
                         "nrmse": qual[j]["nrmse"], "max_abs_err": qual[j]["max_abs_err"],
                         "errors_over_bound": qual[j]["over_bound"],
+                        "eb": qual[j]["eb"], "eb_requested": qual[j]["eb_requested"],
+                        "step": qual[j]["step"],
+                        "max_err_over_eb": qual[j]["max_abs_err"] / qual[j]["eb"],
+                        "variants": qual[j]["variants"],
                         "compress_gbs": 4 * n / med(comp_ms[j]) / 1e6,
                         "encode_kernel_gbs": 4 * n / med(enc_ms[j]) / 1e6,
                         "encode_kernel_hbm_gbs": (4 * n + sizes[j]) / med(enc_ms[j]) / 1e6,

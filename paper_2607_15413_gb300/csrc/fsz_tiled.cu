@@ -77,6 +77,14 @@ __device__ __forceinline__ uint32_t quantize_bits(float d, float r) {
 
 __device__ __forceinline__ uint32_t bswap32(uint32_t w) { return __byte_perm(w, 0, 0x0123); }
 
+// A warp's tile buffer in shared memory holds each 32-element row (one register of the
+// warp) in kRowWords words, so element e sits at word e + 4 (e / 32). Row writes stay
+// conflict-free, and the 128-bit reads of any 8 consecutive lanes at a stride of 4, 8, 16
+// or 32 words (a lane's 8-element run, or its E consecutive elements) fall in 8 distinct
+// bank groups.
+constexpr int kRowWords = 36;
+__device__ __forceinline__ int padded(int e) { return e + 4 * (e >> 5); }
+
 // The predecessor of every element of the tile (element 32 k + L sits in register k of
 // lane L): one rotation of each register by a lane, lane 0 taking the previous register's
 // rotated value (element 32 k - 1); zero before the tile, and before every block when
@@ -185,7 +193,7 @@ __device__ __forceinline__ uint32_t tile_mu(const float (&d)[E], float r, int la
   constexpr int R = B * T / 8;
   constexpr int U = (R + 31) / 32;  // runs per lane: 1, 2 or 4
 #pragma unroll
-  for (int k = 0; k < E; ++k) tile[32 * k + lane] = d[k];
+  for (int k = 0; k < E; ++k) tile[kRowWords * k + lane] = d[k];
   __syncwarp();
   float P[U];
 #pragma unroll
@@ -193,8 +201,8 @@ __device__ __forceinline__ uint32_t tile_mu(const float (&d)[E], float r, int la
     const int j = lane + 32 * u;
     float acc = 0.0f;
     if (j < R) {
-      const float4 x = reinterpret_cast<const float4*>(tile)[2 * j];
-      const float4 y = reinterpret_cast<const float4*>(tile)[2 * j + 1];
+      const float4 x = *reinterpret_cast<const float4*>(tile + padded(8 * j));
+      const float4 y = *reinterpret_cast<const float4*>(tile + padded(8 * j + 4));
       acc = __fadd_rn(x.x, x.y);
       acc = __fadd_rn(acc, x.z);
       acc = __fadd_rn(acc, x.w);
@@ -223,7 +231,7 @@ __device__ __forceinline__ uint32_t tile_mu(const float (&d)[E], float r, int la
 template <int B, int T>
 __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_cost_kernel(KernelArgs a, TiledPtrs p) {
   constexpr int E = B * T / 32;
-  __shared__ __align__(16) float s_tile[kTiledWarps][B * T];
+  __shared__ __align__(16) float s_tile[kTiledWarps][kRowWords * E];
   __shared__ uint8_t s_rates[kTiledWarps][4][T];
   FieldInfo* fi = a.fields;
   if (fi->status != 0) return;
@@ -583,6 +591,8 @@ template <int B, int T>
 __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_decode_kernel(KernelArgs a, TiledPtrs p,
                                                                          uint32_t nparts) {
   constexpr int E = B * T / 32;
+  static_assert(E % 4 == 0, "each lane's run is whole 128-bit words");
+  __shared__ __align__(16) uint32_t s_tile[kTiledWarps][E <= 16 ? kRowWords * E : 4];
   FieldInfo* fi = a.fields;
   int cb = 0, ct = 0;
   if (!config_of(fi->features_off, &cb, &ct) || cb != B || ct != T) return;  // another instance's
@@ -640,24 +650,74 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_decode_kernel(KernelA
       pos += uint32_t(B / 8) * (rate + 1);
     }
     // inverse prediction: inclusive prefix sums in element order (once for LZ1, twice for
-    // LZ2), restarting at every block without the cross-block state
+    // LZ2), restarting at every block without the cross-block state.
+    if constexpr (E <= 16) {
+      // Through the warp's buffer each lane takes E consecutive elements: a sum runs along
+      // the lane, then one scan of the lanes' totals (over the 32 / T lanes of a block
+      // when blocks restart) gives each lane its offset; mu comes in with the last offset.
+      uint32_t* const tb = s_tile[warp];
+#pragma unroll
+      for (int k = 0; k < E; ++k) tb[kRowWords * k + lane] = x[k];
+      __syncwarp();
+      uint32_t v[E];
+#pragma unroll
+      for (int u = 0; u < E / 4; ++u) {
+        const uint4 w4 = *reinterpret_cast<const uint4*>(tb + padded(E * lane + 4 * u));
+        v[4 * u] = w4.x; v[4 * u + 1] = w4.y; v[4 * u + 2] = w4.z; v[4 * u + 3] = w4.w;
+      }
+      __syncwarp();  // the buffer is the next tile's
+      auto prefix = [&](const uint32_t add) {
+#pragma unroll
+        for (int i = 1; i < E; ++i) v[i] += v[i - 1];
+        const uint32_t tot = v[E - 1];
+        uint32_t inc = tot;
+        if (indep) {
+#pragma unroll
+          for (int o = 1; o < 32 / T; o <<= 1) inc = scan_step_up<32 / T>(inc, o);
+        } else {
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) inc = scan_step_up(inc, o);
+        }
+        const uint32_t ex = inc - tot + add;
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] += ex;
+      };
+      if (second) prefix(0u);
+      prefix(mu);
+      float o[E];
+#pragma unroll
+      for (int i = 0; i < E; ++i) o[i] = __fmul_rn(__int2float_rn(int32_t(v[i])), s);
+      const uint64_t e0 = t * uint64_t(B * T) + uint64_t(E) * uint64_t(lane);
+      if (t * uint64_t(B * T) + uint64_t(B * T) <= n) {  // a whole tile: 128-bit stores
+#pragma unroll
+        for (int u = 0; u < E / 4; ++u)
+          reinterpret_cast<float4*>(dout + e0)[u] = make_float4(o[4 * u], o[4 * u + 1], o[4 * u + 2], o[4 * u + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i)
+          if (e0 + uint64_t(i) < n) dout[e0 + i] = o[i];
+      }
+    } else {
+      // 32 elements per lane would make a 31-step chain per sum: a warp scan per register
+      // instead, the running total carried from one register to the next.
 #pragma unroll 1
-    for (int pass = 0; pass < (second ? 2 : 1); ++pass) {
-      uint32_t carry = 0;
+      for (int pass = 0; pass < (second ? 2 : 1); ++pass) {
+        uint32_t carry = 0;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          if (indep && ((32 * k) % B) == 0) carry = 0;
+          uint32_t inc = x[k];
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) inc = scan_step_up(inc, o);
+          x[k] = inc + carry;
+          carry = __shfl_sync(FULL, x[k], 31);
+        }
+      }
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        if (indep && ((32 * k) % B) == 0) carry = 0;
-        uint32_t inc = x[k];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) inc = scan_step_up(inc, o);
-        x[k] = inc + carry;
-        carry = __shfl_sync(FULL, x[k], 31);
+        const uint64_t i = t * uint64_t(B * T) + uint64_t(32 * k + lane);
+        if (i < n) dout[i] = __fmul_rn(__int2float_rn(int32_t(x[k] + mu)), s);
       }
-    }
-#pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const uint64_t i = t * uint64_t(B * T) + uint64_t(32 * k + lane);
-      if (i < n) dout[i] = __fmul_rn(__int2float_rn(int32_t(x[k] + mu)), s);
     }
     if (!__all_sync(FULL, good) && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
   }

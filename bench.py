@@ -647,7 +647,7 @@ def run_config(args, fsz, inputs, dev, cfg: int):
             raise fsz.FszError(st, f"config {cfg}")
         k = int(nb[0].item())
         q = fsz.quality(x, rec, rel * (float(x.max().item()) - float(x.min().item())), k)
-        nbytes_in, comp_bytes = 4 * n, k
+        nbytes_in = 4 * n
         out.update({"n": n, "cr": 4 * n / k, "psnr_db": q["psnr_db"], "bit_rate": q["bit_rate"],
                     "errors_over_bound": q["over_bound"]})
     else:
@@ -666,16 +666,19 @@ def run_config(args, fsz, inputs, dev, cfg: int):
         for k in range(max(3, args.warmup) + args.steps):
             e = [ev() for _ in range(3)]
             e[0].record(stream)
-            cb.launch_graph()
+            st = cb.launch_graph()
             e[1].record(stream)
-            db.launch_graph()
+            st |= db.launch_graph()
             e[2].record(stream)
+            if st:
+                raise fsz.FszError(st, "config 4 graph launch")
             torch.cuda.synchronize(dev)
             if k >= max(3, args.warmup):
                 times["compress"].append(e[0].elapsed_time(e[1]))
                 times["decompress"].append(e[1].elapsed_time(e[2]))
-        if cb.status()[0] != fsz.OK or db.status()[0] != fsz.OK:
-            raise fsz.FszError(fsz.ERR_CORRUPT, "config 4")
+        st = cb.status()[0] or db.status()[0]
+        if st != fsz.OK:
+            raise fsz.FszError(st, "config 4")
         out.update({"n": nbytes_in // 4, "fields": len(fields), "cr": nbytes_in / comp_bytes})
     for name, ts in times.items():
         out[f"{name}_gbs"] = nbytes_in / statistics.median(ts) / 1e6

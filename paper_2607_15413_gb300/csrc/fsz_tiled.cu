@@ -7,9 +7,10 @@
 // A generic path for the configuration sweep, in the paper's two-read structure: the
 // value-range pass; a cost pass (one warp per tile: the four variants' costs, the
 // selection, the rate header, the tile's size); an exclusive scan of the sizes; an
-// encoding pass (the tile read again, the bit-planes built by warp ballots); the
-// preamble. Element i of a tile sits in register i / 32 of lane i % 32, so every load and
-// store of a register is one coalesced 128-byte row. The decoder mirrors it. The
+// encoding pass (the tile read again, each 32-element row's bit-planes built by one
+// warp bit transpose); the preamble. Element i of a tile sits in register i / 32 of lane
+// i % 32, so every load and store of a register is one coalesced 128-byte row. The
+// decoder mirrors it (the same transpose, then prefix sums in element order). The
 // specialised single-pass kernels cover the default configuration only.
 #include <algorithm>
 

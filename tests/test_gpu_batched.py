@@ -49,7 +49,7 @@ def test_batched_matches_single_and_oracle(fszlib, oracle):
     batch = fszlib.CompressBatch(fields, dev)
     assert batch.run() == fszlib.OK
     st, per = batch.status()
-    # the oracle's verdict per field (a tiny field with a large offset can be refused)
+    # the oracle's status per field (a tiny field with a large offset can be refused)
     refs, want = [], []
     for x, shape, mode, eb in host:
         try:

@@ -386,3 +386,138 @@ def test_corrupt_streams_are_rejected(oracle):
             bad[int(pos)] = int(rng.integers(0, 256))
         assert oracle.decompress_status(bytes(bad)) in (oracle.OK, oracle.ERR_CORRUPT,
                                                         oracle.ERR_CAPACITY)
+
+
+# --------------------------------------------------------------------------- value range, ties, mean order
+
+def _stats_np(x):
+    """numpy restatement of the value-range pass: min, max and the all-finite flag."""
+    fin = bool(np.isfinite(x).all())
+    if not fin or x.size == 0:
+        return None, None, fin
+    return float(x.min()), float(x.max()), fin
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 255, 256, 257, 4099])
+def test_stats_against_numpy(oracle, n):
+    # The extremes are put at the first and at the last element (a loop that skips either
+    # end fails here), and one check puts them in the middle.
+    rng = np.random.default_rng(n)
+    base = rng.uniform(-5.0, 5.0, n).astype(np.float32)
+    for lo_at, hi_at in ((0, n - 1), (n - 1, 0), (n // 2, n // 3)):
+        x = base.copy()
+        x[hi_at] = np.float32(7.25)
+        if lo_at != hi_at:
+            x[lo_at] = np.float32(-9.5)
+        lo, hi, fin = oracle.stats(x)
+        want = _stats_np(x)
+        assert fin and want[2]
+        assert (lo, hi) == (want[0], want[1]), (lo_at, hi_at)
+    for bad in (np.nan, np.inf, -np.inf):
+        for at in {0, n - 1, n // 2}:
+            x = base.copy()
+            x[at] = bad
+            assert oracle.stats(x)[2] is False and _stats_np(x)[2] is False, (bad, at)
+
+
+def test_stats_empty_and_constant(oracle):
+    assert oracle.stats(np.zeros(0, np.float32)) == (0.0, 0.0, True)
+    assert oracle.stats(np.full(300, -3.5, np.float32)) == (-3.5, -3.5, True)
+
+
+def _exact_ties(r, ks):
+    """float32 inputs d with fl32(d r) exactly k + 1/2, found among the float32 neighbours
+    of (k + 1/2) / r (numpy float32 multiplies round once, to nearest)."""
+    r32 = np.float32(r)
+    out = []
+    for k in ks:
+        t = np.float32(k + 0.5)
+        d = np.float32(float(t) / float(r32))
+        for _ in range(6):
+            d = np.nextafter(d, np.float32(-np.inf))
+        for _ in range(13):
+            if np.float32(d * r32) == t:
+                out.append(d)
+                break
+            d = np.nextafter(d, np.float32(np.inf))
+    return np.array(out, np.float32)
+
+
+@pytest.mark.parametrize("r", [0.125, 1.0, 2.0 ** -20, 1.0 / 0.0062, 1.0 / 3.3e-3, 37.9])
+def test_quantize_ties_to_even(oracle, r):
+    # Sec. 4.2.2 rounds d / (2 eb) to an integer; the reading fixes t = fl32(d r) and the
+    # nearest integer with ties to even. Inputs that land exactly on k + 1/2 for even and
+    # odd k, both signs, from 1/2 up to 2^17 + 1/2: a half-away-from-zero rounding fails.
+    rng = np.random.default_rng(int(r * 1000) % 2 ** 31)
+    ks = sorted(set([0, 1, 2, 3, 4, 5, 100, 101, 4096, 4097, 131070, 131071]
+                    + [int(k) for k in rng.integers(0, 1 << 17, 60)]))
+    ks = ks + [-k - 1 for k in ks]            # k + 1/2 for k = -1, -2, ...: -1/2, -3/2, ...
+    d = _exact_ties(r, ks)
+    assert d.size >= len(ks) * 3 // 4
+    t = (d * np.float32(r)).astype(np.float32)
+    assert np.all(t - np.floor(t) == 0.5)     # every input sits on a tie
+    want = np.rint(t).astype(np.int64)        # numpy's rint: ties to even
+    got = oracle.quantize(d, r).astype(np.int64)
+    assert np.array_equal(got, want)
+    assert np.all(got % 2 == 0)               # every tie went to the even neighbour
+    # off the ties the same rule is plain rounding to nearest
+    y = rng.uniform(-1e5, 1e5, 2000).astype(np.float32) / np.float32(r)
+    y = y.astype(np.float32)
+    assert np.array_equal(oracle.quantize(y, r), np.rint(y * np.float32(r)).astype(np.int32))
+
+
+def _mu_np(d, r, order):
+    """The tile mean's quantized value with the float32 sum taken in a given order."""
+    d = np.asarray(d, np.float32)
+    if order == "runs":        # 8-element runs left to right, then the pairwise tree
+        P = d.reshape(32, 8)[:, 0].copy()
+        for i in range(1, 8):
+            P = (P + d.reshape(32, 8)[:, i]).astype(np.float32)
+        h = 16
+        while h >= 1:
+            P[:h] = (P[:h] + P[h:2 * h]).astype(np.float32)
+            h //= 2
+        S = P[0]
+    elif order == "sequential":
+        S = d[0]
+        for v in d[1:]:
+            S = np.float32(S + v)
+    elif order == "strided":   # P_j = d_j + d_{32+j} + ... + d_{224+j}, then the tree
+        P = d[0:32].copy()
+        for i in range(1, 8):
+            P = (P + d[32 * i:32 * i + 32]).astype(np.float32)
+        h = 16
+        while h >= 1:
+            P[:h] = (P[:h] + P[h:2 * h]).astype(np.float32)
+            h //= 2
+        S = P[0]
+    else:
+        raise ValueError(order)
+    dbar = np.float32(S * np.float32(2.0 ** -8))
+    return int(np.rint(np.float32(dbar * np.float32(r))))
+
+
+def test_tile_mu_summation_order(oracle):
+    # Sec. 4.2.2 takes the tile's floating-point mean; the reading fixes the order of the
+    # float32 sum (8-element runs, then a pairwise tree). Tiles with large cancelling terms
+    # make the order visible: each one used here gives a different mu under a sequential
+    # sum and under the strided order, so a summation order other than the fixed one fails.
+    rng = np.random.default_rng(2024)
+    found = 0
+    for _ in range(4000):
+        mag = 2.0 ** rng.integers(0, 31, 256)
+        d = (rng.choice([-1.0, 1.0], 256) * mag * rng.uniform(1.0, 2.0, 256)).astype(np.float32)
+        r = 1.0
+        m_runs = _mu_np(d, r, "runs")
+        if m_runs in (_mu_np(d, r, "sequential"), _mu_np(d, r, "strided")):
+            continue
+        assert oracle.tile_mu(d, r) == m_runs
+        found += 1
+        if found == 25:
+            break
+    assert found == 25
+    # and on ordinary tiles, with the step of a real field
+    for seed in range(40):
+        x = inputs.grf((8, 8, 4), seed=seed).ravel() * np.float32(100.0) + np.float32(seed)
+        p = oracle.params_for(x, oracle.REL, 1e-4)
+        assert oracle.tile_mu(x, p.r) == _mu_np(x, p.r, "runs")

@@ -289,28 +289,14 @@ def run_serving(fsz, inputs, dev, nreq: int = 20000, seed: int = 4, linger_us: i
     import torch
 
     from paper_2607_15413_gb300 import serve
-    pool_shape = (256, 512, 512)
-    g = inputs.grf(pool_shape, seed=seed, device=str(dev))
-    pool = [g.reshape(-1).contiguous(),
-            inputs.particles(g.numel(), seed=seed, device=str(dev)),
-            inputs.zero_slabs(pool_shape, seed=seed, device=str(dev), base=g).reshape(-1).contiguous()]
-    del g
+    pool = inputs.serving_pool(seed=seed, device=str(dev))
+    numels = [p.numel() for p in pool]
     torch.cuda.empty_cache()
     rng = random.Random(seed)
     srv = serve.Server(budget_bytes=40 << 30, n_slots=4, max_batch=32, max_batch_elems=4 << 30,
                        linger_s=linger_us * 1e-6, futures=False)
     L = fsz.lib()
     next_id = [1]
-
-    def windows(count):
-        out = []
-        for _ in range(count):
-            src = pool[rng.randrange(3)]
-            n = int(math.exp(rng.uniform(math.log(4096), math.log(64 << 20))))
-            n = max(4, min(n, src.numel()) // 4 * 4)
-            off = rng.randrange(0, (src.numel() - n) // 4 + 1) * 4
-            out.append((src.data_ptr() + 4 * off, n, rng.choice([1e-2, 1e-3, 1e-4])))
-        return out
 
     def trace(count, sources, dec_share=0.4):
         """A request table: compress requests of pool windows, and with `dec_share`
@@ -319,12 +305,13 @@ def run_serving(fsz, inputs, dev, nreq: int = 20000, seed: int = 4, linger_us: i
         t["id"] = np.arange(next_id[0], next_id[0] + count, dtype=np.uint64)
         next_id[0] += count
         rows = []
-        for ptr, n, rel in windows(count):
-            if sources and rng.random() < dec_share:
-                sp, sb, sn = sources[rng.randrange(len(sources))]
+        for row in inputs.serving_trace(rng, numels, count, len(sources or ()), dec_share):
+            if row[0] == "decompress":
+                sp, sb, sn = sources[row[1]]
                 rows.append((fsz.REQ_DECOMPRESS, 0, 0, 0, 0.0, sp, sb, sn))
             else:
-                rows.append((fsz.REQ_COMPRESS, 1, 1, n, rel, ptr, 0, 0))
+                _, k, off, n, rel = row
+                rows.append((fsz.REQ_COMPRESS, 1, 1, n, rel, pool[k].data_ptr() + 4 * off, 0, 0))
         cols = list(zip(*rows))
         for name, col in zip(("kind", "mode", "ndim", "d0", "eb", "d_in", "in_bytes", "n"), cols):
             t[name] = col

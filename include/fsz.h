@@ -323,8 +323,10 @@ fsz_status fsz_compress_noalloc(const float* d_in, fsz_dims dims, fsz_eb_mode mo
  *    is 0), in submission order: submitting requests ahead of their arrival times replays
  *    a trace without a client thread on the clock.
  *  - Admission: requests are admitted in arrival order while the device-memory budget
- *    allows. The budget counts the output memory the server allocates for the requests
- *    in flight (see fsz_server_request_cost), from admission to completion. A
+ *    allows. The budget counts the output memory the server allocates for a request (see
+ *    fsz_server_request_cost) from its admission until the client releases its output,
+ *    so the output memory the server holds never exceeds the budget: a client that keeps
+ *    outputs, or polls completions slowly, holds back admission. A
  *    request that can never fit (cost above the whole budget, or more elements than a
  *    batch may hold) completes at once with FSZ_ERR_REJECTED. A request that does not fit
  *    yet waits at the head of the queue; later requests do not overtake it.
@@ -342,9 +344,11 @@ fsz_status fsz_compress_noalloc(const float* d_in, fsz_dims dims, fsz_eb_mode mo
  *    (that field's device status), its output and its latency (arrival to completion on
  *    the host's monotonic clock).
  * Outputs live in one device allocation per batch, from a memory pool of the server's own.
- * Outputs that the client holds after completion are no longer charged to the budget.
- * An output stays valid until fsz_server_release; the batch's allocation is freed when all
- * its outputs are released. Every completion other than FSZ_ERR_REJECTED must be released.
+ * An output stays valid until fsz_server_release, which returns its cost to the budget;
+ * the batch's allocation is freed when all its outputs are released. Every completion other
+ * than FSZ_ERR_REJECTED must be released. Stopping (fsz_server_stop, fsz_server_destroy)
+ * refuses, with FSZ_ERR_REJECTED, requests still waiting for memory that only a release
+ * would return.
  * With sim_service_ns > 0 the server makes no CUDA call: a batch completes that long after
  * its launch, outputs are NULL (for testing the scheduling rules without a GPU). */
 typedef struct fsz_server_s* fsz_server;
@@ -407,8 +411,13 @@ fsz_status fsz_server_release(fsz_server s, uint64_t id, fsz_stream stream);
 fsz_status fsz_server_release_many(fsz_server s, const uint64_t* h_ids, uint64_t count,
                                    fsz_stream stream);
 fsz_status fsz_server_get_stats(fsz_server s, fsz_server_stats* h_stats);
-/* Finishes the queued and running work, then frees the server. Outputs not yet released
- * are freed with it. */
+/* Stops the server: no further submissions are accepted; queued and running work is
+ * finished, except requests that wait for memory only a release would return, which
+ * complete with FSZ_ERR_REJECTED. Completions stay available to fsz_server_poll until
+ * fsz_server_destroy (a polling thread can drain them first). Thread-safe; returns at once. */
+fsz_status fsz_server_stop(fsz_server s);
+/* fsz_server_stop, then waits for the scheduler to finish and frees the server. Outputs
+ * not yet released are freed with it. */
 fsz_status fsz_server_destroy(fsz_server s);
 /* Device-to-device copy on `stream` (for clients without a CUDA binding of their own). */
 fsz_status fsz_copy_device(void* d_dst, const void* d_src, uint64_t bytes, fsz_stream stream);

@@ -244,9 +244,8 @@ void fsz_server_s::finish(Slot& sl) {
     c.d_out = sl.arena->base ? static_cast<uint8_t*>(sl.arena->base) + sl.offs[i] : nullptr;
     c.out_bytes = sim ? 0 : (q.r.kind == FSZ_REQ_COMPRESS ? sl.h_sizes[i] : 4 * q.r.n);
     c.latency_ns = t > q.arrival ? t - q.arrival : 0;
-    held[q.r.id] = Held{sl.arena, q.cost};
+    held[q.r.id] = Held{sl.arena, q.cost};  // stays charged to the budget until released
     completions.push_back(c);
-    budget_free += q.cost;  // the request is no longer in flight
   }
   st.budget_free = budget_free;
   st.completed += k;
@@ -360,6 +359,23 @@ void fsz_server_s::run() {
     }
     bool progressed = complete();
     progressed |= launch();
+    if (stopping && inflight == 0 && !progressed && !pending.empty()) {
+      // Stopping with requests that wait for memory the client still holds: nothing in
+      // flight will return budget, so they are refused rather than waited for.
+      std::lock_guard<std::mutex> lk(mu);
+      const uint64_t t = now_ns();
+      for (const Req& q : pending) {
+        fsz_completion c{};
+        c.id = q.r.id;
+        c.status = FSZ_ERR_REJECTED;
+        c.batch = UINT64_MAX;
+        c.latency_ns = t > q.arrival ? t - q.arrival : 0;
+        completions.push_back(c);
+        st.rejected += 1;
+      }
+      pending.clear();
+      ready.notify_all();
+    }
     if (stopping && pending.empty() && inflight == 0) {
       std::lock_guard<std::mutex> lk(mu);
       if (arrivals.empty()) return;
@@ -490,10 +506,13 @@ fsz_status fsz_server_release_many(fsz_server s, const uint64_t* h_ids, uint64_t
         continue;
       }
       if (--it->second.arena->refs == 0) to_free.push_back(it->second.arena);
+      s->budget_free += it->second.cost;
       s->held.erase(it);
     }
+    s->st.budget_free = s->budget_free;
   }
   for (Arena* a : to_free) s->free_arena(a, reinterpret_cast<cudaStream_t>(stream));
+  s->wake.notify_one();  // memory returned: waiting requests may fit now
   return code;
 }
 
@@ -505,13 +524,19 @@ fsz_status fsz_server_get_stats(fsz_server s, fsz_server_stats* h_stats) {
   return FSZ_OK;
 }
 
-fsz_status fsz_server_destroy(fsz_server s) {
+fsz_status fsz_server_stop(fsz_server s) {
   if (s == nullptr) return FSZ_ERR_INVALID_ARG;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
   }
   s->wake.notify_all();
+  return FSZ_OK;
+}
+
+fsz_status fsz_server_destroy(fsz_server s) {
+  if (s == nullptr) return FSZ_ERR_INVALID_ARG;
+  fsz_server_stop(s);
   if (s->thread.joinable()) s->thread.join();
   std::vector<Arena*> arenas;
   for (auto& kv : s->held)

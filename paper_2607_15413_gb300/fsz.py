@@ -37,7 +37,7 @@ EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_byt
            "fsz_graph_compress_batched", "fsz_graph_decompress_batched", "fsz_graph_launch",
            "fsz_graph_destroy", "fsz_set_schedule", "fsz_get_schedule_limits",
            "fsz_server_request_cost", "fsz_server_create", "fsz_server_submit", "fsz_server_poll",
-           "fsz_server_submit_many", "fsz_server_release_many", "fsz_server_release", "fsz_server_get_stats", "fsz_server_destroy", "fsz_copy_device"]
+           "fsz_server_submit_many", "fsz_server_release_many", "fsz_server_release", "fsz_server_get_stats", "fsz_server_stop", "fsz_server_destroy", "fsz_copy_device"]
 REQ_COMPRESS, REQ_DECOMPRESS = 0, 1
 
 
@@ -205,6 +205,8 @@ def lib():
             L.fsz_server_release.restype = i32
             L.fsz_server_get_stats.argtypes = [P, P]
             L.fsz_server_get_stats.restype = i32
+            L.fsz_server_stop.argtypes = [P]
+            L.fsz_server_stop.restype = i32
             L.fsz_server_destroy.argtypes = [P]
             L.fsz_server_destroy.restype = i32
             L.fsz_copy_device.argtypes = [P, P, u64, P]

@@ -194,3 +194,48 @@ def make_field(spec, device: str = "cpu"):
     else:
         f = zero_slabs(dims, sd, device)
     return f.reshape(-1)
+
+
+# ----------------------------------------------------------------------------- serving mix
+
+SERVING_POOL_SHAPE = (256, 512, 512)
+
+
+def serving_pool(seed: int = 4, device: str = "cuda"):
+    """The serving workload's source fields (flat float32 tensors on the device): a k^-3
+    GRF, a particle-like array and the GRF's zero-slab/+280 variant, 2^26 elements each."""
+    g = grf(SERVING_POOL_SHAPE, seed=seed, device=device)
+    pool = [g.reshape(-1).contiguous(),
+            particles(g.numel(), seed=seed, device=device),
+            zero_slabs(SERVING_POOL_SHAPE, seed=seed, device=device, base=g).reshape(-1).contiguous()]
+    return pool
+
+
+def serving_windows(rng, pool_numels, count: int, min_elems: int = 4096,
+                    max_elems: int = 64 << 20):
+    """Request windows: (pool index, element offset, n, REL) with n log-uniform in
+    [min_elems, max_elems] (16 KiB - 256 MiB of float32), rounded down to a multiple of 4 and
+    to the field's size, at a uniformly drawn 16-byte-aligned offset; `rng` is a
+    random.Random."""
+    out = []
+    for _ in range(count):
+        k = rng.randrange(len(pool_numels))
+        size = int(pool_numels[k])
+        n = int(math.exp(rng.uniform(math.log(min_elems), math.log(max_elems))))
+        n = max(4, min(n, size) // 4 * 4)
+        off = rng.randrange(0, (size - n) // 4 + 1) * 4
+        out.append((k, off, n, rng.choice([1e-2, 1e-3, 1e-4])))
+    return out
+
+
+def serving_trace(rng, pool_numels, count: int, nsources: int, dec_share: float = 0.4):
+    """A request trace: each entry is ("compress", pool index, offset, n, REL) or
+    ("decompress", source index), the latter with probability `dec_share` when there are
+    `nsources` earlier streams to draw from."""
+    rows = []
+    for k, off, n, rel in serving_windows(rng, pool_numels, count):
+        if nsources and rng.random() < dec_share:
+            rows.append(("decompress", rng.randrange(nsources)))
+        else:
+            rows.append(("compress", k, off, n, rel))
+    return rows

@@ -127,11 +127,13 @@ class Server:
         return {k: getattr(st, k) for k, _ in fsz.FszServerStats._fields_}
 
     def close(self) -> None:
-        """Finishes the queued work, stops the poller and frees the server (and any output
+        """Finishes the queued work (requests still waiting for memory that only a release
+        would return are refused), stops the poller and frees the server (and any output
         not yet released)."""
         if self._h:
             with self._lock:
                 self._stop = True
+            self._L.fsz_server_stop(self._h)
             if self._poller is not None:
                 self._poller.join()
             self._L.fsz_server_destroy(self._h)

@@ -1,9 +1,10 @@
 """CUDA path vs the CPU oracle, through the C ABI (GB300 only).
 
 The bar is bit-exact: the compressed stream byte for byte, the decompressed floats
-bit for bit (the tolerance is 0). Small and ragged sizes are compared whole; the
-full-size workloads are compared on sampled tiles the oracle encodes one by one,
-and on every element through properties that hold at any size.
+bit for bit (the tolerance is 0). Small, ragged and full-size fields (the 512^3 fields
+at all three bounds, the 2^28-element particle array) are compared whole. The field past
+2^32 elements is compared on sampled tiles the oracle encodes one by one, and on every
+element through properties that hold at any size.
 """
 import numpy as np
 import pytest
@@ -320,20 +321,66 @@ def sampled_parity(fszlib, oracle, xd, rel, shape, nsample=48, seed=0):
     return nb
 
 
-@pytest.mark.parametrize("rel", [1e-2, 1e-3, 1e-4])
-def test_config2_grf_512cubed(fszlib, oracle, rel):
-    dev = _cuda()
-    f = inputs.grf((512, 512, 512), seed=1, device="cuda")
-    sampled_parity(fszlib, oracle, f.reshape(-1), rel, (512, 512, 512), seed=int(rel * 1e4))
-    z = inputs.zero_slabs((512, 512, 512), seed=1, device="cuda", base=f)
+def _first_diff(a: bytes, b: bytes) -> str:
+    if len(a) != len(b):
+        return f"lengths {len(a)} vs {len(b)}"
+    u, v = np.frombuffer(a, np.uint8), np.frombuffer(b, np.uint8)
+    k = int(np.nonzero(u != v)[0][0])
+    return f"first difference at byte {k} of {len(a)}"
+
+
+def _oracle_roundtrip(oracle, x, rel, shape):
+    ref = oracle.compress(x, rel, oracle.REL, dims=shape)
+    return ref, oracle.decompress(ref)
+
+
+def whole_parity(fszlib, oracle, xd, rels, shape):
+    """Full-size check: for each bound, the whole GPU stream against the oracle's stream byte
+    for byte, and the whole GPU reconstruction against the oracle decoder's bit for bit (the
+    oracle runs on host threads, one per bound, while the GPU works)."""
+    import concurrent.futures as cf
+    n = xd.numel()
+    x = xd.reshape(-1).cpu().numpy()
+    with cf.ThreadPoolExecutor(max_workers=len(rels)) as ex:
+        futs = {rel: ex.submit(_oracle_roundtrip, oracle, x, rel, shape) for rel in rels}
+        for rel in rels:
+            sb, nb = fszlib.compress(xd, rel, fszlib.EB_REL, shape=shape)
+            y = fszlib.decompress(sb, n=n)
+            got = sb.cpu().numpy().tobytes()
+            yg = y.cpu().numpy()
+            del sb, y
+            ref, yref = futs[rel].result()
+            assert got == ref, (rel, _first_diff(got, ref))
+            assert np.array_equal(yg.view(np.uint32), yref.view(np.uint32)), rel
+            p = oracle.params_for(x, oracle.REL, rel)
+            assert np.abs(x.astype(np.float64) - yg.astype(np.float64)).max() <= p.eb
+            del yg, yref
+
+
+def test_config2_grf_512cubed_whole_streams(fszlib, oracle):
+    _cuda()
+    shape = (512, 512, 512)
+    f = inputs.grf(shape, seed=1, device="cuda")
+    whole_parity(fszlib, oracle, f.reshape(-1), (1e-2, 1e-3, 1e-4), shape)
+    z = inputs.zero_slabs(shape, seed=1, device="cuda", base=f)
     del f
-    sampled_parity(fszlib, oracle, z.reshape(-1), rel, (512, 512, 512), seed=7)
+    whole_parity(fszlib, oracle, z.reshape(-1), (1e-2, 1e-3, 1e-4), shape)
 
 
-def test_config3_particles_2p28(fszlib, oracle):
+def test_config3_particles_2p28_whole_stream(fszlib, oracle):
     _cuda()
     x = inputs.particles(1 << 28, seed=2, device="cuda")
-    sampled_parity(fszlib, oracle, x, 1e-4, (1 << 28,), nsample=64)
+    whole_parity(fszlib, oracle, x, (1e-4,), (1 << 28,))
+
+
+@pytest.mark.parametrize("rel", [1e-2, 1e-4])
+def test_config2_sampled_tiles_and_properties(fszlib, oracle, rel):
+    """The same fields by the checks that hold at any size: every element by the
+    quantization property and the bound, sampled tile ranges against the oracle's tile
+    encoder where the GPU header places them."""
+    _cuda()
+    f = inputs.grf((512, 512, 512), seed=1, device="cuda")
+    sampled_parity(fszlib, oracle, f.reshape(-1), rel, (512, 512, 512), seed=int(rel * 1e4))
 
 
 def test_field_past_2p32_elements(fszlib, oracle):

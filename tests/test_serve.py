@@ -291,3 +291,30 @@ def test_bulk_submit_is_all_or_nothing_and_bulk_release_reports_unknown_ids():
     finally:
         srv.close()
     assert len(got) == 3 and st["completed"] == 3 and st["budget_free"] == 10 ** 9
+
+
+def test_held_outputs_stay_charged_until_released():
+    # A client that keeps its outputs holds back admission (the output memory the server
+    # holds never exceeds the budget); each release returns its request's cost; closing the
+    # server refuses what still waits for memory the client never gave back.
+    probe = Server(budget_bytes=1 << 30, sim_service_s=0.001)
+    c = cost(probe, 1000)
+    probe.close()
+    srv = Server(budget_bytes=2 * c, n_slots=4, max_batch=8, sim_service_s=0.005)
+    try:
+        first = [srv.submit(creq(1000)).result(timeout=5) for _ in range(2)]
+        assert all(r.status == 0 for r in first)
+        assert srv.stats()["budget_free"] == 0                 # both outputs still held
+        waiting = srv.submit(creq(1000))
+        time.sleep(0.05)
+        assert not waiting.done()                              # no memory until a release
+        first[0].release()
+        r = waiting.result(timeout=5)
+        assert r.status == 0
+        assert srv.stats()["budget_free"] == 0
+        stuck = srv.submit(creq(1000))                         # waits: nothing is released
+        time.sleep(0.05)
+        assert not stuck.done()
+    finally:
+        srv.close()
+    assert stuck.result(timeout=5).status == 10                # refused at close

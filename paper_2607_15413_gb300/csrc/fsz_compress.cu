@@ -1,54 +1,57 @@
 // FSZ single-pass compression kernel (Sec. 3.1 steps 1-5, Sec. 4).
 //
-// Persistent, warp-specialised CTAs (no CTA-wide barrier in the main loop; the roles
-// hand work to one another through mbarriers):
-//   producer warp  takes a ticket per chunk of kCChunkTiles tiles and stages the chunk
-//                  in shared memory, one half of kStageTiles tiles per 1-D TMA bulk copy;
-//   compute warps  (8) quantize, predict, evaluate the four variants, select and encode
-//                  two tiles at a time (16 elements per lane) from registers into the
-//                  warp's own ring buffer in shared memory, and write the tiles' rate
-//                  headers (steps 1-3 and 5; each tile is read from HBM once). The last
-//                  warp through a chunk scans its tile sizes and publishes the chunk's
-//                  aggregate flag;
-//   resolver warp  looks back for the chunk's exclusive byte offset (step 4, Sec. 4.4)
+// Persistent, warp-specialised CTAs; the roles hand work to one another through mbarriers
+// (no CTA-wide barrier in the main loop):
+//   ticket warp    takes a ticket per chunk of kCChunkTiles tiles (one quad of 4 tiles per
+//                  compute warp) just ahead of its use and leaves the chunk's parameters in
+//                  one of kSets chunk slots;
+//   compute warps  (kWarps) each stream their own quad of every chunk into a private
+//                  staging buffer with cp.async (16-byte pieces, zero-filled past the end of
+//                  the field), one chunk ahead of the one they encode. Lane L of a warp
+//                  holds block L & 7 of tile L >> 3 of its quad: 32 consecutive elements,
+//                  read from the buffer with conflict-free 128-bit loads (the pieces sit in
+//                  a 128-byte swizzled layout). They quantize, predict, evaluate the four
+//                  variants, select and size the quad's tiles (steps 1-3; the input is read
+//                  from HBM once), write the rate headers, and encode the quad as one
+//                  contiguous run into the warp's ring in shared memory (step 5). The last
+//                  warp to size a chunk scans the quads' sizes and publishes the chunk's
+//                  aggregate flag before any warp has encoded it;
+//   resolver warp  looks back for each chunk's exclusive byte offset (step 4, Sec. 4.4)
 //                  and publishes the inclusive prefix;
-//   compute warps  copy their tiles of each resolved chunk from the ring to the stream,
-//                  whenever one has resolved (between stages and while waiting for input);
-//                  they wait for an offset only when their ring is full.
-// The ring decouples encoding from the device-wide scan: chunks finish out of ticket order
+//   compute warps  copy their quad runs of resolved chunks from the ring to the stream
+//                  (one contiguous copy per warp and chunk), waiting for an offset only
+//                  when their ring lacks room for the next quad.
+// The rings decouple encoding from the device-wide scan: chunks finish out of ticket order
 // across the grid, and a chunk's offset is known only when every earlier chunk has
-// published its size, so the encoded bytes wait in shared memory meanwhile (about
-// kRingBytes / 250 B tiles per warp at the typical rate, at least one chunk at the worst).
+// published its size.
 #include "fsz_internal.cuh"
 
 namespace fsz {
 
 namespace {
 
-constexpr int kComputeWarps = 8;
-constexpr int kProducerWarp = kComputeWarps;
-constexpr int kResolverWarp = kComputeWarps + 1;
-constexpr int kThreads = (kComputeWarps + 2) * 32;
-constexpr int kStageTiles = 16;                    // tiles per TMA stage (half a chunk)
-constexpr int kStageElems = kStageTiles * kTile;
-constexpr int kStages = 2;                         // TMA input stages
-constexpr int kSets = 8;                           // chunks in flight per CTA
-constexpr int kCtasPerSm = 2;                      // 96 registers per thread
-constexpr int kRingBytes = 8192;                   // encoded-tile ring per compute warp
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr int kWarps = 8;                          // compute warps per CTA
+constexpr int kQuadTiles = 4;                      // tiles per compute warp and chunk
+constexpr int kTicketWarp = kWarps;
+constexpr int kResolverWarp = kWarps + 1;
+constexpr int kThreads = (kWarps + 2) * 32;
+constexpr int kSets = 8;                           // chunk slots per CTA
+constexpr int kCtasPerSm = 2;
+constexpr int kQuadElems = kQuadTiles * kTile;     // 1024
+constexpr int kQuadBytes = 4 * kQuadElems;         // 4096: a warp's staging buffer
+constexpr int kMaxQuadOut = kQuadTiles * kMaxTileBytes;
+constexpr int kRing = 4096;                        // logical ring bytes per compute warp
+constexpr int kRingAlloc = kRing + kMaxQuadOut;    // + room for a run that crosses the end
 constexpr int kLookbackPerLane = 4;                // lookback window: 128 flags
-constexpr int kTicketAhead = 2;                    // chunk tickets taken ahead of use
 constexpr uint32_t kNone = 0xffffffffu;
-static_assert(kCChunkTiles == 2 * kStageTiles, "a chunk is two stages");
-static_assert(kCChunkTiles <= 32, "one lane per tile in the chunk scan");
-static_assert(kRingBytes >= 3 * 2 * kMaxTileBytes,
-              "with only the current chunk's first pair live, a free pair gap exists");
-static_assert((kRingBytes & (kRingBytes - 1)) == 0, "ring counters wrap with the ring");
-static_assert(kStageTiles == 2 * kComputeWarps, "one pair per warp per stage");
-static_assert(kRingBytes <= 65536, "ring offsets are 16-bit");
-static_assert(kMaxTileBytes % 4 == 0, "tiles are 32-bit words");
+static_assert(kCChunkTiles == kWarps * kQuadTiles, "a chunk is one quad per compute warp");
+static_assert(kRing >= kMaxQuadOut, "a worst-case quad fits the ring");
+static_assert(kRingAlloc % 16 == 0 && kQuadBytes % 1024 == 0, "alignment of the buffers");
+static_assert(kWarps <= 32, "one lane per quad in the chunk scan");
 
-// A chunk's parameters, read once from the field record by the producer and kept in the
-// chunk's set until every compute warp has placed the chunk.
+// A chunk's parameters, read once from the field record by the ticket warp and kept in the
+// chunk's slot until every compute warp has placed the chunk.
 constexpr uint32_t kInfoOk = 1u, kInfoLast = 2u, kInfoFirst = 4u, kInfoSkip = 8u;
 struct ChunkInfo {
   const float* in;       // the chunk's first element
@@ -66,173 +69,234 @@ struct ChunkInfo {
   uint32_t off;          // the field's switched-off features (kOff* bits)
 };
 
-struct StageInfo {
-  uint32_t seq;   // the CTA's chunk sequence number of the staged chunk
-  uint32_t half;  // which half of it
-};
-
-struct __align__(16) CompressSmem {
-  float in[kStages][kStageElems];                 // TMA stages
-  uint8_t ring[kComputeWarps][kRingBytes];        // encoded tiles awaiting their offset
+struct __align__(1024) CompressSmem {
+  float stage[kWarps][kQuadElems];                // per-warp staging (swizzled pieces)
+  uint8_t ring[kWarps][kRingAlloc];               // encoded quads awaiting their offset
   ChunkInfo meta[kSets];
-  ChunkInfo pre[kTicketAhead];                    // producer's tickets taken ahead
-  uint64_t set_excl[kSets];
-  uint32_t toff[kSets][kCChunkTiles];             // tile offsets inside the chunk
-  uint32_t ring_mark[kComputeWarps][kSets];       // ring head after the warp's share
+  uint64_t set_excl[kSets];                       // a resolved chunk's exclusive offset
+  uint32_t qlen[kSets][kWarps];                   // each warp's quad run: bytes,
+  uint32_t qoff[kSets][kWarps];                   // ... offset inside the chunk,
+  uint32_t qpos[kSets][kWarps];                   // ... position in the warp's ring
   uint32_t set_tot[kSets];
   uint32_t done_cnt[kSets];
-  uint32_t tinfo[kSets][kCChunkTiles];            // ring offset << 16 | encoded size
-  StageInfo stage[kStages];
-  uint64_t full[kStages], empty[kStages], computed[kSets], resolved[kSets], setfree[kSets];
+  uint64_t info[kSets], computed[kSets], resolved[kSets], setfree[kSets], started[kSets];
 };
 
 // Eq. 3: S_b = 0 for r_b = 0, else 4 + 4 r_b.
-__device__ __forceinline__ uint32_t block_cost(int R) { return (uint32_t(R) + (R != 0 ? 1u : 0u)) << 2; }
+__device__ __forceinline__ uint32_t block_cost(int R) {
+  return (uint32_t(R) + (R != 0 ? 1u : 0u)) << 2;
+}
 
-// v = 2|l| + sign: bit 0 is the sign-map bit, bit k + 1 magnitude bit-plane k (Sec. 4.3).
-__device__ __forceinline__ uint32_t sign_mag(int l) { return (uabs32(l) << 1) | (uint32_t(l) >> 31); }
+// Bit length of x (Sec. 4.1.2: r_b = ceil(log2(max |l| + 1))).
+__device__ __forceinline__ int bitlen(uint32_t x) { return 32 - __clz(int(x)); }
 
-// The sign-magnitude word by multiply-adds: 2|l| + s = l (2 - 4s) + s with s the sign bit.
+// The sign-magnitude word v = 2|l| + sign by multiply-adds, l (2 - 4s) + s with s the sign
+// bit: bit 0 is the sign-map bit, bit k + 1 magnitude bit-plane k (Sec. 4.3).
 __device__ __forceinline__ uint32_t sign_mag_fma(int l) {
   const int sg = int(uint32_t(l) >> 31);
   return uint32_t(mad_s32(l, mad_s32(sg, -4, 2), sg));
 }
+__device__ __forceinline__ uint32_t sign_mag(int l) {
+  return (uabs32(l) << 1) | (uint32_t(l) >> 31);
+}
 
-// Loads lane hl = lane & 15's 16 elements (16 hl..16 hl + 15) of its half's tile from
-// the stage into registers, in element order.
-__device__ __forceinline__ void load_pair(const float* __restrict__ tile, const int lane,
-                                          float (&d)[16]) {
-  const int hl = lane & 15;
-  const float4* t4 = reinterpret_cast<const float4*>(tile) + 4 * hl;
-  // Load k of lane hl reads chunk (k + 2 (hl/2 mod 2)) mod 4 of its 64 bytes, so each
-  // 128-bit phase of 8 lanes hits every bank group twice rather than two of them four
-  // times; one select stage puts the chunks back in order.
-  const int rot = (hl >> 1) & 1;
-  float4 u[4], q[4];
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+// Copies the first `bytes` (0..16) of the piece and zero-fills the rest of it.
+__device__ __forceinline__ void cp_async16_fill(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+// Staging layout of a quad (4 KiB): the 16-byte piece at quad offset o sits at
+// o ^ (((o >> 7) & 7) << 4), so piece k of block g (128 bytes) lands in column k ^ g of the
+// block's row and the 8 lanes reading piece k of blocks 0..7 hit 8 different bank groups.
+//
+// Issues the cp.async pieces of this warp's quad of a chunk: lane L copies pieces
+// 32 j + L, j = 0..7 (each instruction of the warp reads 512 consecutive bytes). `qv` is
+// the quad's count of valid elements (1..1024); pieces past it are zero-filled and read
+// nothing beyond the field (their source operand is `safe`, the chunk's first element).
+__device__ __forceinline__ void issue_quad(uint32_t buf, const float* src, uint32_t qv, int lane,
+                                           const float* safe) {
+  // piece 32 j + L is at byte 512 j + 16 L; its block is (4 j + (L >> 3)) & 7
+  const uint32_t pe = uint32_t(16 * lane) ^ (uint32_t(lane >> 3) << 4);
+  const uint32_t po = pe ^ 64u;
+  const char* s = reinterpret_cast<const char*>(src) + 16 * lane;
+  if (qv == uint32_t(kQuadElems)) {
 #pragma unroll
-  for (int k = 0; k < 4; ++k) u[k] = t4[(k + 2 * rot) & 3];
+    for (int j = 0; j < 8; ++j) cp_async16(buf + 512 * j + ((j & 1) ? po : pe), s + 512 * j);
+  } else {
+    const uint32_t vb = 4 * qv;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) q[c] = rot ? u[(c + 2) & 3] : u[c];
+    for (int j = 0; j < 8; ++j) {
+      const uint32_t o = uint32_t(512 * j + 16 * lane);
+      const uint32_t nb = o >= vb ? 0u : min(16u, vb - o);
+      cp_async16_fill(buf + 512 * j + ((j & 1) ? po : pe),
+                      nb ? static_cast<const void*>(s + 512 * j) : static_cast<const void*>(safe), nb);
+    }
+  }
+  cp_async_commit();
+}
+
+// One byte-slice (bit-planes 8c .. 8c + 7) of a block's sign-magnitude words v[0..31] as the
+// 8 stream words of those planes (Sec. 4.3: element j at bit 31 - j, most significant byte
+// first, so stored little-endian element j sits at bit 8 (j >> 3) + 7 - (j & 7)).
+// X[k] gathers byte c of elements 7 - k, 15 - k, 23 - k, 31 - k: bit 8 m + i of X[k] is bit
+// i of element 8 m + 7 - k. Three delta swaps between register pairs (k, k ^ 2^t) exchange
+// bit t of the register index with bit t of the bit index i, after which register b holds
+// bit b of element 8 m + 7 - k at bit 8 m + k: the stream word of plane 8c + b.
+template <int c>
+__device__ __forceinline__ void planes8(const uint32_t (&v)[32], uint32_t (&X)[8]) {
+  constexpr uint32_t sel = uint32_t(c) | (uint32_t(4 + c) << 4);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    d[4 * k] = q[k].x; d[4 * k + 1] = q[k].y; d[4 * k + 2] = q[k].z; d[4 * k + 3] = q[k].w;
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t a = __byte_perm(v[7 - k], v[15 - k], sel);
+    const uint32_t b = __byte_perm(v[23 - k], v[31 - k], sel);
+    X[k] = __byte_perm(a, b, 0x5410);
+  }
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int s = 1 << t;
+    const uint32_t M = t == 0 ? 0x55555555u : (t == 1 ? 0x33333333u : 0x0F0F0F0Fu);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k & s) continue;
+      const uint32_t a = X[k], b = X[k | s];
+      // b keeps its bits whose index has bit t set and takes a's bits with it set, moved
+      // down; a keeps its bits with it clear and takes b's bits with it clear, moved up.
+      X[k | s] = (b & ~M) | ((a >> s) & M);
+      X[k] = (a & M) | (shl_fma(b, s) & ~M);
+    }
   }
 }
 
-// Compresses two tiles with one warp: lanes 0-15 take one tile and lanes 16-31 the next
-// (half = lane >> 4). Lane hl = lane & 15 holds elements 16 hl..16 hl + 15 of its tile in
-// d, so lanes 2g, 2g + 1 of a half own block g (Sec. 3.1: a tile is 8 blocks of 32
-// elements). The halves run in lockstep but each takes its own decisions (variant, rates).
-// `hdr` is this half's; the first half's bytes go to `slot`, the second half's right after
-// them. A half with `live` false computes but stores nothing. Returns this half's byte
-// count (uniform within the half). Switched-off features (kOff* bits) arrive as `restart`
-// (this lane starts from zero predecessors: the tile's first lane, and without the
-// cross-block state every block's first lane) and as penalties pen2, pen3 (2^16 for the
-// second-order and the centred variants when off), which raise a switched-off variant's
-// cost past any tile's so that it is never selected.
-// With kGiven the four tile costs come from `given` (this half's tile, stride gT between
-// variants) rather than from the costs computed here: the multipass evaluation's
-// encoding pass. They are equal, so the stream is the same.
+// Compresses one quad (4 tiles) with one warp. Lane L = 8 tq + g holds block g of tile tq
+// (elements 32 g .. 32 g + 31 of the tile) in d. `live`: the lane's tile exists. Writes the
+// tile's rate-header byte of block g to hdr (the quad's 32 header bytes are consecutive),
+// and returns this lane's block as (byte offset of its data inside the quad's run, word
+// count), with the quad's run length in *qlen; the words go to ring + offset by encode().
+// Switched-off features arrive as `restart` (this lane starts from zero predecessors: the
+// tile's first block, and every block without the cross-block state) and as penalties
+// pen2, pen3 (2^16 for the second-order and the centred variants when off). With kGiven
+// the four tile costs come from `given` (this lane's tile, stride gT between variants): the
+// multipass evaluation's encoding pass; they are equal, so the stream is the same.
+struct QuadPlan {
+  uint32_t v[32];   // sign-magnitude words of the selected variant
+  uint32_t off;     // byte offset of this lane's block data in the quad's run
+  int nw;           // the block's words (sign map + planes), 0 for rate 0 or a dead tile
+  uint32_t mu_off;  // byte offset of the tile's mean slot (lane g = 0 of a centred tile)
+  bool mu_slot;
+  int mu;
+  uint32_t qlen;    // the quad's run length (uniform)
+  int Rmax;         // largest live rate of the quad (uniform)
+};
+
 template <bool kGiven>
-__device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
-                                                  uint8_t* __restrict__ slot,
-                                                  uint8_t* __restrict__ hdr, const float r,
-                                                  const int lane, const bool live,
-                                                  const bool restart, const int pen2,
-                                                  const int pen3,
-                                                  const uint32_t* __restrict__ given,
-                                                  const uint64_t gT) {
-  constexpr uint32_t FULL = 0xffffffffu;
-  const int hl = lane & 15;
-  // Step 1, quantize (Sec. 4.2.2): t = fl(d r) then the nearest integer, ties to even.
-  // Y holds q + bits(M); differences of Y are differences of q.
-  int Y[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) Y[i] = __float_as_int(__fadd_rn(__fmul_rn(d[i], r), kMagic));
-
+__device__ __forceinline__ void plan_quad(const float (&d)[32], const float r, const int lane,
+                                          const bool live, const bool restart, const int pen2,
+                                          const int pen3, const uint32_t* __restrict__ given,
+                                          const uint64_t gT, uint8_t* __restrict__ hdr,
+                                          QuadPlan& P) {
+  const int g = lane & 7;
   // Tile sum for centring (Sec. 4.2.2, variant 3) in the fixed order: the sums of elements
-  // 8j..8j+7 left to right (two per lane: V0 for j even, V1 for j odd), then a butterfly
-  // over j by 16, 8, 4, 2 (lanes xor 8, 4, 2, 1 within the half) and finally by 1
-  // (V0 + V1). Float addition is commutative, so both partners of a step get equal sums.
-  float V0 = d[0], V1 = d[8];
+  // 8j..8j+7 left to right (four runs per lane: runs 4g .. 4g + 3), then a butterfly over
+  // the run index by 16, 8, 4 (lanes xor 4, 2, 1 within the tile's 8 lanes), 2 and 1
+  // (in-lane). Float addition is commutative, so both partners of a step get equal sums.
+  float R[4];
 #pragma unroll
-  for (int i = 1; i < 8; ++i) {
-    V0 = __fadd_rn(V0, d[i]);
-    V1 = __fadd_rn(V1, d[8 + i]);
+  for (int m = 0; m < 4; ++m) {
+    float acc = d[8 * m];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) acc = __fadd_rn(acc, d[8 * m + i]);
+    R[m] = acc;
   }
 #pragma unroll
-  for (int o = 8; o >= 1; o >>= 1) {
-    V0 = __fadd_rn(V0, __shfl_xor_sync(FULL, V0, o));
-    V1 = __fadd_rn(V1, __shfl_xor_sync(FULL, V1, o));
-  }
-  const float P = __fadd_rn(V0, V1);
+  for (int o = 4; o >= 1; o >>= 1)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) R[m] = __fadd_rn(R[m], __shfl_xor_sync(FULL, R[m], o));
+  const float S = __fadd_rn(__fadd_rn(R[0], R[2]), __fadd_rn(R[1], R[3]));
+
+  // Step 1, quantize (Sec. 4.2.2): t = fl(d r) then the nearest integer, ties to even. Y
+  // holds q + bits(M); differences of Y are differences of q.
+  int Y[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) Y[i] = __float_as_int(__fadd_rn(__fmul_rn(d[i], r), kMagic));
   const int mu =
-      __float_as_int(__fadd_rn(__fmul_rn(__fmul_rn(P, 0.00390625f), r), kMagic)) - kMagicBits;
+      __float_as_int(__fadd_rn(__fmul_rn(__fmul_rn(S, 0.00390625f), r), kMagic)) - kMagicBits;
 
-  // LZ1 residuals with the state carried across lane and block boundaries (Eq. 2); the
-  // tile's first predecessor is zero. LZ2 as the difference of LZ1 residuals:
+  // Residuals with the state carried across block boundaries (Eq. 2); the tile's first
+  // predecessors are zero. LZ2 as the difference of LZ1 residuals:
   // l2_i = (q_i - q_{i-1}) - (q_{i-1} - q_{i-2}).
-  int prevY = __shfl_up_sync(FULL, Y[15], 1, 16);
-  if (restart) prevY = kMagicBits;
-  int l1[16], l2[16];
-  l1[0] = Y[0] - prevY;
+  int prevY = __shfl_up_sync(FULL, Y[31], 1, 8);
+  int prevL = __shfl_up_sync(FULL, Y[31] - Y[30], 1, 8);
+  if (restart) {
+    prevY = kMagicBits;
+    prevL = 0;
+  }
+  const int l1_0 = Y[0] - prevY;
+  const int l2_0 = l1_0 - prevL;
+  const int l1_1 = Y[1] - Y[0];
+  const int l2_1 = l1_1 - l1_0;
+  // Block maxima as ORs (same bit length). rest* leave out the tile's first residual(s),
+  // the only ones centring changes (Eq. 4).
+  uint32_t rest1 = uabs32(l1_1), rest2 = 0;
+  int lp = l1_1;
 #pragma unroll
-  for (int i = 1; i < 16; ++i) l1[i] = Y[i] - Y[i - 1];
-  int prevL = __shfl_up_sync(FULL, l1[15], 1, 16);
-  if (restart) prevL = 0;
-  l2[0] = l1[0] - prevL;
-#pragma unroll
-  for (int i = 1; i < 16; ++i) l2[i] = l1[i] - l1[i - 1];
-
-  // Block maxima as ORs (same bit length); the block's two lanes combine by one shuffle.
-  // rest* leave out the tile's first residual(s), the only ones centring changes (Eq. 4).
-  uint32_t rest1 = 0, rest2 = 0;
-#pragma unroll
-  for (int i = 1; i < 16; ++i) rest1 |= uabs32(l1[i]);
-#pragma unroll
-  for (int i = 2; i < 16; ++i) rest2 |= uabs32(l2[i]);
-  const uint32_t o1 = rest1 | uabs32(l1[0]);
-  const uint32_t o2 = rest2 | uabs32(l2[0]) | uabs32(l2[1]);
-  const uint32_t x1 = __shfl_xor_sync(FULL, o1, 1);
-  const uint32_t y1 = __shfl_xor_sync(FULL, o2, 1);
-  // Rate r_b = bit length of the block maximum (Sec. 4.1.2).
-  const int R1 = 32 - __clz(int(o1 | x1));
-  const int R2 = 32 - __clz(int(o2 | y1));
-
-  // Centred block-0 rates (lane hl = 0): l1c_0 = q_0 - mu, l2c_0 = q_0 - mu,
+  for (int i = 2; i < 32; ++i) {
+    const int l1 = Y[i] - Y[i - 1];
+    rest1 |= uabs32(l1);
+    rest2 |= uabs32(l1 - lp);
+    lp = l1;
+  }
+  const int R1 = bitlen(rest1 | uabs32(l1_0));
+  const int R2 = bitlen(rest2 | uabs32(l2_0) | uabs32(l2_1));
+  // Centred block-0 rates (lane g = 0): l1c_0 = q_0 - mu, l2c_0 = q_0 - mu,
   // l2c_1 = q_1 - 2 q_0 + mu = l2_1 + mu; the rest of block 0 is unchanged (Eq. 4).
   const int q0 = Y[0] - kMagicBits;
   const uint32_t c10 = uabs32(q0 - mu);
-  const uint32_t c21 = uabs32(l2[1] + mu);
-  const int R1c = 32 - __clz(int(rest1 | x1 | c10));
-  const int R2c = 32 - __clz(int(rest2 | y1 | c10 | c21));
+  const uint32_t c21 = uabs32(l2_1 + mu);
+  const int R1c = bitlen(rest1 | c10);
+  const int R2c = bitlen(rest2 | c10 | c21);
 
-  // Block costs S_b (Eq. 3) of LZ1 and LZ2 as 16-bit halves. An inclusive scan over the
-  // 8 blocks (lanes 2 apart) gives every block's end offset for both variants; lane 15 of
-  // the half holds the tile costs C = sum of S_b. Centring changes block 0 only: its cost
-  // deltas and rates come from lane 0; variants 3 and 4 pay 4 bytes for mu (step 2).
-  const uint32_t pk = block_cost(R1) | (block_cost(R2) << 16);
-  uint32_t pinc = pk;
-  pinc = scan_step_up<16>(pinc, 2);
-  pinc = scan_step_up<16>(pinc, 4);
-  pinc = scan_step_up<16>(pinc, 8);
-  const uint32_t ptot = __shfl_sync(FULL, pinc, 15, 16);
-  int C1 = int(ptot & 0xffffu), C2 = int(ptot >> 16);
-  uint32_t bc = (block_cost(R1c) - block_cost(R1) + 1024u) |
-                ((block_cost(R2c) - block_cost(R2) + 1024u) << 11) | (uint32_t(R1c) << 22) |
-                (uint32_t(R2c) << 27);
-  bc = __shfl_sync(FULL, bc, 0, 16);
-  const int dC1 = int(bc & 0x7ffu) - 1024, dC2 = int((bc >> 11) & 0x7ffu) - 1024;
-  int C3 = 4 + C1 + dC1 + pen3;
-  int C4 = 4 + C2 + dC2 + pen2 + pen3;
+  // Tile costs (Eq. 3; variants 3 and 4 pay 4 bytes for mu): sums over the tile's 8 lanes
+  // of the block costs as 16-bit halves; centring changes block 0 only.
+  const uint32_t S1 = block_cost(R1), S2 = block_cost(R2);
+  uint32_t A = S1 | (S2 << 16);
+  uint32_t B = g == 0 ? (block_cost(R1c) | (block_cost(R2c) << 16)) : A;
+#pragma unroll
+  for (int o = 1; o <= 4; o <<= 1) {
+    A += __shfl_xor_sync(FULL, A, o);
+    B += __shfl_xor_sync(FULL, B, o);
+  }
+  int C1 = int(A & 0xffffu), C2 = int(A >> 16);
+  int C3 = 4 + int(B & 0xffffu) + pen3;
+  int C4 = 4 + int(B >> 16) + pen2 + pen3;
   if constexpr (kGiven) {
     C1 = int(given[0]);
     C2 = int(given[gT]);
     C3 = int(given[2 * gT]);
     C4 = int(given[3 * gT]);
   }
-  const int R1c0 = int((bc >> 22) & 31u), R2c0 = int(bc >> 27);
-
   // Step 3: first strict minimum in the order LZ1, LZ2, LZ1c, LZ2c.
   int v = 0, best = C1;
   if (C2 + pen2 < best) { v = 1; best = C2; }
@@ -240,76 +304,72 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
   if (C4 < best) { v = 3; best = C4; }
   const bool second = (v & 1) != 0, centred = v >= 2;
 
-  const int g = hl >> 1, t2 = hl & 1;
   int Rg = second ? R2 : R1;
-  if (g == 0 && centred) Rg = second ? R2c0 : R1c0;
+  if (g == 0 && centred) Rg = second ? R2c : R1c;
   // Rate header (Sec. 3.1): block 0 carries bit 7 = order 2, bit 6 = centred.
-  if (t2 == 0 && live) {
+  if (live) {
     uint32_t hb = uint32_t(Rg);
     if (g == 0) hb |= (second ? 0x80u : 0u) | (centred ? 0x40u : 0u);
-    hdr[g] = uint8_t(hb);
+    hdr[lane] = uint8_t(hb);
   }
 
-  // Step 5: residuals of the selected variant as sign-magnitude words v = 2|l| + sign,
-  // so that bit 0 is the sign map and bit k + 1 is magnitude bit-plane k (Sec. 4.3). The
-  // halves may select different variants: select per element rather than branch.
-  // The selected residual is l1_i + m l1_{i-1} with m = 0 (LZ1) or -1 (LZ2).
+  // Offsets: one scan over the quad's 32 blocks in stream order of the lane's bytes (its
+  // block's data, preceded in block 0 of a centred tile by the 4-byte mean).
+  const bool slot = live && centred && g == 0;
+  const uint32_t mine = live ? block_cost(Rg) + (slot ? 4u : 0u) : 0u;
+  uint32_t inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) inc = scan_step_up<32>(inc, o);
+  const uint32_t excl = inc - mine;
+  P.qlen = __shfl_sync(FULL, inc, 31);
+  P.mu_slot = slot;
+  P.mu_off = excl;
+  P.mu = mu;
+  P.off = excl + (slot ? 4u : 0u);
+  P.nw = live && Rg > 0 ? Rg + 1 : 0;
+  P.Rmax = int(__reduce_max_sync(FULL, live ? uint32_t(Rg) : 0u));
+
+  // Step 5: residuals of the selected variant as sign-magnitude words, in place over Y from
+  // the top (v_i needs Y_i, Y_{i-1}, Y_{i-2}). The selected residual is l1_i + m l1_{i-1}
+  // with m = 0 (LZ1) or -1 (LZ2).
   const int m = second ? -1 : 0;
-  uint32_t vv[16];
-  vv[0] = sign_mag_fma(mad_s32(prevL, m, l1[0]));
+  int up = Y[31] - Y[30];
 #pragma unroll
-  for (int i = 1; i < 16; ++i) vv[i] = sign_mag_fma(mad_s32(l1[i - 1], m, l1[i]));
-  const bool fix = centred && hl == 0;
-  vv[0] = fix ? sign_mag(q0 - mu) : vv[0];
-  vv[1] = (fix && second) ? sign_mag(l2[1] + mu) : vv[1];
-
-  // Byte offset of block g inside the tile's data: the variant's exclusive prefix; when
-  // centred, mu's 4 bytes come first and block 0's cost changes by its delta.
-  const uint32_t pexc = pinc - pk;
-  int off = int(second ? (pexc >> 16) : (pexc & 0xffffu));
-  if (centred) off += 4 + (g > 0 ? (second ? dC2 : dC1) : 0);
-  const uint32_t size_first = __shfl_sync(FULL, uint32_t(best), 0);
-  uint8_t* const my_slot = slot + (lane >= 16 ? size_first : 0u);
-  uint8_t* const blk = my_slot + off;
-  if (fix && live) *reinterpret_cast<float*>(my_slot) = __int2float_rn(mu);
-
-  const int nwords = live && Rg > 0 ? Rg + 1 : 0;  // block g's words: sign map + Rg planes
-  const int Rmax = int(__reduce_max_sync(FULL, live ? uint32_t(Rg) : 0u));
-  if (Rmax > 0) {
-    const int nch = (Rmax + 8) >> 3;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (c < nch) {
-        // Byte c of v_7..v_4 into lo, of v_3..v_0 into hi (element order reversed), so the
-        // 8x8 transpose leaves plane 8c + b in byte b with element i at bit 7 - i; the
-        // same for the lane's elements 8-15.
-        const uint32_t sel = uint32_t(c) | (uint32_t(4 + c) << 4);
-        uint32_t lo0 = __byte_perm(__byte_perm(vv[7], vv[6], sel), __byte_perm(vv[5], vv[4], sel), 0x5410);
-        uint32_t hi0 = __byte_perm(__byte_perm(vv[3], vv[2], sel), __byte_perm(vv[1], vv[0], sel), 0x5410);
-        uint32_t lo1 = __byte_perm(__byte_perm(vv[15], vv[14], sel), __byte_perm(vv[13], vv[12], sel), 0x5410);
-        uint32_t hi1 = __byte_perm(__byte_perm(vv[11], vv[10], sel), __byte_perm(vv[9], vv[8], sel), 0x5410);
-        transpose8x8(lo0, hi0);
-        transpose8x8(lo1, hi1);
-        // Lane t2 = 0 builds the words of planes 8c..8c+3, lane t2 = 1 those of 8c+4..8c+7;
-        // each needs the partner's bytes of those planes.
-        const uint32_t r0 = __shfl_xor_sync(FULL, t2 ? lo0 : hi0, 1);
-        const uint32_t r1 = __shfl_xor_sync(FULL, t2 ? lo1 : hi1, 1);
-        const uint32_t X0 = t2 ? r0 : lo0, X1 = t2 ? r1 : lo1;
-        const uint32_t Y0 = t2 ? hi0 : r0, Y1 = t2 ? hi1 : r1;
-        // word b = [X0.b, X1.b, Y0.b, Y1.b] in memory order: elements 0-7, 8-15, 16-23,
-        // 24-31, each byte with its first element in the top bit (Sec. 4.3)
-        const uint32_t u0 = __byte_perm(X0, X1, 0x5140), u1 = __byte_perm(X0, X1, 0x7362);
-        const uint32_t u2 = __byte_perm(Y0, Y1, 0x5140), u3 = __byte_perm(Y0, Y1, 0x7362);
-        const uint32_t w[4] = {__byte_perm(u0, u2, 0x5410), __byte_perm(u0, u2, 0x7632),
-                               __byte_perm(u1, u3, 0x5410), __byte_perm(u1, u3, 0x7632)};
-        const int wb = 8 * c + 4 * t2;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (wb + b < nwords) reinterpret_cast<uint32_t*>(blk)[wb + b] = w[b];
-      }
-    }
+  for (int i = 31; i >= 2; --i) {
+    const int dn = Y[i - 1] - Y[i - 2];
+    P.v[i] = sign_mag_fma(mad_s32(dn, m, up));
+    up = dn;
   }
-  return uint32_t(best);
+  P.v[1] = sign_mag_fma(mad_s32(l1_0, m, l1_1));
+  P.v[0] = sign_mag_fma(mad_s32(prevL, m, l1_0));
+  if (g == 0 && centred) {
+    P.v[0] = sign_mag(q0 - mu);
+    if (second) P.v[1] = sign_mag(l2_1 + mu);
+  }
+}
+
+// Writes this lane's block words (sign map, then bit-planes from the least significant) at
+// the shared-memory address blk, for the quad's byte-slices that any lane needs.
+__device__ __forceinline__ void encode_block(const QuadPlan& P, uint32_t blk) {
+  uint32_t X[8];
+  if (P.Rmax > 0) {
+    planes8<0>(P.v, X);
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      if (b < P.nw) sts32(blk + 4 * b, X[b]);
+  }
+  if (P.Rmax >= 8) {
+    planes8<1>(P.v, X);
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      if (8 + b < P.nw) sts32(blk + 32 + 4 * b, X[b]);
+  }
+  if (P.Rmax >= 16) {
+    planes8<2>(P.v, X);
+#pragma unroll
+    for (int b = 0; b < 8; ++b)
+      if (16 + b < P.nw) sts32(blk + 64 + 4 * b, X[b]);
+  }
 }
 
 // kGiven: the multipass evaluation's encoding pass (selection from a.given_costs).
@@ -317,7 +377,7 @@ __device__ __forceinline__ uint32_t compress_pair(const float (&d)[16],
 // with none of that handling.
 template <bool kGiven, bool kFeat>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(KernelArgs a) {
-  extern __shared__ __align__(128) uint8_t smem_raw[];
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
   CompressSmem& S = *reinterpret_cast<CompressSmem*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t total = a.ctrl->total_chunks;
@@ -326,37 +386,50 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
   const uint64_t wait_ns = 4 * a.timeout_ns;
 
   if (tid == 0) {
-    for (int k = 0; k < kStages; ++k) {
-      mbar_init(&S.full[k], 1);
-      mbar_init(&S.empty[k], kComputeWarps);
-    }
     for (int k = 0; k < kSets; ++k) {
+      mbar_init(&S.info[k], 1);
       mbar_init(&S.computed[k], 1);
       mbar_init(&S.resolved[k], 1);
-      mbar_init(&S.setfree[k], kComputeWarps);
+      mbar_init(&S.setfree[k], kWarps);
+      mbar_init(&S.started[k], 1);
       S.done_cnt[k] = 0;
     }
     fence_mbar_init();
   }
   __syncthreads();
 
-  if (warp == kProducerWarp) {
-    // ---------------------------------------------------------------- producer
-    // Tickets are taken two chunks ahead, so the ticket atomic and the field-record loads
-    // overlap the waits; a chunk's record goes to its set once the chunk kSets earlier has
-    // been placed by every compute warp, and each half goes out as soon as a stage frees.
+  if (warp == kTicketWarp) {
+    // ---------------------------------------------------------------- tickets
+    // The ticket of chunk seq is taken once the compute warps have begun chunk seq - 2 (so
+    // the chunk order across the grid stays close to the ticket order) and its slot is
+    // free (chunk seq - kSets placed by every compute warp).
     if (lane != 0) return;
     const bool single = a.ctrl->nfields == 1;
-    auto fetch = [&](ChunkInfo& ci) {
+    for (uint32_t seq = 0;; ++seq) {
+      const int b = int(seq % kSets);
+      if (seq >= 2 &&
+          !mbar_wait(&S.started[(seq - 2) % kSets], ((seq - 2) / kSets) & 1u, wait_ns)) {
+        set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      if (seq >= uint32_t(kSets) && !mbar_wait(&S.setfree[b], ((seq / kSets) - 1) & 1u, wait_ns)) {
+        set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      ChunkInfo& ci = S.meta[b];
       const uint32_t c = atomicAdd(&a.ctrl->ticket, 1u);
-      ci.chunk = c;
-      if (c >= total) return;
+      if (c >= total) {
+        ci.chunk = kNone;
+        mbar_arrive(&S.info[b]);
+        return;
+      }
       FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
       const uint64_t first = fi->chunk_first;
       const uint64_t lc = c - first;
       const uint64_t tile0 = lc * kCChunkTiles;
       const uint64_t e0 = tile0 * kTile;
       const uint64_t T = fi->T;
+      ci.chunk = c;
       ci.in = fi->in + e0;
       ci.out = fi->out;
       ci.fi = fi;
@@ -371,46 +444,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       ci.flags = (fi->s > 0.0f ? kInfoOk : 0u) |  // a field without a step has nothing to load
                  (lc + 1 == fi->nchunks ? kInfoLast : 0u) | (lc == 0 ? kInfoFirst : 0u) |
                  (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
-    };
-    for (int k = 0; k < kTicketAhead; ++k) fetch(S.pre[k]);
-    uint32_t u = 0;  // stage uses so far
-    auto take_stage = [&](uint32_t seq, uint32_t h) -> int {
-      const int s = int(u % kStages);
-      if (u >= uint32_t(kStages) && !mbar_wait(&S.empty[s], ((u / kStages) - 1) & 1u, wait_ns)) {
-        set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-        return -1;
-      }
-      S.stage[s].seq = seq;
-      S.stage[s].half = h;
-      ++u;
-      return s;
-    };
-    for (uint32_t seq = 0;; ++seq) {
-      const int b = int(seq % kSets);
-      if (seq >= uint32_t(kSets) && !mbar_wait(&S.setfree[b], ((seq / kSets) - 1) & 1u, wait_ns)) {
-        set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-        return;
-      }
-      ChunkInfo& q = S.pre[seq % kTicketAhead];
-      S.meta[b] = q;
-      if (q.chunk >= total) {
-        S.meta[b].chunk = kNone;
-        const int s = take_stage(seq, 0);
-        if (s >= 0) mbar_arrive(&S.full[s]);
-        return;
-      }
-      const uint32_t halves = q.ntiles > uint32_t(kStageTiles) ? 2u : 1u;
-      for (uint32_t h = 0; h < halves; ++h) {
-        const int s = take_stage(seq, h);
-        if (s < 0) return;
-        const uint32_t e_h = h * kStageElems;
-        const uint32_t valid = min(q.cnt - e_h, uint32_t(kStageElems));
-        const uint32_t bulk = (q.flags & kInfoOk) ? ((valid * 4) & ~15u) : 0u;
-        fence_proxy_async();
-        mbar_arrive_expect_tx(&S.full[s], bulk);
-        if (bulk) tma_load_1d(S.in[s], q.in + e_h, bulk, &S.full[s]);
-      }
-      fetch(q);  // the ticket kTicketAhead chunks ahead
+      mbar_arrive(&S.info[b]);
     }
   }
 
@@ -428,7 +462,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       const uint32_t c = ci.chunk;
       if (c == kNone) return;
       const uint32_t flags = ci.flags;
-      const uint32_t tot = S.set_tot[b];
       uint64_t excl = 0;
       if (!(flags & kInfoFirst)) {
         bool to = false;
@@ -436,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
                                           globaltimer_ns() + a.timeout_ns, &to);
         if (lane == 0) {
           if (to) set_error(a.ctrl, ci.fi, FSZ_ERR_TIMEOUT);
-          if (!(flags & kInfoSkip)) st_flag(a.flags + c, kFlagIncl | (excl + tot));
+          if (!(flags & kInfoSkip)) st_flag(a.flags + c, kFlagIncl | (excl + S.set_tot[b]));
         }
       }
       __syncwarp();
@@ -448,47 +481,43 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
   }
 
   // ------------------------------------------------------------------ compute warps
-  uint8_t* const ring = S.ring[warp];
-  uint32_t head = 0, tail = 0;  // ring byte counters (warp-uniform)
+  const uint32_t buf = smem_u32(S.stage[warp]);
+  const uint32_t ring_u32 = smem_u32(S.ring[warp]);
+  uint32_t head = 0, used = 0;  // ring state (warp-uniform): logical write position, bytes held
   uint32_t placed = 0;          // this CTA's chunks placed by this warp so far
-  uint32_t done = 0;            // ... encoded by this warp so far
+  uint32_t done = 0;            // ... sized and encoded by this warp so far
 
-  // Copies this warp's tiles of chunk `placed` (resolved) into the stream and frees them.
+  // Copies this warp's quad run of chunk `placed` (resolved) into the stream and frees it.
   auto place = [&]() {
     const int b = int(placed % kSets);
     const ChunkInfo& ci = S.meta[b];
+    const uint32_t len = S.qlen[b][warp];
     if ((ci.flags & (kInfoOk | kInfoSkip)) == kInfoOk) {
       const uint64_t excl = S.set_excl[b];
       const uint32_t tot = S.set_tot[b];
       if (ci.data_base + excl + tot > ci.cap) {
         if (lane == 0) set_error(a.ctrl, ci.fi, FSZ_ERR_CAPACITY);
       } else {
-        uint8_t* base = ci.out + ci.data_base + excl;
-        // the warp's pair of each stage: contiguous in the ring and in the stream
-        const int nt = int(ci.ntiles);
-        for (int t0 = 2 * warp; t0 < nt; t0 += kStageTiles) {
-          const uint32_t ti = S.tinfo[b][t0];
-          const uint32_t nw = ((ti & 0xffffu) + (t0 + 1 < nt ? (S.tinfo[b][t0 + 1] & 0xffffu) : 0u)) >> 2;
-          const uint32_t* src = reinterpret_cast<const uint32_t*>(ring + (ti >> 16));
-          uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.toff[b][t0]);
-          for (uint32_t q0 = 0; q0 < nw; q0 += 128) {  // 4 words per lane in flight
-            uint32_t v[4];
+        const uint32_t src = ring_u32 + S.qpos[b][warp];
+        uint32_t* dst = reinterpret_cast<uint32_t*>(ci.out + ci.data_base + excl + S.qoff[b][warp]);
+        const uint32_t nw = len >> 2;
+        for (uint32_t q0 = 0; q0 < nw; q0 += 128) {  // 4 words per lane in flight
+          uint32_t w[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const uint32_t q = q0 + 32 * u + lane;
-              if (q < nw) v[u] = src[q];
-            }
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t q = q0 + 32 * u + lane;
+            if (q < nw) w[u] = lds32(src + 4 * q);
+          }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const uint32_t q = q0 + 32 * u + lane;
-              if (q < nw) dst[q] = v[u];
-            }
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t q = q0 + 32 * u + lane;
+            if (q < nw) dst[q] = w[u];
           }
         }
         if (warp == 0 && lane == 0 && (ci.flags & kInfoLast)) write_preamble(ci.fi, excl + tot);
       }
     }
-    tail = S.ring_mark[warp][b];
+    used -= len;
     ++placed;
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.setfree[b]);
@@ -503,147 +532,147 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
     place();
     return true;
   };
-
-  bool ok_run = true;
-  for (uint32_t u = 0;; ++u) {
-    const int s = int(u % kStages);
-    const uint32_t par = (u / kStages) & 1u;
-    // Wait for the stage, placing resolved chunks meanwhile (the producer may be waiting
-    // for this warp to free a set). The stage is usually full already: one test, no timer.
-    if (!mbar_test(&S.full[s], par)) {
-      const uint64_t deadline = globaltimer_ns() + wait_ns;
-      bool got = false;
-      while (!got) {
-        if (placed < done) {
-          if (mbar_test(&S.resolved[placed % kSets], (placed / kSets) & 1u)) {
-            place();
-            continue;
-          }
-          got = mbar_try_wait_for(&S.full[s], par, 2000u);
-        } else {
-          got = mbar_try_wait_sleep(&S.full[s], par);
-        }
-        if (!got && globaltimer_ns() > deadline) break;
+  // Waits for chunk slot b's parameters (phase parity par), placing resolved chunks
+  // meanwhile: the ticket warp may be waiting for this warp to free a slot.
+  auto wait_info = [&](int b, uint32_t par) -> bool {
+    if (mbar_test(&S.info[b], par)) return true;
+    const uint64_t deadline = globaltimer_ns() + wait_ns;
+    for (;;) {
+      if (placed < done && mbar_test(&S.resolved[placed % kSets], (placed / kSets) & 1u)) {
+        place();
+        continue;
       }
-      if (!got) {
-        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-        ok_run = false;
-        break;
-      }
+      if (mbar_try_wait_for(&S.info[b], par, 2000u)) return true;
+      if (globaltimer_ns() > deadline) return false;
     }
-    const uint32_t seq = S.stage[s].seq, h = S.stage[s].half;
-    const int b = int(seq % kSets);
+  };
+  // The quad of chunk slot b that this warp loads: valid elements (0: nothing to load).
+  auto quad_valid = [&](const ChunkInfo& ci) -> uint32_t {
+    if (ci.chunk == kNone || !(ci.flags & kInfoOk)) return 0u;
+    const int e0 = kQuadElems * warp;
+    return ci.cnt > uint32_t(e0) ? min(ci.cnt - uint32_t(e0), uint32_t(kQuadElems)) : 0u;
+  };
+
+  bool ok_run = mbar_wait(&S.info[0], 0u, wait_ns);
+  if (!ok_run) {
+    if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+  } else {
+    const uint32_t qv0 = quad_valid(S.meta[0]);
+    if (qv0) issue_quad(buf, S.meta[0].in + kQuadElems * warp, qv0, lane, S.meta[0].in);
+  }
+  for (uint32_t u = 0; ok_run; ++u) {
+    const int b = int(u % kSets);
+    if (warp == 0 && lane == 0) mbar_arrive(&S.started[b]);  // step u begins
     const ChunkInfo& ci = S.meta[b];
     const uint32_t c = ci.chunk;
-    const uint32_t flags = ci.flags;
-    const int ntiles = int(ci.ntiles);
     const bool end = (c == kNone);
-    const bool last_half = end || (h + 1 == (ntiles > kStageTiles ? 2u : 1u));
-    bool released = false;
-    if (!end && (flags & kInfoOk)) {
-      const float r = ci.r;
-      const uint32_t e_h = h * kStageElems;
-      const uint32_t cnt = min(ci.cnt - e_h, uint32_t(kStageElems));
-      const uint32_t bulk_elems = ((cnt * 4) & ~15u) / 4;
-      const float* gin = ci.in + e_h;
-      uint8_t* hdr_out = ci.out + 64 + 8 * ci.tile0;
-      const int t_end = min(ntiles, int(h + 1) * kStageTiles);
-      const bool ragged = cnt < uint32_t(kStageElems);
-      const int ta = int(h) * kStageTiles + 2 * warp;  // this warp's pair in the stage
-      if (ta < t_end) {
-        const int half = lane >> 4;
-        const bool live = ta + half < t_end;
-        const int tl = live ? ta + half : ta;          // a missing second tile repeats the first
-        const int ts = tl - int(h) * kStageTiles;
-        float* tile = S.in[s] + ts * kTile;
-        // ragged end of a field: this lane's 16 elements past the bulk copy by plain loads
-        const uint32_t k0 = uint32_t(ts) * kTile + 16u * uint32_t(lane & 15);
-        if (ragged && live && k0 + 16 > bulk_elems) {
+    const uint32_t qv = quad_valid(ci);
+    const uint32_t flags = end ? 0u : ci.flags;
+    float d[32];
+    if (qv) {
+      cp_async_wait_all();
+      __syncwarp();
+      // lane L reads block g = L & 7 of tile L >> 3: piece k at column k ^ g of its row
+      const uint32_t row = buf + uint32_t(lane) * 128u;
+      const uint32_t base = row | (uint32_t(lane & 7) << 4);
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const uint32_t k = k0 + uint32_t(i);
-            if (k >= bulk_elems) tile[16 * (lane & 15) + i] = k < cnt ? gin[k] : 0.0f;
-          }
-        }
-        __syncwarp();
-        float d[16];
-        load_pair(tile, lane, d);
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.empty[s]);  // the pair is in registers
-        released = true;
-        // room for a worst-case pair, contiguous in the ring
-        constexpr uint32_t kPair = 2 * kMaxTileBytes;
-        uint32_t pos = head % kRingBytes;
-        uint32_t skip = pos + kPair > uint32_t(kRingBytes) ? kRingBytes - pos : 0u;
-        while (kRingBytes - (head - tail) < skip + kPair) {
-          if (placed == done || !place_oldest()) {  // cannot happen with <= one pair live
-            if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-            ok_run = false;
-            break;
-          }
-          pos = head % kRingBytes;
-          skip = pos + kPair > uint32_t(kRingBytes) ? kRingBytes - pos : 0u;
-        }
-        if (!ok_run) break;
-        head += skip;
-        pos = head % kRingBytes;
-        // switched-off features: zero predecessors for every block's first lane without
-        // the carried state; cost penalties for switched-off variants
-        const uint32_t foff = kFeat ? ci.off : 0u;
-        const bool restart = (lane & 15) == 0 || ((foff & kOffCross) && (lane & 1) == 0);
-        const int pen2 = (foff & kOffLz2) ? 0x10000 : 0;
-        const int pen3 = (foff & kOffCenter) ? 0x10000 : 0;
-        const uint32_t nb = compress_pair<kGiven>(d, ring + pos, hdr_out + 8 * tl, r, lane, live,
-                                                  restart, pen2, pen3,
-                                                  a.given_costs + ci.tile0 + tl, a.given_T);
-        const uint32_t na = __shfl_sync(0xffffffffu, nb, 0);
-        const uint32_t nbb = __shfl_sync(0xffffffffu, nb, 16);
-        const bool second_live = ta + 1 < t_end;
-        if (lane == 0) S.tinfo[b][ta] = (pos << 16) | na;
-        if (lane == 16 && second_live) S.tinfo[b][ta + 1] = ((pos + na) << 16) | nbb;
-        head += na + (second_live ? nbb : 0u);
+      for (int k = 0; k < 8; ++k) {
+        const float4 x = lds128(base ^ uint32_t(k << 4));
+        d[4 * k] = x.x; d[4 * k + 1] = x.y; d[4 * k + 2] = x.z; d[4 * k + 3] = x.w;
       }
-      if (!ok_run) break;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) d[i] = 0.0f;
     }
-    __syncwarp();
-    if (!end && !released && lane == 0) mbar_arrive(&S.empty[s]);  // done reading the stage
-    if (last_half) {
-      // This warp is through the chunk: the last warp to get here scans the chunk's tile
-      // sizes and publishes its aggregate (step 4, thread and warp levels).
+    // The next chunk's pieces go into the same buffer once every lane has its values.
+    if (!end) {
+      const int b1 = int((u + 1) % kSets);
+      if (!wait_info(b1, ((u + 1) / kSets) & 1u)) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        ok_run = false;
+      } else {
+        __syncwarp();  // every lane's loads of this buffer are done
+        const ChunkInfo& cn = S.meta[b1];
+        const uint32_t qv1 = quad_valid(cn);
+        if (qv1) issue_quad(buf, cn.in + kQuadElems * warp, qv1, lane, cn.in);
+      }
+    }
+    uint32_t qlen = 0;
+    QuadPlan P;
+    const int qt0 = kQuadTiles * warp;            // the quad's first tile in the chunk
+    const bool any = !end && (flags & kInfoOk) && qt0 < int(ci.ntiles);
+    if (any) {
+      const int t = qt0 + (lane >> 3);
+      const bool live = t < int(ci.ntiles);
+      const uint32_t foff = kFeat ? ci.off : 0u;
+      const bool restart = (lane & 7) == 0 || (foff & kOffCross);
+      const int pen2 = (foff & kOffLz2) ? 0x10000 : 0;
+      const int pen3 = (foff & kOffCenter) ? 0x10000 : 0;
+      uint8_t* hdr = ci.out + 64 + 8 * (ci.tile0 + uint64_t(qt0));
+      // (a lane of a missing tile reads the quad's first tile's given costs)
+      plan_quad<kGiven>(d, ci.r, lane, live, restart, pen2, pen3,
+                        a.given_costs + ci.tile0 + uint64_t(live ? t : qt0), a.given_T, hdr, P);
+      qlen = P.qlen;
+    }
+    if (!end) {
+      // sized: the last warp through the chunk scans the quads' sizes and publishes its
+      // aggregate (step 4, warp level), before the quads are encoded
+      if (lane == 0) S.qlen[b][warp] = qlen;
       uint32_t last = 0;
-      S.ring_mark[warp][b] = head;  // every lane (the same value): read by every lane
       if (lane == 0) {
         __threadfence_block();
-        last = atomicAdd(&S.done_cnt[b], 1u) == uint32_t(kComputeWarps - 1) ? 1u : 0u;
+        last = atomicAdd(&S.done_cnt[b], 1u) == uint32_t(kWarps - 1) ? 1u : 0u;
         __threadfence_block();
       }
-      last = __shfl_sync(0xffffffffu, last, 0);
-      __syncwarp();
+      last = __shfl_sync(FULL, last, 0);
       if (last) {
-        if (!end) {
-          const uint32_t mine = ((flags & kInfoOk) && lane < ntiles) ? (S.tinfo[b][lane] & 0xffffu) : 0u;
-          uint32_t inc = mine;
+        const uint32_t ql = lane < kWarps ? S.qlen[b][lane] : 0u;
+        uint32_t inc = ql;
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += x;
-          }
-          S.toff[b][lane] = inc - mine;
-          const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-          if (lane == 0) {
-            S.set_tot[b] = tot;
-            if (!(flags & kInfoSkip)) st_flag(a.flags + c, ((flags & kInfoFirst) ? kFlagIncl : kFlagAgg) | tot);
-          }
+        for (int o = 1; o < kWarps; o <<= 1) inc = scan_step_up<32>(inc, o);
+        if (lane < kWarps) S.qoff[b][lane] = inc - ql;
+        const uint32_t tot = __shfl_sync(FULL, inc, kWarps - 1);
+        if (lane == 0) {
+          S.set_tot[b] = tot;
+          S.done_cnt[b] = 0;
+          if (!(flags & kInfoSkip))
+            st_flag(a.flags + c, ((flags & kInfoFirst) ? kFlagIncl : kFlagAgg) | tot);
         }
         __syncwarp();
-        if (lane == 0) {
-          S.done_cnt[b] = 0;
-          mbar_arrive(&S.computed[b]);
+        if (lane == 0) mbar_arrive(&S.computed[b]);
+      }
+    } else {
+      // the end marker: the last warp here tells the resolver
+      uint32_t last = 0;
+      if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&S.done_cnt[b], 1u) == uint32_t(kWarps - 1) ? 1u : 0u;
+      }
+      last = __shfl_sync(FULL, last, 0);
+      if (last && lane == 0) mbar_arrive(&S.computed[b]);
+      break;
+    }
+    if (!ok_run) break;
+    if (any) {
+      // room for the run in the ring (logical bytes), placing older chunks as they resolve
+      while (kRing - used < qlen) {
+        if (placed == done || !place_oldest()) {  // cannot happen: a quad fits an empty ring
+          if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+          ok_run = false;
+          break;
         }
       }
-      if (end) break;
-      ++done;
+      if (!ok_run) break;
+      const uint32_t run = ring_u32 + head;
+      if (P.mu_slot) sts32(run + P.mu_off, __float_as_uint(__int2float_rn(P.mu)));
+      encode_block(P, run + P.off);
     }
+    if (lane == 0) S.qpos[b][warp] = head;
+    head += qlen;
+    if (head >= uint32_t(kRing)) head -= kRing;
+    used += qlen;
+    ++done;
+    __syncwarp();
     place_ready();
   }
   // Chunks encoded but not yet placed.
@@ -653,6 +682,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       break;
     }
   }
+  cp_async_wait_all();
 }
 
 }  // namespace

@@ -1,29 +1,28 @@
 // FSZ single-pass compression kernel (Sec. 3.1 steps 1-5, Sec. 4).
 //
-// Persistent, warp-specialised CTAs; the roles hand work to one another through mbarriers
-// (no CTA-wide barrier in the main loop):
-//   ticket warp    takes a ticket per chunk of kCChunkTiles tiles (one quad of 4 tiles per
-//                  compute warp) just ahead of its use and leaves the chunk's parameters in
-//                  one of kSets chunk slots;
-//   compute warps  (kWarps) each stream their own quad of every chunk into a private
-//                  staging buffer with cp.async (16-byte pieces, zero-filled past the end of
-//                  the field), one chunk ahead of the one they encode. Lane L of a warp
-//                  holds block L & 7 of tile L >> 3 of its quad: 32 consecutive elements,
-//                  read from the buffer with conflict-free 128-bit loads (the pieces sit in
-//                  a 128-byte swizzled layout). They quantize, predict, evaluate the four
-//                  variants, select and size the quad's tiles (steps 1-3; the input is read
-//                  from HBM once), write the rate headers, and encode the quad as one
-//                  contiguous run into the warp's ring in shared memory (step 5). The last
-//                  warp to size a chunk scans the quads' sizes and publishes the chunk's
-//                  aggregate flag before any warp has encoded it;
+// Persistent, warp-specialised CTAs (two per SM); the roles hand work to one another
+// through mbarriers and shared counters (no CTA-wide barrier in the main loop):
+//   compute warps  (kWarps) each stream their own quad (4 tiles) of every chunk into a
+//                  private staging buffer with cp.async (16-byte pieces, zero-filled past
+//                  the end of the field), one chunk ahead of the one they encode. Lane L of
+//                  a warp holds block L & 7 of tile L >> 3 of its quad: 32 consecutive
+//                  elements, read from the buffer with conflict-free 128-bit loads (the
+//                  pieces sit in a 128-byte swizzled layout). They quantize, predict,
+//                  evaluate the four variants, select and size the quad's tiles (steps 1-3;
+//                  the input is read from HBM once), write the rate headers, and encode the
+//                  quad as one contiguous run into the warp's ring in shared memory
+//                  (step 5). The last warp to size a chunk scans the quads' sizes and
+//                  publishes the chunk's aggregate flag before any warp has encoded it;
 //   resolver warp  looks back for each chunk's exclusive byte offset (step 4, Sec. 4.4)
 //                  and publishes the inclusive prefix;
-//   compute warps  copy their quad runs of resolved chunks from the ring to the stream
-//                  (one contiguous copy per warp and chunk), waiting for an offset only
-//                  when their ring lacks room for the next quad.
+//   host warp      takes a ticket per chunk just ahead of its use and leaves the chunk's
+//                  parameters in one of kSets chunk slots; and places each chunk, once it
+//                  is resolved and encoded, by copying the compute warps' runs from their
+//                  rings to the stream and giving the ring space back.
 // The rings decouple encoding from the device-wide scan: chunks finish out of ticket order
 // across the grid, and a chunk's offset is known only when every earlier chunk has
-// published its size.
+// published its size. Keeping the placement out of the compute warps keeps them within 96
+// registers, so that 16 of them fit on an SM.
 #include "fsz_internal.cuh"
 
 namespace fsz {
@@ -31,27 +30,59 @@ namespace fsz {
 namespace {
 
 constexpr uint32_t FULL = 0xffffffffu;
-constexpr int kWarps = 8;                          // compute warps per CTA
 constexpr int kQuadTiles = 4;                      // tiles per compute warp and chunk
-constexpr int kTicketWarp = kWarps;
+constexpr int kWarps = kCChunkTiles / kQuadTiles;  // compute warps per CTA
+constexpr int kHostWarp = kWarps;                  // tickets and placement
 constexpr int kResolverWarp = kWarps + 1;
 constexpr int kThreads = (kWarps + 2) * 32;
-constexpr int kSets = 8;                           // chunk slots per CTA
-constexpr int kCtasPerSm = 2;
+#ifndef FSZ_COMPRESS_SETS
+#define FSZ_COMPRESS_SETS 12
+#endif
+#ifndef FSZ_RING_BYTES
+#define FSZ_RING_BYTES 6144
+#endif
+constexpr int kSets = FSZ_COMPRESS_SETS;           // chunk slots per CTA
+#ifndef FSZ_TICKET_LEAD
+#define FSZ_TICKET_LEAD 2
+#endif
+// The ticket of chunk seq is taken when the compute warps begin chunk seq - kTicketLead.
+constexpr int kTicketLead = FSZ_TICKET_LEAD;
+static_assert(kTicketLead >= 1 && kTicketLead < FSZ_COMPRESS_SETS, "ticket lead");
+#ifndef FSZ_COMPRESS_CTAS
+#define FSZ_COMPRESS_CTAS 2
+#endif
+constexpr int kCtasPerSm = FSZ_COMPRESS_CTAS;
 constexpr int kQuadElems = kQuadTiles * kTile;     // 1024
 constexpr int kQuadBytes = 4 * kQuadElems;         // 4096: a warp's staging buffer
 constexpr int kMaxQuadOut = kQuadTiles * kMaxTileBytes;
-constexpr int kRing = 4096;                        // logical ring bytes per compute warp
+constexpr int kRing = FSZ_RING_BYTES;              // logical ring bytes per compute warp
 constexpr int kRingAlloc = kRing + kMaxQuadOut;    // + room for a run that crosses the end
-constexpr int kLookbackPerLane = 4;                // lookback window: 128 flags
+#ifndef FSZ_LOOKBACK_K
+#define FSZ_LOOKBACK_K 4
+#endif
+constexpr int kLookbackPerLane = FSZ_LOOKBACK_K;   // lookback window: 32 K flags
 constexpr uint32_t kNone = 0xffffffffu;
+// Polling intervals of waits that sleep between tests (ns): the host warp, the resolver
+// waiting for a chunk to be sized, the compute warps waiting for a ticket or ring space.
+#ifndef FSZ_HOST_SLEEP_NS
+#define FSZ_HOST_SLEEP_NS 100
+#endif
+#ifndef FSZ_RESOLVER_SLEEP_NS
+#define FSZ_RESOLVER_SLEEP_NS 200
+#endif
+#ifndef FSZ_COMPUTE_SLEEP_NS
+#define FSZ_COMPUTE_SLEEP_NS 100
+#endif
+constexpr uint32_t kHostSleepNs = FSZ_HOST_SLEEP_NS;
+constexpr uint32_t kResolverSleepNs = FSZ_RESOLVER_SLEEP_NS;
+constexpr uint32_t kComputeSleepNs = FSZ_COMPUTE_SLEEP_NS;
 static_assert(kCChunkTiles == kWarps * kQuadTiles, "a chunk is one quad per compute warp");
 static_assert(kRing >= kMaxQuadOut, "a worst-case quad fits the ring");
 static_assert(kRingAlloc % 16 == 0 && kQuadBytes % 1024 == 0, "alignment of the buffers");
 static_assert(kWarps <= 32, "one lane per quad in the chunk scan");
 
-// A chunk's parameters, read once from the field record by the ticket warp and kept in the
-// chunk's slot until every compute warp has placed the chunk.
+// A chunk's parameters, read once from the field record by the host warp and kept in the
+// chunk's slot until the chunk is placed.
 constexpr uint32_t kInfoOk = 1u, kInfoLast = 2u, kInfoFirst = 4u, kInfoSkip = 8u;
 struct ChunkInfo {
   const float* in;       // the chunk's first element
@@ -79,8 +110,11 @@ struct __align__(1024) CompressSmem {
   uint32_t qpos[kSets][kWarps];                   // ... position in the warp's ring
   uint32_t set_tot[kSets];
   uint32_t done_cnt[kSets];
-  uint64_t info[kSets], computed[kSets], resolved[kSets], setfree[kSets], started[kSets];
+  uint32_t ring_tail[kWarps];                     // ring bytes given back, per compute warp
+  uint64_t info[kSets], computed[kSets], encoded[kSets], resolved[kSets], started[kSets];
 };
+
+static_assert(sizeof(CompressSmem) <= 227 * 1024, "shared memory of one CTA");
 
 // Eq. 3: S_b = 0 for r_b = 0, else 4 + 4 r_b.
 __device__ __forceinline__ uint32_t block_cost(int R) {
@@ -117,6 +151,15 @@ __device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
 __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
   uint32_t v;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_cta(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_cta(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
   return v;
 }
 
@@ -259,15 +302,18 @@ __device__ __forceinline__ void plan_quad(const float (&d)[32], const float r, c
   const int l2_1 = l1_1 - l1_0;
   // Block maxima as ORs (same bit length). rest* leave out the tile's first residual(s),
   // the only ones centring changes (Eq. 4).
-  uint32_t rest1 = uabs32(l1_1), rest2 = 0;
+  // (four partial ORs each, so that the chains are short)
+  uint32_t o1[4] = {uabs32(l1_1), 0u, 0u, 0u}, o2[4] = {0u, 0u, 0u, 0u};
   int lp = l1_1;
 #pragma unroll
   for (int i = 2; i < 32; ++i) {
     const int l1 = Y[i] - Y[i - 1];
-    rest1 |= uabs32(l1);
-    rest2 |= uabs32(l1 - lp);
+    o1[i & 3] |= uabs32(l1);
+    o2[i & 3] |= uabs32(l1 - lp);
     lp = l1;
   }
+  const uint32_t rest1 = (o1[0] | o1[1]) | (o1[2] | o1[3]);
+  const uint32_t rest2 = (o2[0] | o2[1]) | (o2[2] | o2[3]);
   const int R1 = bitlen(rest1 | uabs32(l1_0));
   const int R2 = bitlen(rest2 | uabs32(l2_0) | uabs32(l2_1));
   // Centred block-0 rates (lane g = 0): l1c_0 = q_0 - mu, l2c_0 = q_0 - mu,
@@ -389,63 +435,127 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
     for (int k = 0; k < kSets; ++k) {
       mbar_init(&S.info[k], 1);
       mbar_init(&S.computed[k], 1);
+      mbar_init(&S.encoded[k], kWarps);
       mbar_init(&S.resolved[k], 1);
-      mbar_init(&S.setfree[k], kWarps);
       mbar_init(&S.started[k], 1);
       S.done_cnt[k] = 0;
     }
+    for (int w = 0; w < kWarps; ++w) S.ring_tail[w] = 0;
     fence_mbar_init();
   }
   __syncthreads();
 
-  if (warp == kTicketWarp) {
-    // ---------------------------------------------------------------- tickets
-    // The ticket of chunk seq is taken once the compute warps have begun chunk seq - 2 (so
-    // the chunk order across the grid stays close to the ticket order) and its slot is
-    // free (chunk seq - kSets placed by every compute warp).
-    if (lane != 0) return;
+  if (warp == kHostWarp) {
+    // ---------------------------------------------------------------- host
+    // Tickets and placement, polled in turn:
+    //  * the ticket of chunk seq is taken once the compute warps have begun chunk
+    //    seq - kTicketLead (so the chunk order across the grid stays close to the ticket
+    //    order) and its slot is free (chunk seq - kSets placed); lane 0 reads the field
+    //    record and leaves the chunk's parameters in the slot;
+    //  * chunk p is placed, in this CTA's order, once its offset is resolved and every
+    //    compute warp has encoded its quad: each warp's run is copied from its ring to the
+    //    stream and the ring space is given back.
     const bool single = a.ctrl->nfields == 1;
-    for (uint32_t seq = 0;; ++seq) {
-      const int b = int(seq % kSets);
-      if (seq >= 2 &&
-          !mbar_wait(&S.started[(seq - 2) % kSets], ((seq - 2) / kSets) & 1u, wait_ns)) {
-        set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-        return;
+    uint32_t seq_t = 0, p = 0, end_seq = kNone;
+    uint64_t deadline = globaltimer_ns() + wait_ns;
+    for (;;) {
+      bool progress = false;
+      if (end_seq == kNone && seq_t - p < uint32_t(kSets) &&
+          (seq_t < uint32_t(kTicketLead) ||
+           mbar_test(&S.started[(seq_t - kTicketLead) % kSets], ((seq_t - kTicketLead) / kSets) & 1u))) {
+        const int b = int(seq_t % kSets);
+        uint32_t c = 0;
+        if (lane == 0) {
+          ChunkInfo& ci = S.meta[b];
+          c = atomicAdd(&a.ctrl->ticket, 1u);
+          if (c >= total) {
+            ci.chunk = kNone;
+          } else {
+            FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
+            const uint64_t first = fi->chunk_first;
+            const uint64_t lc = c - first;
+            const uint64_t tile0 = lc * kCChunkTiles;
+            const uint64_t e0 = tile0 * kTile;
+            const uint64_t T = fi->T;
+            ci.chunk = c;
+            ci.in = fi->in + e0;
+            ci.out = fi->out;
+            ci.fi = fi;
+            ci.tile0 = tile0;
+            ci.data_base = 64 + 8 * T;
+            ci.cap = fi->cap;
+            ci.chunk_first = first;
+            ci.ntiles = uint32_t(min(uint64_t(kCChunkTiles), T - tile0));
+            ci.cnt = uint32_t(min(fi->n - e0, uint64_t(kCChunkElems)));
+            ci.r = fi->r;
+            ci.off = fi->features_off;
+            ci.flags = (fi->s > 0.0f ? kInfoOk : 0u) |  // a field without a step has nothing to load
+                       (lc + 1 == fi->nchunks ? kInfoLast : 0u) | (lc == 0 ? kInfoFirst : 0u) |
+                       (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
+          }
+          mbar_arrive(&S.info[b]);
+        }
+        c = __shfl_sync(FULL, c, 0);
+        if (c >= total) end_seq = seq_t;
+        ++seq_t;
+        progress = true;
       }
-      if (seq >= uint32_t(kSets) && !mbar_wait(&S.setfree[b], ((seq / kSets) - 1) & 1u, wait_ns)) {
-        set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-        return;
+      if (p < seq_t && p != end_seq) {
+        const int b = int(p % kSets);
+        const uint32_t par = (p / kSets) & 1u;
+        if (mbar_test(&S.resolved[b], par) && mbar_test(&S.encoded[b], par)) {
+          const ChunkInfo& ci = S.meta[b];
+          if ((ci.flags & (kInfoOk | kInfoSkip)) == kInfoOk) {
+            const uint64_t excl = S.set_excl[b];
+            const uint32_t tot = S.set_tot[b];
+            if (ci.data_base + excl + tot > ci.cap) {
+              if (lane == 0) set_error(a.ctrl, ci.fi, FSZ_ERR_CAPACITY);
+            } else {
+              uint8_t* const base = ci.out + ci.data_base + excl;
+              for (int w = 0; w < kWarps; ++w) {
+                const uint32_t nw = S.qlen[b][w] >> 2;
+                const uint32_t src = smem_u32(S.ring[w]) + S.qpos[b][w];
+                uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.qoff[b][w]);
+                for (uint32_t q0 = 0; q0 < nw; q0 += 128) {  // 4 words per lane in flight
+                  uint32_t v[4];
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) {
+                    const uint32_t q = q0 + 32 * k + lane;
+                    if (q < nw) v[k] = lds32(src + 4 * q);
+                  }
+#pragma unroll
+                  for (int k = 0; k < 4; ++k) {
+                    const uint32_t q = q0 + 32 * k + lane;
+                    if (q < nw) dst[q] = v[k];
+                  }
+                }
+              }
+              if (lane == 0 && (ci.flags & kInfoLast)) write_preamble(ci.fi, excl + tot);
+            }
+          }
+          // the runs are read: their ring space goes back to the compute warps
+          __syncwarp();
+          if (lane < kWarps) {
+            __threadfence_block();
+            st_release_cta(&S.ring_tail[lane], S.ring_tail[lane] + S.qlen[b][lane]);
+          }
+          __syncwarp();
+          ++p;
+          progress = true;
+        }
       }
-      ChunkInfo& ci = S.meta[b];
-      const uint32_t c = atomicAdd(&a.ctrl->ticket, 1u);
-      if (c >= total) {
-        ci.chunk = kNone;
-        mbar_arrive(&S.info[b]);
-        return;
+      if (end_seq != kNone && p == end_seq) break;
+      if (progress) {
+        deadline = globaltimer_ns() + wait_ns;
+      } else {
+        __nanosleep(kHostSleepNs);
+        if (globaltimer_ns() > deadline) {
+          if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+          break;
+        }
       }
-      FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
-      const uint64_t first = fi->chunk_first;
-      const uint64_t lc = c - first;
-      const uint64_t tile0 = lc * kCChunkTiles;
-      const uint64_t e0 = tile0 * kTile;
-      const uint64_t T = fi->T;
-      ci.chunk = c;
-      ci.in = fi->in + e0;
-      ci.out = fi->out;
-      ci.fi = fi;
-      ci.tile0 = tile0;
-      ci.data_base = 64 + 8 * T;
-      ci.cap = fi->cap;
-      ci.chunk_first = first;
-      ci.ntiles = uint32_t(min(uint64_t(kCChunkTiles), T - tile0));
-      ci.cnt = uint32_t(min(fi->n - e0, uint64_t(kCChunkElems)));
-      ci.r = fi->r;
-      ci.off = fi->features_off;
-      ci.flags = (fi->s > 0.0f ? kInfoOk : 0u) |  // a field without a step has nothing to load
-                 (lc + 1 == fi->nchunks ? kInfoLast : 0u) | (lc == 0 ? kInfoFirst : 0u) |
-                 (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
-      mbar_arrive(&S.info[b]);
     }
+    return;
   }
 
   if (warp == kResolverWarp) {
@@ -454,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
     // as the chunk's aggregate is out: the compute warps keep encoding meanwhile.
     for (uint32_t seq = 0;; ++seq) {
       const int b = int(seq % kSets);
-      if (!mbar_wait(&S.computed[b], (seq / kSets) & 1u, wait_ns)) {
+      if (!mbar_wait_idle(&S.computed[b], (seq / kSets) & 1u, wait_ns, kResolverSleepNs)) {
         if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
         return;
       }
@@ -469,7 +579,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
                                           globaltimer_ns() + a.timeout_ns, &to);
         if (lane == 0) {
           if (to) set_error(a.ctrl, ci.fi, FSZ_ERR_TIMEOUT);
-          if (!(flags & kInfoSkip)) st_flag(a.flags + c, kFlagIncl | (excl + S.set_tot[b]));
+          if (!(flags & kInfoSkip))
+            st_flag(a.flags + uint64_t(c) * kFlagStride, kFlagIncl | (excl + S.set_tot[b]));
         }
       }
       __syncwarp();
@@ -483,77 +594,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
   // ------------------------------------------------------------------ compute warps
   const uint32_t buf = smem_u32(S.stage[warp]);
   const uint32_t ring_u32 = smem_u32(S.ring[warp]);
-  uint32_t head = 0, used = 0;  // ring state (warp-uniform): logical write position, bytes held
-  uint32_t placed = 0;          // this CTA's chunks placed by this warp so far
-  uint32_t done = 0;            // ... sized and encoded by this warp so far
+  uint32_t head = 0;  // bytes this warp has written to its ring (warp-uniform, wrapping)
+  uint32_t pos = 0;   // ... its logical write position, head mod kRing
 
-  // Copies this warp's quad run of chunk `placed` (resolved) into the stream and frees it.
-  auto place = [&]() {
-    const int b = int(placed % kSets);
-    const ChunkInfo& ci = S.meta[b];
-    const uint32_t len = S.qlen[b][warp];
-    if ((ci.flags & (kInfoOk | kInfoSkip)) == kInfoOk) {
-      const uint64_t excl = S.set_excl[b];
-      const uint32_t tot = S.set_tot[b];
-      if (ci.data_base + excl + tot > ci.cap) {
-        if (lane == 0) set_error(a.ctrl, ci.fi, FSZ_ERR_CAPACITY);
-      } else {
-        const uint32_t src = ring_u32 + S.qpos[b][warp];
-        uint32_t* dst = reinterpret_cast<uint32_t*>(ci.out + ci.data_base + excl + S.qoff[b][warp]);
-        const uint32_t nw = len >> 2;
-        for (uint32_t q0 = 0; q0 < nw; q0 += 128) {  // 4 words per lane in flight
-          uint32_t w[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint32_t q = q0 + 32 * u + lane;
-            if (q < nw) w[u] = lds32(src + 4 * q);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint32_t q = q0 + 32 * u + lane;
-            if (q < nw) dst[q] = w[u];
-          }
-        }
-        if (warp == 0 && lane == 0 && (ci.flags & kInfoLast)) write_preamble(ci.fi, excl + tot);
-      }
-    }
-    used -= len;
-    ++placed;
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&S.setfree[b]);
-  };
-  // Places every chunk that has resolved, without waiting.
-  auto place_ready = [&]() {
-    while (placed < done && mbar_test(&S.resolved[placed % kSets], (placed / kSets) & 1u)) place();
-  };
-  // Places the oldest chunk, waiting for its offset.
-  auto place_oldest = [&]() -> bool {
-    if (!mbar_wait(&S.resolved[placed % kSets], (placed / kSets) & 1u, wait_ns)) return false;
-    place();
-    return true;
-  };
-  // Waits for chunk slot b's parameters (phase parity par), placing resolved chunks
-  // meanwhile: the ticket warp may be waiting for this warp to free a slot.
-  auto wait_info = [&](int b, uint32_t par) -> bool {
-    if (mbar_test(&S.info[b], par)) return true;
-    const uint64_t deadline = globaltimer_ns() + wait_ns;
-    for (;;) {
-      if (placed < done && mbar_test(&S.resolved[placed % kSets], (placed / kSets) & 1u)) {
-        place();
-        continue;
-      }
-      if (mbar_try_wait_for(&S.info[b], par, 2000u)) return true;
-      if (globaltimer_ns() > deadline) return false;
-    }
-  };
-  // The quad of chunk slot b that this warp loads: valid elements (0: nothing to load).
+  // The quad of a chunk that this warp loads: valid elements (0: nothing to load).
   auto quad_valid = [&](const ChunkInfo& ci) -> uint32_t {
     if (ci.chunk == kNone || !(ci.flags & kInfoOk)) return 0u;
     const int e0 = kQuadElems * warp;
     return ci.cnt > uint32_t(e0) ? min(ci.cnt - uint32_t(e0), uint32_t(kQuadElems)) : 0u;
   };
 
-  bool ok_run = mbar_wait(&S.info[0], 0u, wait_ns);
+  bool ok_run = mbar_wait_idle(&S.info[0], 0u, wait_ns, kComputeSleepNs);
   if (!ok_run) {
     if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
   } else {
@@ -584,19 +635,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
 #pragma unroll
       for (int i = 0; i < 32; ++i) d[i] = 0.0f;
     }
-    // The next chunk's pieces go into the same buffer once every lane has its values.
-    if (!end) {
-      const int b1 = int((u + 1) % kSets);
-      if (!wait_info(b1, ((u + 1) / kSets) & 1u)) {
-        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-        ok_run = false;
-      } else {
-        __syncwarp();  // every lane's loads of this buffer are done
-        const ChunkInfo& cn = S.meta[b1];
-        const uint32_t qv1 = quad_valid(cn);
-        if (qv1) issue_quad(buf, cn.in + kQuadElems * warp, qv1, lane, cn.in);
-      }
-    }
     uint32_t qlen = 0;
     QuadPlan P;
     const int qt0 = kQuadTiles * warp;            // the quad's first tile in the chunk
@@ -614,18 +652,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
                         a.given_costs + ci.tile0 + uint64_t(live ? t : qt0), a.given_T, hdr, P);
       qlen = P.qlen;
     }
-    if (!end) {
-      // sized: the last warp through the chunk scans the quads' sizes and publishes its
-      // aggregate (step 4, warp level), before the quads are encoded
-      if (lane == 0) S.qlen[b][warp] = qlen;
-      uint32_t last = 0;
-      if (lane == 0) {
-        __threadfence_block();
-        last = atomicAdd(&S.done_cnt[b], 1u) == uint32_t(kWarps - 1) ? 1u : 0u;
-        __threadfence_block();
-      }
-      last = __shfl_sync(FULL, last, 0);
-      if (last) {
+    // sized: the last warp through the chunk scans the quads' sizes and publishes its
+    // aggregate (step 4, warp level), before the quads are encoded; the end marker tells
+    // the resolver that the CTA's chunks have run out
+    if (lane == 0) S.qlen[b][warp] = qlen;
+    uint32_t last = 0;
+    if (lane == 0) {
+      __threadfence_block();
+      last = atomicAdd(&S.done_cnt[b], 1u) == uint32_t(kWarps - 1) ? 1u : 0u;
+      __threadfence_block();
+    }
+    last = __shfl_sync(FULL, last, 0);
+    if (last) {
+      if (!end) {
         const uint32_t ql = lane < kWarps ? S.qlen[b][lane] : 0u;
         uint32_t inc = ql;
 #pragma unroll
@@ -634,53 +673,54 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
         const uint32_t tot = __shfl_sync(FULL, inc, kWarps - 1);
         if (lane == 0) {
           S.set_tot[b] = tot;
-          S.done_cnt[b] = 0;
           if (!(flags & kInfoSkip))
-            st_flag(a.flags + c, ((flags & kInfoFirst) ? kFlagIncl : kFlagAgg) | tot);
+            st_flag(a.flags + uint64_t(c) * kFlagStride,
+                    ((flags & kInfoFirst) ? kFlagIncl : kFlagAgg) | tot);
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.computed[b]);
       }
-    } else {
-      // the end marker: the last warp here tells the resolver
-      uint32_t last = 0;
+      __syncwarp();
       if (lane == 0) {
-        __threadfence_block();
-        last = atomicAdd(&S.done_cnt[b], 1u) == uint32_t(kWarps - 1) ? 1u : 0u;
+        S.done_cnt[b] = 0;
+        mbar_arrive(&S.computed[b]);
       }
-      last = __shfl_sync(FULL, last, 0);
-      if (last && lane == 0) mbar_arrive(&S.computed[b]);
-      break;
     }
-    if (!ok_run) break;
-    if (any) {
-      // room for the run in the ring (logical bytes), placing older chunks as they resolve
-      while (kRing - used < qlen) {
-        if (placed == done || !place_oldest()) {  // cannot happen: a quad fits an empty ring
+    if (end) break;
+    // The next chunk's pieces go into the same buffer once every lane has its values.
+    {
+      const int b1 = int((u + 1) % kSets);
+      if (!mbar_wait_idle(&S.info[b1], ((u + 1) / kSets) & 1u, wait_ns, kComputeSleepNs)) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        ok_run = false;
+      } else {
+        __syncwarp();  // every lane's loads of this buffer are done
+        const ChunkInfo& cn = S.meta[b1];
+        const uint32_t qv1 = quad_valid(cn);
+        if (qv1) issue_quad(buf, cn.in + kQuadElems * warp, qv1, lane, cn.in);
+      }
+    }
+    // room for the run in the ring (logical bytes), given back by the host as it places
+    if (any && kRing - (head - ld_acquire_cta(&S.ring_tail[warp])) < qlen) {
+      const uint64_t deadline = globaltimer_ns() + wait_ns;
+      while (kRing - (head - ld_acquire_cta(&S.ring_tail[warp])) < qlen) {
+        __nanosleep(kComputeSleepNs);
+        if (globaltimer_ns() > deadline) {
           if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
           ok_run = false;
           break;
         }
       }
-      if (!ok_run) break;
-      const uint32_t run = ring_u32 + head;
+    }
+    if (any && ok_run) {
+      const uint32_t run = ring_u32 + pos;
       if (P.mu_slot) sts32(run + P.mu_off, __float_as_uint(__int2float_rn(P.mu)));
       encode_block(P, run + P.off);
     }
-    if (lane == 0) S.qpos[b][warp] = head;
+    if (lane == 0) S.qpos[b][warp] = pos;
     head += qlen;
-    if (head >= uint32_t(kRing)) head -= kRing;
-    used += qlen;
-    ++done;
+    pos += qlen;
+    if (pos >= uint32_t(kRing)) pos -= kRing;
     __syncwarp();
-    place_ready();
-  }
-  // Chunks encoded but not yet placed.
-  while (ok_run && placed < done) {
-    if (!place_oldest()) {
-      if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-      break;
-    }
+    if (lane == 0) mbar_arrive(&S.encoded[b]);  // this warp's run of the chunk is in its ring
   }
   cp_async_wait_all();
 }

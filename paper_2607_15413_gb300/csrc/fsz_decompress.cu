@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
       }
       const uint32_t tot = __shfl_sync(FULL, inc, 31);
       if (lane == 0) {
-        if (uint64_t(c) != a.skip_chunk) st_flag(a.flags + c, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
+        if (uint64_t(c) != a.skip_chunk) st_flag(a.flags + uint64_t(c) * kFlagStride, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
         q.chunk = c;
         q.lc = uint32_t(lc);
         q.last = (lc + 1 == fi->nchunks) ? 1u : 0u;
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
                                           globaltimer_ns() + a.timeout_ns, &to);
         if (lane == 0) {
           if (to) set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
-          if (!skip) st_flag(a.flags + c, kFlagIncl | (excl + tot));
+          if (!skip) st_flag(a.flags + uint64_t(c) * kFlagStride, kFlagIncl | (excl + tot));
         }
       }
       // The payload stage frees once the decode warps are through chunk seq - kStages.

@@ -21,10 +21,13 @@ constexpr int kMaxDecTileBytes = 1028;  // any header-valid tile: 8 * (4 + 4 * 3
 constexpr uint32_t kQmax = 174761;    // largest Q with (3Q + 4) 2^-23 <= 2^-4
 constexpr int kMinChunkTiles = 16;    // smallest chunk any kernel uses (workspace sizing)
 // Tiles per work item (one ticket, one lookback flag). Compression (and its value-range
-// pass, which shares the chunk -> field table) uses 32-tile chunks: fewer device-wide
-// scan links per byte. Decompression stages a chunk's whole payload at once, so its
-// chunks stay at 16 tiles.
-constexpr int kCChunkTiles = 32;
+// pass, which shares the chunk -> field table) uses chunks of one 4-tile quad per compute
+// warp of a CTA: 8 warps, 32 tiles. Decompression stages a chunk's whole payload at once,
+// so its chunks stay at 16 tiles.
+#ifndef FSZ_CCHUNK_TILES
+#define FSZ_CCHUNK_TILES 32
+#endif
+constexpr int kCChunkTiles = FSZ_CCHUNK_TILES;
 constexpr int kCChunkElems = kCChunkTiles * kTile;
 constexpr int kDChunkTiles = 16;
 constexpr int kDChunkElems = kDChunkTiles * kTile;
@@ -41,6 +44,11 @@ constexpr int kMagicBits = 0x4B400000;
 constexpr uint64_t kFlagAgg = uint64_t(1) << 62;   // local sum available
 constexpr uint64_t kFlagIncl = uint64_t(2) << 62;  // inclusive prefix available
 constexpr uint64_t kFlagValue = (uint64_t(1) << 62) - 1;
+// Words between consecutive chunks' flags in the workspace (1: packed).
+#ifndef FSZ_FLAG_STRIDE
+#define FSZ_FLAG_STRIDE 1
+#endif
+constexpr int kFlagStride = FSZ_FLAG_STRIDE;
 
 // Per-field state in the workspace: descriptor, value-range accumulators, derived step.
 struct alignas(16) FieldInfo {
@@ -110,8 +118,8 @@ inline WsLayout ws_layout(uint64_t tiles_upper, uint32_t nfields) {
   L.chunk_cap = (tiles_upper + kMinChunkTiles - 1) / kMinChunkTiles + nfields + 1;
   L.fields_off = 256;
   L.map_off = L.fields_off + uint64_t(nfields) * sizeof(FieldInfo);
-  L.flags_off = (L.map_off + 4 * L.chunk_cap + 15) & ~uint64_t(15);
-  L.bytes = L.flags_off + 8 * L.chunk_cap;
+  L.flags_off = (L.map_off + 4 * L.chunk_cap + 127) & ~uint64_t(127);
+  L.bytes = L.flags_off + 8 * kFlagStride * L.chunk_cap;
   return L;
 }
 
@@ -243,6 +251,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64
   }
 }
 
+// Waits for the phase of `bar` with the given parity, sleeping about sleep_ns between
+// tests: for warps with nothing else to do, so that their polling takes few issue slots
+// from the working warps of the SM. False if timeout_ns ran out first.
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity, uint64_t timeout_ns,
+                                               uint32_t sleep_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t deadline = globaltimer_ns() + timeout_ns;
+  for (;;) {
+    __nanosleep(sleep_ns);
+    if (mbar_test(bar, parity)) return true;
+    if (globaltimer_ns() > deadline) return false;
+  }
+}
+
 // 1-D TMA bulk copy global -> shared (16-byte aligned ends, size a multiple of 16).
 __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
@@ -350,6 +372,11 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 // Every spin is bounded by `deadline`; a wait that runs out reads as a zero inclusive
 // prefix and sets *timed_out (the caller records FSZ_ERR_TIMEOUT and still publishes, so
 // no successor waits forever).
+#ifndef FSZ_LOOKBACK_SLEEP_NS
+#define FSZ_LOOKBACK_SLEEP_NS 64
+#endif
+constexpr uint32_t kLookbackSleepNs = FSZ_LOOKBACK_SLEEP_NS;  // between polls of a window
+
 template <int K>
 __device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchunk, int64_t first,
                                              uint64_t deadline, bool* timed_out) {
@@ -380,7 +407,7 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchu
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int64_t idx = pos - (32 * k + lane);
-      take(k, idx >= first ? ld_flag(flags + idx) : kFlagIncl);  // before the field: 0
+      take(k, idx >= first ? ld_flag(flags + idx * kFlagStride) : kFlagIncl);  // before the field: 0
     }
     uint32_t d_incl;
     for (uint32_t spins = 0;; ++spins) {
@@ -396,11 +423,12 @@ __device__ __forceinline__ uint64_t lookback(const uint64_t* flags, int64_t gchu
           if (wait_mask & (1u << k)) take(k, kFlagIncl);
         continue;
       }
-      __nanosleep(64);
+      __nanosleep(kLookbackSleepNs);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const uint32_t d = uint32_t(32 * k + lane);
-        if ((wait_mask & (1u << k)) && d < d_incl) take(k, ld_flag(flags + (pos - int64_t(d))));
+        if ((wait_mask & (1u << k)) && d < d_incl)
+          take(k, ld_flag(flags + (pos - int64_t(d)) * kFlagStride));
       }
     }
     // Sum the aggregates nearer than the nearest inclusive prefix, then that prefix.

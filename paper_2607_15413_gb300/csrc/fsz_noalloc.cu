@@ -25,8 +25,8 @@ constexpr uint64_t kNoAllocMaxTiles = (kNoAllocMaxElems + kTile - 1) / kTile;
 constexpr uint64_t noalloc_scratch_bytes() {
   const uint64_t cap = (kNoAllocMaxTiles + kMinChunkTiles - 1) / kMinChunkTiles + 1 + 1;
   const uint64_t map_off = 256 + sizeof(FieldInfo);
-  const uint64_t flags_off = (map_off + 4 * cap + 15) & ~uint64_t(15);
-  return flags_off + 8 * cap;
+  const uint64_t flags_off = (map_off + 4 * cap + 127) & ~uint64_t(127);
+  return flags_off + 8 * kFlagStride * cap;
 }
 constexpr uint64_t kScratchBytes = (noalloc_scratch_bytes() + 255) & ~uint64_t(255);
 

@@ -162,6 +162,49 @@ def cpu_baseline_run(fields, elems=None):
             "seconds": dt}
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model name (lscpu / /proc/cpuinfo), or the machine type."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def cpu_all_core_run(fields, elems=None):
+    """The oracle's functions on every host core (element and tile ranges, one thread each,
+    a serial scan to place the ranges; the same streams as the single-threaded oracle):
+    compressing and decompressing the same sample as cpu_baseline_run."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    nbytes = 0
+    t0 = time.perf_counter()
+    for f in fields:
+        x = f if elems is None else f[:elems]
+        for rel in RELS:
+            s = oracle.mt_compress(x, rel, oracle.REL, nthreads=cores)
+            y = oracle.mt_decompress(s, nthreads=cores)
+            assert y.size == x.size
+            nbytes += 2 * x.nbytes
+    dt = time.perf_counter() - t0
+    return {"value": nbytes / dt / 1e9, "unit": "GB/s", "cores": cores, "seconds": dt,
+            "cpu_model": host_cpu_model(),
+            "how": "oracle tile functions over contiguous tile ranges, one thread per core, "
+                   "serial scan of the ranges' byte counts"}
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle as it stands, one host core. The 2^26-element
     sample is split across the warm-up and timed steps so any --steps/--warmup stays
@@ -713,7 +756,11 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and args.config is None:
-        cpu = cpu_baseline_run(cpu_sample_fields())   # on the host, before any GPU work
+        sample = cpu_sample_fields()
+        cpu = cpu_baseline_run(sample)   # on the host, before any GPU work
+        cpu["all_core"] = cpu_all_core_run(sample)
+        cpu["cpu_model"] = cpu["all_core"]["cpu_model"]
+        del sample
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)

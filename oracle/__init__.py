@@ -19,6 +19,10 @@ _SRC = os.path.join(_HERE, "fsz_oracle.cpp")
 _HDR = os.path.join(_HERE, "fsz_oracle.h")
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "libfsz_oracle.so")
+# All-core timing driver (the oracle's functions over element and tile ranges, one thread
+# per range; for the benchmark's CPU baseline only).
+_SRC_MT = os.path.join(_HERE, "fsz_oracle_mt.cpp")
+_LIB_MT = os.path.join(_LIBDIR, "libfsz_oracle_mt.so")
 
 ABS, REL = 0, 1
 LZ1, LZ2, LZ1C, LZ2C = 0, 1, 2, 3
@@ -39,14 +43,36 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle into oracle/_lib (idempotent)."""
+    """Compile the oracle (and its all-core timing driver) into oracle/_lib (idempotent)."""
     os.makedirs(_LIBDIR, exist_ok=True)
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.run(["g++", *CFLAGS, "-o", tmp, _SRC], check=True)
         os.replace(tmp, _LIB)
+    newest = max(newest, os.path.getmtime(_SRC_MT))
+    if force or not os.path.exists(_LIB_MT) or os.path.getmtime(_LIB_MT) < newest:
+        tmp = _LIB_MT + f".tmp{os.getpid()}"
+        subprocess.run(["g++", *CFLAGS, "-pthread", "-o", tmp, _SRC_MT, _SRC], check=True)
+        os.replace(tmp, _LIB_MT)
     return _LIB
+
+
+_lib_mt = None
+
+
+def lib_mt():
+    """The all-core timing driver (loaded on first use)."""
+    global _lib_mt
+    with _lock:
+        if _lib_mt is None:
+            build()
+            L = ctypes.CDLL(_LIB_MT)
+            P, u64, u32, f64 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_double
+            L.fszo_mt_compress.argtypes = [P, u32, P, ctypes.c_int, f64, P, u64, P, ctypes.c_int]
+            L.fszo_mt_decompress.argtypes = [P, u64, P, u64, P, ctypes.c_int]
+            _lib_mt = L
+    return _lib_mt
 
 
 class Params(ctypes.Structure):
@@ -309,3 +335,35 @@ def decompress_status(stream: bytes, cap: int | None = None) -> int:
     out = np.zeros(max(cap, 1), np.float32)
     nn = ctypes.c_uint64()
     return lib().fszo_decompress(_ptr(buf), len(stream), _ptr(out), cap, ctypes.byref(nn))
+
+
+def mt_compress(d: np.ndarray, eb: float, mode: int = REL, dims=None, nthreads: int = 0) -> bytes:
+    """The oracle's stream computed on `nthreads` host threads (all cores by default): the
+    same bytes as compress(); for timing the all-core CPU baseline."""
+    d = np.ascontiguousarray(d, dtype=np.float32)
+    if dims is None:
+        dims = d.shape if d.ndim >= 1 else (d.size,)
+    dims_arr = np.zeros(3, np.uint64)
+    dims_arr[: len(dims)] = dims
+    cap = compress_bound(d.size)
+    out = np.zeros(cap, np.uint8)
+    nb = ctypes.c_uint64()
+    st = lib_mt().fszo_mt_compress(_ptr(d), len(dims), _ptr(dims_arr), mode, eb, _ptr(out), cap,
+                                   ctypes.byref(nb), nthreads or (os.cpu_count() or 1))
+    if st != OK:
+        raise OracleError(st, "mt_compress")
+    return out[: nb.value].tobytes()
+
+
+def mt_decompress(stream: bytes, nthreads: int = 0) -> np.ndarray:
+    """decompress() on `nthreads` host threads (all cores by default); valid streams of the
+    default tile configuration."""
+    buf = np.frombuffer(stream, np.uint8)
+    n = read_preamble(stream)["n"]
+    out = np.zeros(max(n, 1), np.float32)
+    nn = ctypes.c_uint64()
+    st = lib_mt().fszo_mt_decompress(_ptr(buf), buf.size, _ptr(out), n, ctypes.byref(nn),
+                                     nthreads or (os.cpu_count() or 1))
+    if st != OK:
+        raise OracleError(st, "mt_decompress")
+    return out[:n]

@@ -414,6 +414,28 @@ int fszo_compress_tiles_f(const float* d, uint64_t n, float r, uint64_t t0, uint
   return FSZO_OK;
 }
 
+// Preamble (this project's addition; little-endian fields): magic, version, ndim, mode, n,
+// dims, requested eb, step s, method word (features switched off; 0: the full method),
+// data bytes.
+void fszo_write_preamble(uint8_t* out, uint32_t ndim, const uint64_t* dims, uint64_t n, int mode,
+                         double eb_req, float s, uint32_t method_word, uint64_t data_bytes) {
+  std::memset(out, 0, kPreamble);
+  out[0] = 'F'; out[1] = 'S'; out[2] = 'Z'; out[3] = '1';
+  put_u16(out + 4, 1);
+  out[6] = uint8_t(ndim);
+  out[7] = uint8_t(mode);
+  put_u64(out + 8, n);
+  for (uint32_t k = 0; k < 3; ++k) put_u64(out + 16 + 8 * k, k < ndim ? dims[k] : 0);
+  uint64_t ebits;
+  std::memcpy(&ebits, &eb_req, 8);
+  put_u64(out + 40, ebits);
+  uint32_t sbits;
+  std::memcpy(&sbits, &s, 4);
+  put_u32(out + 48, sbits);
+  put_u32(out + 52, method_word);
+  put_u64(out + 56, data_bytes);
+}
+
 int fszo_compress(const float* d, uint32_t ndim, const uint64_t* dims, int mode, double eb_req,
                   uint8_t* out, uint64_t out_capacity, uint64_t* out_bytes, int force_variant) {
   return fszo_compress_f(d, ndim, dims, mode, eb_req, 0, out, out_capacity, out_bytes,
@@ -456,22 +478,7 @@ int fszo_compress_f(const float* d, uint32_t ndim, const uint64_t* dims, int mod
   const uint64_t total = kPreamble + 8 * T + uint64_t(data.size());
   if (out_bytes) *out_bytes = total;
   if (total > out_capacity) return FSZO_ERR_CAPACITY;
-  // Preamble (this project's addition; little-endian fields).
-  std::memset(out, 0, kPreamble);
-  out[0] = 'F'; out[1] = 'S'; out[2] = 'Z'; out[3] = '1';
-  put_u16(out + 4, 1);
-  out[6] = uint8_t(ndim);
-  out[7] = uint8_t(mode);
-  put_u64(out + 8, n);
-  for (uint32_t k = 0; k < 3; ++k) put_u64(out + 16 + 8 * k, k < ndim ? dims[k] : 0);
-  uint64_t ebits;
-  std::memcpy(&ebits, &eb_req, 8);
-  put_u64(out + 40, ebits);
-  uint32_t sbits;
-  std::memcpy(&sbits, &p.s, 4);
-  put_u32(out + 48, sbits);
-  put_u32(out + 52, off);  // features switched off (0: the full method)
-  put_u64(out + 56, uint64_t(data.size()));
+  fszo_write_preamble(out, ndim, dims, n, mode, eb_req, p.s, off, uint64_t(data.size()));
   if (T) std::memcpy(out + kPreamble, header.data(), header.size());
   if (!data.empty()) std::memcpy(out + kPreamble + 8 * T, data.data(), data.size());
   return FSZO_OK;
@@ -767,6 +774,49 @@ int fszo_compress_cfg(const float* d, uint32_t ndim, const uint64_t* dims, int m
 
 namespace {
 
+// Decompression steps d4-d5 (Sec. 3.1 "Decompression") for one tile: its 8 header bytes h,
+// its data p (validated by the caller's scan of the header), writing its 256 integers q.
+int decode_tile(const uint8_t* h, const uint8_t* p, uint32_t feat_off, int32_t q[256]) {
+  int32_t l[kTile];
+  const bool second = (h[0] & 0x80) != 0;
+  const bool centred = (h[0] & 0x40) != 0;
+  int32_t mu = 0;
+  if (centred) {
+    uint32_t bits = get_u32(p); float muf; std::memcpy(&muf, &bits, 4);
+    // The mean slot must hold an integer of magnitude at most 2^24.
+    if (!(std::fabs(muf) <= 16777216.0f) || std::nearbyint(muf) != muf) return FSZO_ERR_CORRUPT;
+    mu = int32_t(muf);
+    p += 4;
+  }
+  // d4: decode and bit-unshuffle.
+  for (int b = 0; b < kBlocksPerTile; ++b) {
+    uint32_t rb = h[b] & 0x1F;
+    for (int j = 0; j < kBlock; ++j) l[b * kBlock + j] = 0;
+    if (rb == 0) continue;
+    uint32_t sign = get_word_be(p); p += 4;
+    uint32_t mag[kBlock] = {0};
+    for (uint32_t k = 0; k < rb; ++k) {
+      uint32_t w = get_word_be(p); p += 4;
+      for (int j = 0; j < kBlock; ++j)
+        if ((w >> (31 - j)) & 1u) mag[j] |= 1u << k;
+    }
+    for (int j = 0; j < kBlock; ++j) {
+      bool neg = (sign >> (31 - j)) & 1u;
+      l[b * kBlock + j] = neg ? int32_t(uint32_t(0) - mag[j]) : int32_t(mag[j]);
+    }
+  }
+  // d5: inverse prediction with the carried state, then + mu.
+  int32_t prev1 = 0, prev2 = 0;
+  for (int i = 0; i < kTile; ++i) {
+    if ((feat_off & FSZO_OFF_CROSS) && i % kBlock == 0) prev1 = prev2 = 0;  // independent blocks
+    int32_t qh = second ? wsub(wadd(l[i], wadd(prev1, prev1)), prev2) : wadd(l[i], prev1);
+    prev2 = prev1;
+    prev1 = qh;
+    q[i] = wadd(qh, mu);
+  }
+  return FSZO_OK;
+}
+
 // Decompression steps d1-d5 (Sec. 3.1 "Decompression"), writing the integers q.
 int decode_to_q(const uint8_t* in, uint64_t in_bytes, std::vector<int32_t>& qout, uint64_t cap,
                 uint64_t* n_out, float* s_out) {
@@ -801,46 +851,9 @@ int decode_to_q(const uint8_t* in, uint64_t in_bytes, std::vector<int32_t>& qout
   }
   if (off[T] != db) return FSZO_ERR_CORRUPT;
   qout.assign(size_t(T * kTile), 0);
-  int32_t l[kTile];
   for (uint64_t t = 0; t < T; ++t) {
-    const uint8_t* h = header + 8 * t;
-    const bool second = (h[0] & 0x80) != 0;
-    const bool centred = (h[0] & 0x40) != 0;
-    const uint8_t* p = data + off[t];
-    int32_t mu = 0;
-    if (centred) {
-      uint32_t bits = get_u32(p); float muf; std::memcpy(&muf, &bits, 4);
-      // The mean slot must hold an integer of magnitude at most 2^24.
-      if (!(std::fabs(muf) <= 16777216.0f) || std::nearbyint(muf) != muf) return FSZO_ERR_CORRUPT;
-      mu = int32_t(muf);
-      p += 4;
-    }
-    // d4: decode and bit-unshuffle.
-    for (int b = 0; b < kBlocksPerTile; ++b) {
-      uint32_t rb = h[b] & 0x1F;
-      for (int j = 0; j < kBlock; ++j) l[b * kBlock + j] = 0;
-      if (rb == 0) continue;
-      uint32_t sign = get_word_be(p); p += 4;
-      uint32_t mag[kBlock] = {0};
-      for (uint32_t k = 0; k < rb; ++k) {
-        uint32_t w = get_word_be(p); p += 4;
-        for (int j = 0; j < kBlock; ++j)
-          if ((w >> (31 - j)) & 1u) mag[j] |= 1u << k;
-      }
-      for (int j = 0; j < kBlock; ++j) {
-        bool neg = (sign >> (31 - j)) & 1u;
-        l[b * kBlock + j] = neg ? int32_t(uint32_t(0) - mag[j]) : int32_t(mag[j]);
-      }
-    }
-    // d5: inverse prediction with the carried state, then + mu.
-    int32_t prev1 = 0, prev2 = 0;
-    for (int i = 0; i < kTile; ++i) {
-      if ((feat_off & FSZO_OFF_CROSS) && i % kBlock == 0) prev1 = prev2 = 0;  // independent blocks
-      int32_t qh = second ? wsub(wadd(l[i], wadd(prev1, prev1)), prev2) : wadd(l[i], prev1);
-      prev2 = prev1;
-      prev1 = qh;
-      qout[size_t(t * kTile + uint64_t(i))] = wadd(qh, mu);
-    }
+    st = decode_tile(header + 8 * t, data + off[t], feat_off, qout.data() + t * kTile);
+    if (st != FSZO_OK) return st;
   }
   if (n_out) *n_out = n;
   if (s_out) *s_out = s;
@@ -884,6 +897,34 @@ int fszo_decompress_q(const uint8_t* in, uint64_t in_bytes, int32_t* q_out,
   if (st != FSZO_OK) return st;
   for (uint64_t i = 0; i < n; ++i) q_out[i] = q[size_t(i)];
   if (n_out) *n_out = n;
+  return FSZO_OK;
+}
+
+// Tiles [t0, t1) of a stream of the default tile configuration, the first of them starting
+// data_off bytes into the data region (the caller's scan of the header): their elements
+// [256 t0, min(n, 256 t1)) dequantized into out (indexed from element 256 t0).
+int fszo_decompress_tiles(const uint8_t* in, uint64_t in_bytes, uint64_t t0, uint64_t t1,
+                          uint64_t data_off, float* out) {
+  uint64_t n, db; uint32_t nd; uint64_t dims[3]; double eb; float s; uint32_t feat_off;
+  int st = fszo_read_preamble_f(in, in_bytes, &n, &nd, dims, &eb, &s, &db, &feat_off);
+  if (st != FSZO_OK) return st;
+  const uint64_t T = tiles_of(n);
+  if ((feat_off & 0xFF00u) || t1 < t0 || t1 > T || data_off > db) return FSZO_ERR_INVALID_ARG;
+  const uint8_t* header = in + kPreamble;
+  const uint8_t* p = header + 8 * T + data_off;
+  int32_t q[kTile];
+  for (uint64_t t = t0; t < t1; ++t) {
+    const uint8_t* h = header + 8 * t;
+    st = decode_tile(h, p, feat_off, q);
+    if (st != FSZO_OK) return st;
+    uint64_t bytes = (h[0] & 0x40) ? 4 : 0;
+    for (int b = 0; b < kBlocksPerTile; ++b) bytes += fszo_block_cost(h[b] & 0x1F);
+    p += bytes;
+    for (int i = 0; i < kTile; ++i) {
+      const uint64_t g = t * kTile + uint64_t(i);
+      if (g < n) out[g - t0 * kTile] = fszo_dequantize(q[i], s);
+    }
+  }
   return FSZO_OK;
 }
 

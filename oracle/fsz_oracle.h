@@ -145,6 +145,13 @@ typedef struct {
 int fszo_quality(const float* d, const float* y, uint64_t n, double eb, uint64_t stream_bytes,
                  fszo_quality_t* q);
 /* Whole-stream decompression (Sec. 3.1 "Decompression", steps d1-d5). */
+/* The 64-byte preamble of a stream (this project's addition). */
+void fszo_write_preamble(uint8_t* out, uint32_t ndim, const uint64_t* dims, uint64_t n, int mode,
+                         double eb_req, float s, uint32_t method_word, uint64_t data_bytes);
+/* Tiles [t0, t1) of a default-configuration stream whose first tile starts data_off bytes
+ * into the data region: elements [256 t0, min(n, 256 t1)) into out (from element 256 t0). */
+int fszo_decompress_tiles(const uint8_t* in, uint64_t in_bytes, uint64_t t0, uint64_t t1,
+                          uint64_t data_off, float* out);
 int fszo_decompress(const uint8_t* in, uint64_t in_bytes, float* out, uint64_t out_capacity_elems,
                     uint64_t* n_out);
 /* Same, but returns the reconstructed integers q instead of floats. */

@@ -521,3 +521,26 @@ def test_tile_mu_summation_order(oracle):
         x = inputs.grf((8, 8, 4), seed=seed).ravel() * np.float32(100.0) + np.float32(seed)
         p = oracle.params_for(x, oracle.REL, 1e-4)
         assert oracle.tile_mu(x, p.r) == _mu_np(x, p.r, "runs")
+
+
+# --------------------------------------------------------------------------- all-core timing driver
+
+@pytest.mark.parametrize("nthreads", [1, 3, 8])
+def test_all_core_driver_reproduces_the_oracle(oracle, nthreads):
+    # The all-core CPU baseline runs the oracle's functions over element and tile ranges;
+    # its streams and reconstructions must be the single-threaded oracle's, byte for byte.
+    cases = [(inputs.sinusoids(70001, seed=2), 1e-3, (70001,)),
+             (inputs.grf((24, 20, 30), seed=3), 1e-4, (24, 20, 30)),
+             (inputs.zero_slabs((10, 16, 40), seed=4), 1e-2, (10, 16, 40)),
+             (np.zeros(5, np.float32), 1e-3, (5,))]
+    for x, rel, dims in cases:
+        ref = oracle.compress(x.ravel(), rel, oracle.REL, dims=dims)
+        got = oracle.mt_compress(x.ravel(), rel, oracle.REL, dims=dims, nthreads=nthreads)
+        assert got == ref
+        y = oracle.mt_decompress(ref, nthreads=nthreads)
+        assert np.array_equal(y.view(np.uint32), oracle.decompress(ref).view(np.uint32))
+    bad = inputs.sinusoids(3000, seed=5)
+    bad[2999] = np.nan
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.mt_compress(bad, 1e-3, oracle.REL, nthreads=nthreads)
+    assert ei.value.status == oracle.ERR_NONFINITE

@@ -105,8 +105,9 @@ typedef struct {
 
 /* ------------------------------------------------------------------ sizes */
 
-/* Largest stream for n elements: 64 + 8 T + 708 T bytes, T = ceil(n / 256). A tile
- * costs at most 8 * (4 + 4 * 21) + 4 bytes because |q| stays below 2^18 (Sec. 4.2.2 Eq. 3). */
+/* Largest stream for n elements: 64 + 8 T + 772 T bytes, T = ceil(n / 256). A tile
+ * costs at most 8 * (4 + 4 * 23) + 4 bytes because |q| stays below 2^21, so every residual
+ * stays below 2^23 (Sec. 4.2.2, Eq. 3). */
 uint64_t fsz_compress_bound(uint64_t n);
 
 /* Workspace for fsz_compress / fsz_decompress of up to n elements. */

@@ -274,7 +274,7 @@ def compress_tiles(d: np.ndarray, r: float, t0: int, t1: int, features_off: int 
     """Headers (8 bytes per tile) and data of tiles [t0, t1) of field d, given r = 1/s."""
     d = np.ascontiguousarray(d, dtype=np.float32).ravel()
     hdr = np.zeros(8 * max(t1 - t0, 1), np.uint8)
-    cap = 708 * max(t1 - t0, 1)
+    cap = 772 * max(t1 - t0, 1)
     data = np.zeros(cap, np.uint8)
     nb = ctypes.c_uint64()
     st = lib().fszo_compress_tiles_f(_ptr(d), d.size, r, t0, t1, features_off, _ptr(hdr),

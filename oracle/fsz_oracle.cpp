@@ -17,7 +17,10 @@ constexpr int kTile = 256;        // Sec. 3.1: a tile is 8 blocks of 32 elements
 constexpr int kBlock = 32;
 constexpr int kBlocksPerTile = 8;
 constexpr uint64_t kPreamble = 64; // the 64-byte preamble is this project's addition
-constexpr uint32_t kQmax = 174761; // largest Q with (3Q + 4) 2^-23 <= 2^-4
+// The margin eps = (3Q + 4) 2^-23 of reading R2 is capped at 2^-4 (first tier); a field
+// that needs more takes the second tier, capped at 2^-1. Q bounds |q|.
+constexpr uint32_t kQmax1 = 174761;   // largest Q with (3Q + 4) 2^-23 <= 2^-4
+constexpr uint32_t kQmax2 = 1398100;  // largest Q with (3Q + 4) 2^-23 <= 2^-1
 constexpr uint64_t kMaxElems = uint64_t(1) << 40;
 
 uint64_t tiles_of(uint64_t n) { return (n + kTile - 1) / kTile; }
@@ -95,6 +98,9 @@ int fszo_stats(const float* d, uint64_t n, float* vmin, float* vmax, int* all_fi
 //    quantizer and the reconstruction each round, so the half step e is shrunk by
 //    a margin eps that covers both roundings for |q| <= Q, with Q bounded from the
 //    field's max |d| (A). e is rounded toward zero to float32, s = 2e, r = fl(1/s).
+//  * eps = (3Q + 4) 2^-23 is capped at 2^-4, Q = ceil(A / (2 eb (1 - 2^-4))) + 1; a field
+//    beyond that cap takes a second tier, Q = ceil(A / (2 eb (1 - 2^-1))) + 1 with eps
+//    capped at 2^-1 (a finer step: a field the first tier accepts keeps its stream).
 int fszo_params(int mode, double eb_req, float vmin, float vmax, int all_finite, uint64_t n,
                 fszo_params_t* p) {
   if (!(eb_req > 0.0) || !std::isfinite(eb_req)) return FSZO_ERR_INVALID_ARG;
@@ -115,11 +121,19 @@ int fszo_params(int mode, double eb_req, float vmin, float vmax, int all_finite,
   const double two100 = std::ldexp(1.0, 100);
   double eb_eff = eb < two100 ? eb : two100;
   double A = std::fmax(std::fabs(double(vmin)), std::fabs(double(vmax)));
-  double denom = 2.0 * eb_eff * (1.0 - 0.0625);
-  double K = A / denom;
-  if (!(K <= double(kQmax))) return FSZO_ERR_EB_TOO_SMALL;
-  uint32_t Q = uint32_t(std::ceil(K)) + 1u;
-  if (Q > kQmax) return FSZO_ERR_EB_TOO_SMALL;
+  // First tier: K = A / (2 eb (1 - 2^-4)) bounds A / (2e) whenever eps <= 2^-4.
+  double K = A / (2.0 * eb_eff * (1.0 - 0.0625));
+  uint32_t Q = 0;
+  if (K <= double(kQmax1) && uint32_t(std::ceil(K)) + 1u <= kQmax1) {
+    Q = uint32_t(std::ceil(K)) + 1u;
+  } else {
+    // Second tier, for fields the first refuses: K = A / (2 eb (1 - 2^-1)) bounds A / (2e)
+    // whenever eps <= 2^-1 (a step up to half the first tier's).
+    K = A / (2.0 * eb_eff * (1.0 - 0.5));
+    if (!(K <= double(kQmax2))) return FSZO_ERR_EB_TOO_SMALL;
+    Q = uint32_t(std::ceil(K)) + 1u;
+    if (Q > kQmax2) return FSZO_ERR_EB_TOO_SMALL;
+  }
   double eps = double(3u * Q + 4u) * std::ldexp(1.0, -23);
   double x = eb_eff * (1.0 - eps);
   float e = float(x);
@@ -326,7 +340,7 @@ int fszo_features_valid(uint32_t off) {
 
 uint64_t fszo_compress_bound(uint64_t n) {
   uint64_t T = tiles_of(n);
-  return kPreamble + 8 * T + 708 * T;
+  return kPreamble + 8 * T + 772 * T;
 }
 
 }  // extern "C"
@@ -717,7 +731,7 @@ extern "C" {
 
 uint64_t fszo_compress_bound_cfg(uint64_t n, int B, int T) {
   const uint64_t NT = (n + uint64_t(B * T) - 1) / uint64_t(B * T);
-  return kPreamble + uint64_t(T) * NT + (uint64_t(T) * uint64_t(B / 8) * 22 + 4) * NT;
+  return kPreamble + uint64_t(T) * NT + (uint64_t(T) * uint64_t(B / 8) * 24 + 4) * NT;
 }
 
 int fszo_compress_cfg(const float* d, uint32_t ndim, const uint64_t* dims, int mode, double eb_req,

@@ -83,7 +83,7 @@ void fszo_tile_costs_four_pass(const int32_t q[256], int32_t mu, uint32_t C[4], 
 /* First strict minimum in listed order (Sec. 4.2.2: "selects the variant with the minimum C"). */
 int fszo_select(const uint32_t C[4]);
 
-/* Worst-case stream size for n elements: 64 + 8T + 708T bytes. */
+/* Worst-case stream size for n elements: 64 + 8T + 772T bytes (rates stay <= 23). */
 uint64_t fszo_compress_bound(uint64_t n);
 
 /* Whole-field compression. force_variant = -1 selects per tile (the method);

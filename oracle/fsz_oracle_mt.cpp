@@ -18,7 +18,7 @@
 namespace {
 
 constexpr uint64_t kTile = 256;
-constexpr uint64_t kMaxTileBytes = 708;
+constexpr uint64_t kMaxTileBytes = 772;
 
 template <typename F>
 void parallel_ranges(uint64_t count, int nthreads, F&& body) {

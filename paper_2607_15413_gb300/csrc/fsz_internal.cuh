@@ -16,9 +16,13 @@
 namespace fsz {
 
 constexpr int kTile = 256;
-constexpr int kMaxTileBytes = 708;    // 8 * (4 + 4 * 21) + 4, Eq. 3 with rate <= 21
+constexpr int kMaxTileBytes = 772;    // 8 * (4 + 4 * 23) + 4, Eq. 3 with rate <= 23
 constexpr int kMaxDecTileBytes = 1028;  // any header-valid tile: 8 * (4 + 4 * 31) + 4
-constexpr uint32_t kQmax = 174761;    // largest Q with (3Q + 4) 2^-23 <= 2^-4
+// The quantization margin eps = (3Q + 4) 2^-23 is capped at 2^-4 (first tier); fields that
+// need more take the second tier, capped at 2^-1. Q bounds |q|; Q < 2^21 keeps every
+// residual below 2^23 (rate <= 23) and every quantized value exact in the float32 rounding.
+constexpr uint32_t kQmax1 = 174761;   // largest Q with (3Q + 4) 2^-23 <= 2^-4
+constexpr uint32_t kQmax2 = 1398100;  // largest Q with (3Q + 4) 2^-23 <= 2^-1
 constexpr int kMinChunkTiles = 16;    // smallest chunk any kernel uses (workspace sizing)
 // Tiles per work item (one ticket, one lookback flag). Compression (and its value-range
 // pass, which shares the chunk -> field table) uses chunks of one 4-tile quad per compute

@@ -17,8 +17,9 @@ constexpr int kStatsThreads = 256;
 // of the error-bound argument of Sec. 4.2.2): ABS takes eb as given, REL takes
 // REL x (max - min) in float64 (REL x |max|, or REL, for a constant field). The half step
 // e = eb (1 - eps) rounded toward zero, eps = (3Q + 4) 2^-23, Q = ceil(A / (2 eb (1 -
-// 2^-4))) + 1, A = max |d|: the two float32 roundings of quantization and
-// reconstruction then stay inside eb for every |q| <= Q.
+// c))) + 1, A = max |d|, with the cap c = 2^-4 where that gives eps <= 2^-4 and c = 2^-1
+// (eps <= 2^-1) otherwise: the two float32 roundings of quantization and reconstruction
+// then stay inside eb for every |q| <= Q.
 __device__ uint32_t derive_params(FieldInfo* fi) {
   if (fi->max_abs_bits >= 0x7f800000u) return FSZ_ERR_NONFINITE;
   float vmin = 0.0f, vmax = 0.0f;
@@ -40,11 +41,18 @@ __device__ uint32_t derive_params(FieldInfo* fi) {
   const double two100 = 1267650600228229401496703205376.0;  // 2^100
   double eb_eff = eb < two100 ? eb : two100;
   double A = fmax(fabs(double(vmin)), fabs(double(vmax)));
-  double denom = __dmul_rn(__dmul_rn(2.0, eb_eff), 0.9375);
-  double K = __ddiv_rn(A, denom);
-  if (!(K <= double(kQmax))) return FSZ_ERR_EB_TOO_SMALL;
-  uint32_t Q = uint32_t(ceil(K)) + 1u;
-  if (Q > kQmax) return FSZ_ERR_EB_TOO_SMALL;
+  // first tier: K = A / (2 eb (1 - 2^-4)), eps <= 2^-4
+  double K = __ddiv_rn(A, __dmul_rn(__dmul_rn(2.0, eb_eff), 0.9375));
+  uint32_t Q = 0;
+  if (K <= double(kQmax1) && uint32_t(ceil(K)) + 1u <= kQmax1) {
+    Q = uint32_t(ceil(K)) + 1u;
+  } else {
+    // second tier, for fields the first refuses: K = A / (2 eb (1 - 2^-1)), eps <= 2^-1
+    K = __ddiv_rn(A, __dmul_rn(__dmul_rn(2.0, eb_eff), 0.5));
+    if (!(K <= double(kQmax2))) return FSZ_ERR_EB_TOO_SMALL;
+    Q = uint32_t(ceil(K)) + 1u;
+    if (Q > kQmax2) return FSZ_ERR_EB_TOO_SMALL;
+  }
   double eps = __dmul_rn(double(3u * Q + 4u), 1.1920928955078125e-07);  // x 2^-23, exact
   double x = __dmul_rn(eb_eff, __dadd_rn(1.0, -eps));
   float e = __double2float_rz(x);

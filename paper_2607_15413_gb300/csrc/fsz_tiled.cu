@@ -758,7 +758,7 @@ uint64_t fsz_compress_bound_tiled(uint64_t n, uint32_t block, uint32_t tile_bloc
   if ((block != 32 && block != 64) || (tile_blocks != 4 && tile_blocks != 8 && tile_blocks != 16))
     return 0;
   const uint64_t NT = (n + tile - 1) / tile;
-  return 64 + uint64_t(tile_blocks) * NT + (uint64_t(tile_blocks) * (block / 8) * 22 + 4) * NT;
+  return 64 + uint64_t(tile_blocks) * NT + (uint64_t(tile_blocks) * (block / 8) * 24 + 4) * NT;
 }
 
 uint64_t fsz_tiled_workspace_bytes(uint64_t n) { return tiled_layout(n).bytes; }

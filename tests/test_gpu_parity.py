@@ -118,6 +118,29 @@ def test_adversarial_midpoints(fszlib, oracle):
         assert_full_parity(fszlib, oracle, x, eb, mode=0)
 
 
+def test_second_margin_tier(fszlib, oracle):
+    """Fields the first margin tier (eps <= 2^-4) refuses and the second (eps <= 2^-1)
+    accepts: a large offset over a small range, and bin midpoints +-1 ulp over the whole
+    range of q of a second-tier bound; a bound beyond the second tier is refused on the
+    device as by the oracle."""
+    rng = np.random.default_rng(9)
+    x = (1.0e4 + rng.normal(0, 30.0, 150000)).astype(np.float32)
+    for rel in (1e-4, 3e-5):
+        assert oracle.params_for(x, oracle.REL, rel).Q > 174761
+        assert_full_parity(fszlib, oracle, x, rel)
+    assert _status_of_compress(fszlib, x, 1e-5) == fszlib.ERR_EB_TOO_SMALL
+    A = np.float32(1.0)
+    eb = 1.0 / 700000.0
+    p = oracle.params(oracle.ABS, eb, -float(A), float(A))
+    assert p.Q > 174761
+    k = np.arange(-p.Q, p.Q + 1, max(1, p.Q // 30000), dtype=np.int64)
+    mid = ((k.astype(np.float64) + 0.5) * float(np.float32(p.s))).astype(np.float32)
+    xm = np.concatenate([mid, np.nextafter(mid, np.float32(np.inf)),
+                         np.nextafter(mid, np.float32(-np.inf)), np.array([A, -A], np.float32)])
+    xm = xm[np.abs(xm) <= A].astype(np.float32)
+    assert_full_parity(fszlib, oracle, xm, eb, mode=0)
+
+
 def test_empty_field(fszlib, oracle):
     dev = _cuda()
     x = torch.empty(0, dtype=torch.float32, device=dev)

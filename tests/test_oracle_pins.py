@@ -544,3 +544,67 @@ def test_all_core_driver_reproduces_the_oracle(oracle, nthreads):
     with pytest.raises(oracle.OracleError) as ei:
         oracle.mt_compress(bad, 1e-3, oracle.REL, nthreads=nthreads)
     assert ei.value.status == oracle.ERR_NONFINITE
+
+
+# --------------------------------------------------------------------------- second margin tier
+
+def test_params_second_tier(oracle):
+    # A field the first tier (eps <= 2^-4) refuses takes the second: Q from A / (2 eb (1 -
+    # 2^-1)), eps = (3Q + 4) 2^-23 <= 2^-1, e = eb (1 - eps) rounded toward zero.
+    for A, eb in ((1.0, 1.0 / 600000.0), (37.25, 37.25 / 1.2e6), (1.0, 1.0 / 1398000.0)):
+        K1 = A / (2 * eb * (1 - 2 ** -4))
+        assert math.ceil(K1) + 1 > 174761                     # beyond the first tier
+        p = oracle.params(oracle.ABS, eb, -A, A)
+        assert p.Q == math.ceil(A / (2 * eb * (1 - 2 ** -1))) + 1
+        eps = (3 * p.Q + 4) * 2.0 ** -23
+        assert eps <= 0.5
+        target = p.eb_eff * (1 - eps)
+        e = np.float32(p.e)
+        assert float(e) <= target < float(np.nextafter(e, np.float32(np.inf)))
+        assert A / (2 * float(e)) < p.Q                       # Q bounds |q|
+    with pytest.raises(oracle.OracleError) as ei:              # beyond the second tier
+        oracle.params(oracle.ABS, 1.0 / 1.5e6, -1.0, 1.0)
+    assert ei.value.status == oracle.ERR_EB_TOO_SMALL
+    # the first tier is unchanged where it applies
+    p = oracle.params(oracle.ABS, 1.0 / 300000.0, -1.0, 1.0)
+    assert p.Q == math.ceil(1.0 / (2 * (1.0 / 300000.0) * (1 - 2 ** -4))) + 1 <= 174761
+
+
+@pytest.mark.parametrize("eb", [1.0 / 700000.0, 37.25 / 1.3e6])
+def test_error_bound_adversarial_midpoints_second_tier(oracle, eb):
+    # Bin midpoints +-1, +-2 ulp over the whole range of q of a second-tier field, and the
+    # extremes: every reconstruction within eb (exact in float64), the integers round trip.
+    A = np.float32(37.25) if eb > 1e-5 else np.float32(1.0)
+    p = oracle.params(oracle.ABS, eb, -float(A), float(A))
+    assert p.Q > 174761
+    s = np.float32(p.s)
+    k = np.arange(-p.Q, p.Q + 1, max(1, p.Q // 4000), dtype=np.int64)
+    mid = ((k.astype(np.float64) + 0.5) * float(s)).astype(np.float32)
+    cand = [mid]
+    for ulps in (1, 2):
+        cand.append(np.nextafter(mid, np.float32(np.inf)))
+        cand.append(np.nextafter(mid, np.float32(-np.inf)))
+        mid = cand[-2]
+    x = np.concatenate(cand + [np.array([A, -A], np.float32)])
+    x = x[np.abs(x) <= A].astype(np.float32)
+    st = oracle.compress(x, eb, oracle.ABS)
+    y = oracle.decompress(st)
+    assert np.abs(x.astype(np.float64) - y.astype(np.float64)).max() <= p.eb
+    q = oracle.decompress(st, q=True)
+    assert np.array_equal(q, oracle.quantize(x, p.r))
+    hdr = np.frombuffer(st[64:64 + 8 * ((x.size + 255) // 256)], np.uint8)
+    assert int((hdr & 31).max()) <= 23                         # the rate bound of the tier
+    assert len(st) <= oracle.compress_bound(x.size)
+
+
+def test_offset_field_in_the_second_tier(oracle):
+    # A large offset over a small range (A / range ~ 40): REL 1e-4 and 3e-5 need the second
+    # tier; REL 1e-5 is beyond it.
+    rng = np.random.default_rng(9)
+    x = (1.0e4 + rng.normal(0, 30.0, 50000)).astype(np.float32)
+    for rel in (1e-4, 3e-5):
+        _check_bound(oracle, x, rel, oracle.REL)
+        assert oracle.params_for(x, oracle.REL, rel).Q > 174761
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.compress(x, 1e-5, oracle.REL)
+    assert ei.value.status == oracle.ERR_EB_TOO_SMALL

@@ -295,17 +295,19 @@ fsz_status fsz_read_header(const void* h_first64, uint64_t* n, fsz_dims* dims, d
 #define FSZ_NOALLOC_MAX_ELEMS (1ull << 28)
 
 /* fsz_compress for callers that cannot allocate device memory (no counterpart in the
- * paper; an addition of this library). Examples: code that compresses while a stream is
- * captured in the default global capture mode, where cudaMalloc/cudaFree are not
- * allowed; plugins whose host framework owns all device memory through its own pool;
- * latency-critical paths that cannot take the synchronisation an allocation may cause.
+ * paper; an addition of this library). Examples: plugins whose host framework owns all
+ * device memory through its own pool (an allocation of their own would be refused or
+ * unaccounted for); latency-critical paths that cannot take the synchronisation an
+ * allocation may cause.
  * The caller passes only the input and output buffers; the scratch the kernels need
  * lives in a fixed device array of about 0.8 MiB inside the library, which every GPU that
  * loads the library holds until the process exits. The function allocates nothing.
  *  - n above FSZ_NOALLOC_MAX_ELEMS returns FSZ_ERR_WORKSPACE; other argument errors as
  *    fsz_compress.
- *  - The first call on each device looks up that array's device address (a one-time,
- *    non-stream runtime call); make that first call before any stream capture begins.
+ *  - The first call on each device does that device's one-time set-up: it looks up the
+ *    array's device address and sets the compression kernels' attributes (their dynamic
+ *    shared-memory size) and reads their occupancy there, all non-stream runtime calls;
+ *    make that first call before any stream capture begins.
  *  - All calls share the one array and each clears the part it uses on `stream`. Calls
  *    whose work overlaps on the GPU (different streams or threads without ordering)
  *    race on it and produce wrong streams: order them on one stream or serialise them.

@@ -728,7 +728,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
 }  // namespace
 
 LaunchCfg compress_cfg() {
-  static LaunchCfg cfg = [] {
+  static DeviceCfgCache cache;
+  return cache.get([] {
     LaunchCfg c;
     c.smem = int(sizeof(CompressSmem));
     cudaFuncSetAttribute(fsz_compress_kernel<false, false>,
@@ -746,8 +747,7 @@ LaunchCfg compress_cfg() {
     c.per = per > 0 ? per : 1;
     c.grid = sms * c.per;
     return c;
-  }();
-  return cfg;
+  });
 }
 
 void launch_compress(const KernelArgs& a, cudaStream_t st, CompressKind kind) {

@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
 }  // namespace
 
 LaunchCfg decompress_cfg() {
-  static LaunchCfg cfg = [] {
+  static DeviceCfgCache cache;
+  return cache.get([] {
     LaunchCfg c;
     c.smem = int(sizeof(DecompressSmem));
     cudaFuncSetAttribute(fsz_decompress_kernel<false, false>,
@@ -424,8 +425,7 @@ LaunchCfg decompress_cfg() {
     c.per = per > 0 ? per : 1;
     c.grid = sms * c.per;
     return c;
-  }();
-  return cfg;
+  });
 }
 
 void launch_decompress(const KernelArgs& a, cudaStream_t st, DecompressKind kind) {

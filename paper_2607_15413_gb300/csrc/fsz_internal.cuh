@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "../../include/fsz.h"
@@ -497,6 +498,27 @@ struct LaunchCfg {
   int smem;
   int sms;
   int per;   // CTAs per SM that fit
+};
+
+// A kernel's launch configuration for each device the library is used on: `init` (which
+// sets the kernel's attributes and reads its occupancy on the current device) runs once per
+// device, on first use there; later calls on that device reuse the result.
+constexpr int kMaxDevices = 64;
+struct DeviceCfgCache {
+  std::mutex mu;
+  LaunchCfg cfg[kMaxDevices];
+  bool ready[kMaxDevices] = {};
+  template <typename F>
+  LaunchCfg get(F init) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[dev]) {
+      cfg[dev] = init();
+      ready[dev] = true;
+    }
+    return cfg[dev];
+  }
 };
 
 // Persistent CTAs per SM chosen by fsz_set_schedule (0 = as many as fit), per kernel.

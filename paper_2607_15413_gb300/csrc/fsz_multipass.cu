@@ -76,14 +76,18 @@ __global__ void __launch_bounds__(kCostThreads) fsz_cost_pass_kernel(KernelArgs 
 }
 
 int cost_grid() {
-  static int g = [] {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_cost_pass_kernel<0>, kCostThreads, 0);
-    return sms * (per > 0 ? per : 1);
-  }();
-  return g;
+  static DeviceCfgCache cache;  // per device
+  return cache.get([] {
+    LaunchCfg c;
+    c.grid = [&] {
+      int dev = 0, sms = 0, per = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_cost_pass_kernel<0>, kCostThreads, 0);
+      return sms * (per > 0 ? per : 1);
+    }();
+    return c;
+  }).grid;
 }
 
 }  // namespace

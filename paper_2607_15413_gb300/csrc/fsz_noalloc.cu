@@ -1,9 +1,8 @@
 // fsz_compress_noalloc: single-field compression with a built-in workspace.
 //
-// For callers that must not allocate device memory: code that compresses while a
-// stream is being captured in the default (global) capture mode, where cudaMalloc and
-// cudaFree are not allowed; plugins whose host framework owns every byte of device
-// memory through its own pool; and latency-critical paths that cannot afford the
+// For callers that must not allocate device memory: plugins whose host framework owns
+// every byte of device memory through its own pool (an allocation of their own would be
+// refused or unaccounted for), and latency-critical paths that cannot afford the
 // device-wide synchronisation an allocation can cause. Such a caller passes only its
 // input and output buffers; the scratch the kernels need (control words, per-field
 // state and lookback flags) lives in the file-scope array below, which every GPU that

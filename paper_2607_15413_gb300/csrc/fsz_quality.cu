@@ -135,14 +135,18 @@ __global__ void __launch_bounds__(kQThreads) fsz_quality_kernel(const float* __r
 }
 
 int quality_grid() {
-  static int g = [] {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_quality_kernel, kQThreads, 0);
-    return std::min(kQMaxCtas, sms * (per > 0 ? per : 1));
-  }();
-  return g;
+  static DeviceCfgCache cache;  // per device
+  return cache.get([] {
+    LaunchCfg c;
+    c.grid = [&] {
+      int dev = 0, sms = 0, per = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fsz_quality_kernel, kQThreads, 0);
+      return std::min(kQMaxCtas, sms * (per > 0 ? per : 1));
+    }();
+    return c;
+  }).grid;
 }
 
 }  // namespace

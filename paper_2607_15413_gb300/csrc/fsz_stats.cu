@@ -377,7 +377,8 @@ __global__ void __launch_bounds__(kPlanThreads) fsz_plan_kernel(KernelArgs a, co
 }  // namespace
 
 LaunchCfg stats_cfg() {
-  static LaunchCfg cfg = [] {
+  static DeviceCfgCache cache;
+  return cache.get([] {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -388,8 +389,7 @@ LaunchCfg stats_cfg() {
     c.grid = sms * c.per;
     c.smem = 0;
     return c;
-  }();
-  return cfg;
+  });
 }
 
 void launch_stats(const KernelArgs& a, cudaStream_t st) {

@@ -725,13 +725,17 @@ __global__ void __launch_bounds__(kTiledThreads) fsz_tiled_decode_kernel(KernelA
 }
 
 int tiled_grid() {
-  static int g = [] {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms * 8;
-  }();
-  return g;
+  static DeviceCfgCache cache;  // per device
+  return cache.get([] {
+    LaunchCfg c;
+    c.grid = [&] {
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      return sms * 8;
+    }();
+    return c;
+  }).grid;
 }
 
 template <int B, int T>

@@ -1,8 +1,8 @@
 """fsz_compress_noalloc against fsz_compress (GB300 only).
 
 The no-allocation entry point serves callers that cannot allocate device memory
-(for example code running inside a global-mode stream capture, or a plugin whose
-framework owns all device memory). It must produce the same stream as the regular
+(for example a plugin whose framework owns all device memory, or a latency-critical
+path that cannot take the synchronisation an allocation may cause). It must produce the same stream as the regular
 entry point, byte for byte (the tolerance of every parity test here is 0), on two
 calls in a row, because the built-in scratch array keeps the previous call's
 contents and each call must clear what it relies on. This file is collected last so

@@ -217,20 +217,7 @@ __device__ __forceinline__ void planes8(const uint32_t (&v)[32], uint32_t (&X)[8
     const uint32_t b = __byte_perm(v[23 - k], v[31 - k], sel);
     X[k] = __byte_perm(a, b, 0x5410);
   }
-#pragma unroll
-  for (int t = 0; t < 3; ++t) {
-    const int s = 1 << t;
-    const uint32_t M = t == 0 ? 0x55555555u : (t == 1 ? 0x33333333u : 0x0F0F0F0Fu);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      if (k & s) continue;
-      const uint32_t a = X[k], b = X[k | s];
-      // b keeps its bits whose index has bit t set and takes a's bits with it set, moved
-      // down; a keeps its bits with it clear and takes b's bits with it clear, moved up.
-      X[k | s] = (b & ~M) | ((a >> s) & M);
-      X[k] = (a & M) | (shl_fma(b, s) & ~M);
-    }
-  }
+  swap_planes(X);
 }
 
 // Compresses one quad (4 tiles) with one warp. Lane L = 8 tq + g holds block g of tile tq

@@ -10,10 +10,14 @@
 //                 as the record is in, publishes the inclusive prefix, then waits for a
 //                 free payload stage and loads the chunk's payload into it with a 1-D TMA
 //                 bulk copy (the lookback thus overlaps the decoding of earlier chunks);
-//   decode warps  (8) d4 bit-unshuffle one tile at a time (lane j owns elements 8j..8j+7),
-//                 d5 invert the prediction as warp-wide prefix sums (once for LZ1, twice
-//                 for LZ2), add mu, d' = fl(float(q) s), and store the tile with a 1-D TMA
-//                 bulk store from a per-warp double buffer.
+//   decode warps  (8) each decode a quad of 4 tiles at a time, lane L holding block L & 7
+//                 of tile L >> 3 (32 consecutive elements): d4 reads the block's sign map
+//                 and planes and undoes the bit shuffle with the register-pair delta swaps
+//                 of the compressor, run backwards; d5 inverts the prediction as prefix sums
+//                 inside the lane with the carry from the tile's earlier blocks by an 8-lane
+//                 scan (once for LZ1, twice for LZ2), adds mu, d' = fl(float(q) s); the
+//                 floats go through a per-warp swizzled buffer so that each store of the
+//                 warp writes 512 consecutive bytes.
 #include "fsz_internal.cuh"
 
 namespace fsz {
@@ -26,6 +30,7 @@ constexpr int kLoaderWarp = kDecodeWarps + 1;
 constexpr int kThreads = (kDecodeWarps + 2) * 32;
 constexpr int kStages = 2;   // payload stages
 constexpr int kRecs = 6;     // chunk records in flight (fetched .. decoded)
+constexpr int kQuadTiles = 4;  // tiles per decode warp and iteration
 constexpr int kPayloadBytes = kDChunkTiles * kMaxDecTileBytes + 32;
 static_assert(kDChunkTiles <= 32, "one lane per tile in the chunk scan");
 static_assert(kPayloadBytes % 16 == 0, "stage size");
@@ -38,8 +43,6 @@ struct ChunkRec {
   uint64_t hdr[kDChunkTiles];
   uint64_t boff[kDChunkTiles];  // block word offsets of each tile (block_word_offsets)
   uint32_t toff[kDChunkTiles];
-  uint8_t list[kDChunkTiles];   // pre-zeroed output: the tiles to decode (not all-zero ones)
-  uint32_t ndec;                // how many
   FieldInfo* fi;
   float* dout;           // the chunk's first output element
   const uint8_t* sin;    // the field's stream
@@ -62,7 +65,7 @@ struct ChunkRec {
 
 struct __align__(16) DecompressSmem {
   uint8_t payload[kStages][kPayloadBytes];
-  float out[kDecodeWarps][2][kTile];  // per-warp double buffer for the TMA stores
+  float out[kDecodeWarps][kQuadTiles * kTile];  // per-warp re-layout of a quad's floats
   ChunkRec rec[kRecs];
   uint64_t fetched[kRecs], recfree[kRecs], full[kStages], empty[kStages];
 };
@@ -88,28 +91,71 @@ __device__ __forceinline__ bool header_reserved_bits_set(uint64_t h) {
   return (h & 0x20u) || (h & 0xE0E0E0E0E0E0E000ULL);
 }
 
-// Decodes one tile with one warp; returns false if the tile's mean slot is malformed.
-// kAny: the instance that also decodes streams without the cross-block state; for those
-// (`indep`) the inverse prediction's prefix sums restart at every block (4 lanes, zero
-// predecessors): the warp-wide prefix less the prefix at the block's start. The other
-// instance carries none of that code (it costs the full method's decode 3 %).
-template <bool kAny>
-__device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t boff,
-                                                const uint8_t* __restrict__ tp,
-                                                float* __restrict__ out, const float s,
-                                                const int lane, const bool indep) {
-  constexpr uint32_t FULL = 0xffffffffu;
-  const int g = lane >> 2, t = lane & 3;
-  const bool second = (h & 0x80u) != 0, centred = (h & 0x40u) != 0;
-  const int Rg = int((h >> (8 * g)) & 31u);
-  // d2: words per block (rate + 1, or 0) and block offsets by a byte-wise prefix sum.
-  const int offw = int((boff >> (8 * g)) & 0xFFu);
-  const uint8_t* blk = tp + (centred ? 4 : 0) + 4 * offw;
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts128(uint32_t addr, float4 v) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w)
+               : "memory");
+}
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr)
+               : "memory");
+  return v;
+}
 
+// Inclusive prefix sum over a tile of x[0..31] in each lane (the lane's block), the 8
+// lanes of a tile carrying block to block: the lane's own prefix, then the exclusive scan
+// of the blocks' totals over the tile's lanes, plus `add`. Without the carried state
+// (indep) each block restarts. Lanes with `apply` false keep x; every lane of the warp
+// must call this (the scan's shuffles take the full warp), and the 8 lanes of a tile
+// agree on `apply`, so the scan segments of applying tiles see only their own lanes.
+template <bool kAny>
+__device__ __forceinline__ void tile_prefix(uint32_t (&x)[32], const uint32_t add, const bool indep,
+                                            const bool apply) {
+  if (apply) {
+#pragma unroll
+    for (int i = 1; i < 32; ++i) x[i] += x[i - 1];
+  }
+  const uint32_t tot = x[31];
+  uint32_t inc = tot;
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) inc = scan_step_up<8>(inc, o);
+  uint32_t ex = inc - tot;
+  if (kAny && indep) ex = 0;
+  ex += add;
+  if (apply) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] += ex;
+  }
+}
+
+// Decodes one quad (4 tiles) with one warp into o (lane L: block L & 7 of tile L >> 3).
+// h, boff: the lane's tile's header and block word offsets; tp: shared-memory address of
+// the tile's data; live: the tile exists. Returns false if a tile's mean slot is
+// malformed. kAny: the instance that also decodes streams without the cross-block state
+// (`indep`: every block restarts from zero predecessors).
+template <bool kAny>
+__device__ __forceinline__ bool decompress_quad(const uint64_t h, const uint64_t boff,
+                                                const uint32_t tp, const bool live, const float s,
+                                                const int lane, const bool indep, float (&o)[32]) {
+  constexpr uint32_t FULL = 0xffffffffu;
+  const int g = lane & 7;
+  const bool second = (h & 0x80u) != 0, centred = (h & 0x40u) != 0;
+  const int Rg = live ? int((h >> (8 * g)) & 31u) : 0;
+  const int nw = Rg > 0 ? Rg + 1 : 0;  // block g's words: sign map + Rg planes
+  // d2: block offsets by a byte-wise prefix sum (done by the header warp)
+  const uint32_t blk = tp + (centred ? 4u : 0u) + 4u * uint32_t((boff >> (8 * g)) & 0xFFu);
   bool good = true;
   int mu = 0;
-  if (centred) {
-    const float muf = *reinterpret_cast<const float*>(tp);
+  if (live && centred) {
+    const float muf = __uint_as_float(lds32(tp));
     if (!(fabsf(muf) <= 16777216.0f)) {
       good = false;
     } else {
@@ -117,66 +163,43 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
       if (__int2float_rn(mu) != muf) good = false;
     }
   }
-
-  // d4: decode and bit-unshuffle: words -> per-lane plane bytes -> 8x8 transpose.
-  uint32_t vv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // d4: the block's words, back through the plane network, into sign-magnitude words v
+  uint32_t v[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = 0u;
   const int Rmax = int(__reduce_max_sync(FULL, uint32_t(Rg)));
-  const int nwords = Rg > 0 ? Rg + 1 : 0;  // block g's words: sign map + Rg planes
   if (Rmax > 0) {
     const int nch = (Rmax + 8) >> 3;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       if (c < nch) {
-        const int w0 = 8 * c + t, w1 = w0 + 4;
-        uint32_t lo = w0 < nwords ? reinterpret_cast<const uint32_t*>(blk)[w0] : 0u;
-        uint32_t hi = w1 < nwords ? reinterpret_cast<const uint32_t*>(blk)[w1] : 0u;
-        lo = transpose4x4_bytes(lo, t);
-        hi = transpose4x4_bytes(hi, t);
-        transpose8x8(lo, hi);
-        // lo bytes 0..3 are byte c of v_7..v_4, hi bytes 0..3 byte c of v_3..v_0.
+        uint32_t X[8];
+#pragma unroll
+        for (int b = 0; b < 8; ++b) X[b] = 8 * c + b < nw ? lds32(blk + 4u * uint32_t(8 * c + b)) : 0u;
+        swap_planes(X);
+        // byte m of X[k] is byte c of element 8 m + 7 - k
         const uint32_t keep = 0x3210u & ~(0xFu << (4 * c));
-        vv[7] = __byte_perm(vv[7], lo, keep | (4u << (4 * c)));
-        vv[6] = __byte_perm(vv[6], lo, keep | (5u << (4 * c)));
-        vv[5] = __byte_perm(vv[5], lo, keep | (6u << (4 * c)));
-        vv[4] = __byte_perm(vv[4], lo, keep | (7u << (4 * c)));
-        vv[3] = __byte_perm(vv[3], hi, keep | (4u << (4 * c)));
-        vv[2] = __byte_perm(vv[2], hi, keep | (5u << (4 * c)));
-        vv[1] = __byte_perm(vv[1], hi, keep | (6u << (4 * c)));
-        vv[0] = __byte_perm(vv[0], hi, keep | (7u << (4 * c)));
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            v[8 * m + 7 - k] = __byte_perm(v[8 * m + 7 - k], X[k], keep | ((4u + m) << (4 * c)));
       }
     }
   }
-  // Sign-magnitude back to residuals (two's-complement wrap-around arithmetic).
-  uint32_t x[8];
+  // sign-magnitude back to residuals (two's-complement wrap-around arithmetic)
+  uint32_t x[32];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    x[i] = uint32_t(mad_s32(int(vv[i] >> 1), mad_s32(int(vv[i] & 1u), -2, 1), 0));
-  }
+  for (int i = 0; i < 32; ++i) x[i] = uint32_t(mad_s32(int(v[i] >> 1), mad_s32(int(v[i] & 1u), -2, 1), 0));
   // d5: inverse prediction. With zero predecessors, LZ1's q_i = l_i + q_{i-1} is an
   // inclusive prefix sum over the tile; LZ2's q_i = l_i + 2 q_{i-1} - q_{i-2} is the prefix
-  // sum of the prefix sum (the first sum rebuilds the LZ1 residuals).
-  auto prefix = [&](uint32_t (&v)[8]) {
+  // sum of the prefix sum (the first sum rebuilds the LZ1 residuals); then + mu. The
+  // quad's tiles may differ in their predictor: the first sum runs on the whole warp and
+  // applies to the LZ2 tiles only.
+  if (__any_sync(FULL, second)) tile_prefix<kAny>(x, 0u, indep, second);
+  tile_prefix<kAny>(x, uint32_t(mu), indep, true);
 #pragma unroll
-    for (int i = 1; i < 8; ++i) v[i] += v[i - 1];
-    const uint32_t tot = v[7];
-    uint32_t inc = tot;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) inc = scan_step_up(inc, o);
-    uint32_t ex = inc - tot;
-    if (kAny && indep) {  // less the inclusive prefix of the lane before the block's first
-      const uint32_t b = __shfl_sync(FULL, inc, (lane & ~3) - 1);
-      if (lane >= 4) ex -= b;
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] += ex;
-  };
-  if (second) prefix(x);
-  prefix(x);
-  float o[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) o[i] = __fmul_rn(__int2float_rn(int(x[i] + uint32_t(mu))), s);
-  reinterpret_cast<float4*>(out)[2 * lane] = make_float4(o[0], o[1], o[2], o[3]);
-  reinterpret_cast<float4*>(out)[2 * lane + 1] = make_float4(o[4], o[5], o[6], o[7]);
+  for (int i = 0; i < 32; ++i) o[i] = __fmul_rn(__int2float_rn(int(x[i])), s);
   return __all_sync(FULL, good);
 }
 
@@ -184,7 +207,7 @@ __device__ __forceinline__ bool decompress_tile(const uint64_t h, const uint64_t
 // holds zeros; tiles whose 8 blocks all have rate 0 and no mean (all +0.0) are neither
 // decoded nor written (the adaptive pre-zero of Sec. 3.1 for high compression ratios).
 template <bool kAny, bool kPrezero>
-__global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs a) {
+__global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs a) {
   extern __shared__ __align__(128) uint8_t smem_raw[];
   DecompressSmem& S = *reinterpret_cast<DecompressSmem*>(smem_raw);
   constexpr uint32_t FULL = 0xffffffffu;
@@ -254,12 +277,6 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
         if (lane >= o) inc += y;
       }
       if (lane < kDChunkTiles) q.toff[lane] = inc - mine;
-      uint32_t dmask = 0;
-      if constexpr (kPrezero) {
-        const bool dec = lane < ntiles && (hb & 0x1F1F1F1F1F1F1F5FULL) != 0;
-        dmask = __ballot_sync(FULL, dec);
-        if (dec) q.list[__popc(dmask & ((1u << lane) - 1u))] = uint8_t(lane);
-      }
       const uint32_t tot = __shfl_sync(FULL, inc, 31);
       if (lane == 0) {
         if (uint64_t(c) != a.skip_chunk) st_flag(a.flags + uint64_t(c) * kFlagStride, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
@@ -277,7 +294,6 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
         q.ntiles = uint32_t(ntiles);
         q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kDChunkElems)));
         q.step = fi->s;
-        q.ndec = uint32_t(__popc(dmask));
         q.indep = (foff & kOffCross) ? 1u : 0u;
       }
       __syncwarp();
@@ -353,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
   }
 
   // ------------------------------------------------------------------ decode warps
-  uint32_t nstore = 0;
+  const uint32_t obuf = smem_u32(S.out[warp]);
   bool good = true;
   for (uint32_t seq = 0;; ++seq) {
     const int r = int(seq % kRecs), p = int(seq % kStages);
@@ -370,26 +386,47 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
       const int ntiles = int(st.ntiles);
       const uint32_t cnt = st.cnt;
       float* dout = st.dout;
-      const uint8_t* pay = S.payload[p] + st.shift;
-      const int nloop = kPrezero ? int(st.ndec) : ntiles;
-      for (int i = warp; i < nloop; i += kDecodeWarps) {
-        const int tl = kPrezero ? int(st.list[i]) : i;
-        float* buf = S.out[warp][nstore & 1u];
-        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+      const uint32_t pay = smem_u32(S.payload[p]) + st.shift;
+      const int nquads = (ntiles + kQuadTiles - 1) / kQuadTiles;
+      for (int qd = warp; qd < nquads; qd += kDecodeWarps) {
+        const int t = kQuadTiles * qd + (lane >> 3);
+        const bool live = t < ntiles;
+        const uint64_t h = live ? st.hdr[t] : 0ull;
+        // a pre-zeroed output: a tile whose rates are all 0 and that has no mean is +0.0
+        // throughout, neither decoded nor written; a quad of such tiles is skipped
+        const bool write_tile = live && (!kPrezero || (h & 0x1F1F1F1F1F1F1F5FULL) != 0);
+        if (kPrezero && !__any_sync(FULL, write_tile)) continue;
+        float o[32];
+        good &= decompress_quad<kAny>(h, live ? st.boff[t] : 0ull, pay + (live ? st.toff[t] : 0u),
+                                      live, step, lane, st.indep != 0, o);
+        // re-layout: lane L's block goes to row L of the buffer, 16-byte piece k at column
+        // k ^ (L & 7) (conflict-free); then each piece P = 32 j + lane, read back in order,
+        // is stored to the output, the warp writing 512 consecutive bytes per store
+        const uint32_t row = obuf + uint32_t(lane) * 128u;
+        const uint32_t sw = uint32_t(lane & 7) << 4;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          sts128(row + ((uint32_t(k << 4)) ^ sw), make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]));
+        const uint32_t tmask = __ballot_sync(FULL, write_tile && (lane & 7) == 0);
         __syncwarp();
-        good &= decompress_tile<kAny>(st.hdr[tl], st.boff[tl], pay + st.toff[tl], buf, step, lane,
-                                      st.indep != 0);
-        fence_proxy_async();
-        __syncwarp();
-        const uint32_t k0 = uint32_t(tl) * kTile;
-        const uint32_t valid_elems = min(uint32_t(kTile), cnt - k0);
-        const uint32_t bulk = (valid_elems * 4) & ~15u;
-        if (lane == 0 && bulk) {
-          tma_store_1d(dout + k0, buf, bulk);
-          tma_store_commit();
+        const uint32_t e0 = uint32_t(kQuadTiles * qd) * kTile;  // the quad's first element
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const uint32_t P = uint32_t(32 * j + lane);   // piece: row P >> 3, column P & 7
+          const uint32_t rw = P >> 3;
+          const float4 val = lds128(obuf + rw * 128u + (((P & 7u) ^ (rw & 7u)) << 4));
+          const uint32_t e = e0 + 4 * P;
+          if (!((tmask >> (8 * (rw >> 3))) & 1u)) continue;  // (a tile not written)
+          if (e + 4 <= cnt) {
+            *reinterpret_cast<float4*>(dout + e) = val;
+          } else {
+            const float vals[4] = {val.x, val.y, val.z, val.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (e + i < cnt) dout[e + i] = vals[i];
+          }
         }
-        for (uint32_t k = bulk / 4 + lane; k < valid_elems; k += 32) dout[k0 + k] = buf[k];
-        ++nstore;
+        __syncwarp();  // the buffer is read before the next quad overwrites it
       }
     }
     if (!good && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
@@ -400,7 +437,6 @@ __global__ void __launch_bounds__(kThreads, 4) fsz_decompress_kernel(KernelArgs 
       mbar_arrive(&S.recfree[r]);
     }
   }
-  if (lane == 0) tma_store_wait_all();
 }
 
 }  // namespace

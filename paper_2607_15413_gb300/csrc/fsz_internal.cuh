@@ -27,14 +27,14 @@ constexpr uint32_t kQmax2 = 1398100;  // largest Q with (3Q + 4) 2^-23 <= 2^-1
 constexpr int kMinChunkTiles = 16;    // smallest chunk any kernel uses (workspace sizing)
 // Tiles per work item (one ticket, one lookback flag). Compression (and its value-range
 // pass, which shares the chunk -> field table) uses chunks of one 4-tile quad per compute
-// warp of a CTA: 8 warps, 32 tiles. Decompression stages a chunk's whole payload at once,
-// so its chunks stay at 16 tiles.
+// warp of a CTA: 8 warps, 32 tiles. Decompression stages a chunk's whole payload at once:
+// 32 tiles too, one quad per decode warp.
 #ifndef FSZ_CCHUNK_TILES
 #define FSZ_CCHUNK_TILES 32
 #endif
 constexpr int kCChunkTiles = FSZ_CCHUNK_TILES;
 constexpr int kCChunkElems = kCChunkTiles * kTile;
-constexpr int kDChunkTiles = 16;
+constexpr int kDChunkTiles = 32;
 constexpr int kDChunkElems = kDChunkTiles * kTile;
 static_assert(kCChunkTiles >= kMinChunkTiles && kDChunkTiles >= kMinChunkTiles, "workspace sizing");
 constexpr uint64_t kMaxElems = uint64_t(1) << 40;
@@ -328,6 +328,30 @@ __device__ __forceinline__ void transpose8x8(uint32_t& lo, uint32_t& hi) {
   t = (lo ^ (lo >> 14)) & 0x0000CCCCu; lo = lo ^ t ^ shl_fma(t, 14);
   t = (hi ^ (hi >> 14)) & 0x0000CCCCu; hi = hi ^ t ^ shl_fma(t, 14);
   t = (lo ^ shl_fma(hi, 4)) & 0xF0F0F0F0u; lo ^= t; hi ^= (t >> 4);
+}
+
+// The bit-plane network of both kernels. X[k] (k = 0..7) holds 4 bytes, byte m of X[k]
+// standing for bits 0..7 of some element e(m, k); three delta swaps between register
+// pairs (k, k ^ 2^t), t = 0, 1, 2, exchange bit t of the register index k with bit t of
+// the bit index inside each byte, after which X[b] bit 8m + k is bit b of e(m, k): eight
+// bit-plane words. Each swap is its own inverse and the three act on disjoint index
+// bits, so the same network takes the plane words back to the bytes. (Delta swaps as in
+// H. S. Warren, Hacker's Delight, "Transposing a bit matrix", here across registers.)
+__device__ __forceinline__ void swap_planes(uint32_t (&X)[8]) {
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int s = 1 << t;
+    const uint32_t M = t == 0 ? 0x55555555u : (t == 1 ? 0x33333333u : 0x0F0F0F0Fu);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k & s) continue;
+      const uint32_t a = X[k], b = X[k | s];
+      // b keeps its bits whose index has bit t set and takes a's bits with it set, moved
+      // down; a keeps its bits with it clear and takes b's bits with it clear, moved up.
+      X[k | s] = (b & ~M) | ((a >> s) & M);
+      X[k] = (a & M) | (shl_fma(b, s) & ~M);
+    }
+  }
 }
 
 // One step of an inclusive scan: v += v of lane - o, where that lane exists within the

@@ -7,9 +7,11 @@
 //                 leaves the chunk's record (headers, offsets, field parameters) in a ring
 //                 of kRecs records, running ahead of decoding;
 //   loader warp   d3 looks back for the chunk's byte offset (decoupled lookback) as soon
-//                 as the record is in, publishes the inclusive prefix, then waits for a
-//                 free payload stage and loads the chunk's payload into it with a 1-D TMA
-//                 bulk copy (the lookback thus overlaps the decoding of earlier chunks);
+//                 as the record is in, publishes the inclusive prefix, then takes the
+//                 chunk's payload bytes (its actual size, not the worst case) from a byte
+//                 ring, waiting for the oldest chunks' decoding to release space, and loads
+//                 the payload there with a 1-D TMA bulk copy. Compressed chunks being far
+//                 below the worst case, several are in flight per CTA;
 //   decode warps  (8) each decode a quad of 4 tiles at a time, lane L holding block L & 7
 //                 of tile L >> 3 (32 consecutive elements): d4 reads the block's sign map
 //                 and planes and undoes the bit shuffle with the register-pair delta swaps
@@ -28,14 +30,37 @@ constexpr int kDecodeWarps = 8;
 constexpr int kHeaderWarp = kDecodeWarps;
 constexpr int kLoaderWarp = kDecodeWarps + 1;
 constexpr int kThreads = (kDecodeWarps + 2) * 32;
-constexpr int kStages = 2;   // payload stages
-constexpr int kRecs = 6;     // chunk records in flight (fetched .. decoded)
+#ifndef FSZ_DEC_RECS
+#define FSZ_DEC_RECS 12
+#endif
+#ifndef FSZ_DEC_RING_BYTES
+#define FSZ_DEC_RING_BYTES 65536
+#endif
+constexpr int kRecs = FSZ_DEC_RECS;  // chunk records in flight (fetched .. decoded)
+constexpr uint32_t kRingBytes = FSZ_DEC_RING_BYTES;  // payload byte ring
 constexpr int kQuadTiles = 4;  // tiles per decode warp and iteration
-constexpr int kPayloadBytes = kDChunkTiles * kMaxDecTileBytes + 32;
+// Ring bytes a chunk can take: its payload (at most kDChunkTiles header-valid tiles) from
+// the 16-byte boundary below its start, rounded up to 16 bytes.
+constexpr uint32_t kMaxChunkRingBytes = kDChunkTiles * kMaxDecTileBytes + 32;
 static_assert(kDChunkTiles <= 32, "one lane per tile in the chunk scan");
-static_assert(kPayloadBytes % 16 == 0, "stage size");
+static_assert((kRingBytes & (kRingBytes - 1)) == 0 && kRingBytes >= kMaxChunkRingBytes,
+              "the ring is a power of two that holds the largest chunk");
+static_assert(kRecs >= 2 && kRecs <= 16, "records in flight");
 constexpr uint32_t kNoneChunk = 0xffffffffu;
-constexpr int kLookbackPerLane = 4;  // 128-flag lookback window
+#ifndef FSZ_DEC_LOOKBACK_K
+#define FSZ_DEC_LOOKBACK_K 4
+#endif
+#ifndef FSZ_DEC_TICKET_CHUNKS
+#define FSZ_DEC_TICKET_CHUNKS 3
+#endif
+constexpr int kLookbackPerLane = FSZ_DEC_LOOKBACK_K;  // lookback window: 32 K flags
+// Chunks per ticket: a ticket hands a CTA kTicketChunks consecutive chunks. Their rate
+// headers are read together, and a chunk that follows its group's previous chunk in the
+// same field takes its byte offset from that chunk (no lookback), so the atomics and the
+// lookbacks per chunk drop by that factor.
+constexpr int kTicketChunks = FSZ_DEC_TICKET_CHUNKS;
+static_assert(kTicketChunks >= 1 && kTicketChunks <= 4 && kRecs >= 2 * kTicketChunks,
+              "chunks per ticket");
 
 // A chunk's header and parameters, from the header warp to the loader and the decode
 // warps through shared memory (keeps dependent global loads off the decode path).
@@ -56,18 +81,22 @@ struct ChunkRec {
   uint32_t tot;          // payload bytes of the chunk
   uint32_t bad;          // reserved header bits seen
   uint32_t valid;        // payload loaded and decodable
-  uint32_t shift;        // payload start inside the stage
+  uint32_t pay;          // payload start inside the ring
   uint32_t ntiles;
   uint32_t cnt;          // valid elements of the chunk
   uint32_t indep;        // the stream's blocks are independent (no carried state)
+  uint32_t chain;        // the previous record holds chunk - 1 of the same field
   float step;
 };
 
 struct __align__(16) DecompressSmem {
-  uint8_t payload[kStages][kPayloadBytes];
+  uint8_t ring[kRingBytes];
   float out[kDecodeWarps][kQuadTiles * kTile];  // per-warp re-layout of a quad's floats
   ChunkRec rec[kRecs];
-  uint64_t fetched[kRecs], recfree[kRecs], full[kStages], empty[kStages];
+  uint32_t ring_end[kRecs];  // loader only: ring position (mod 2^32) after each chunk's bytes
+  // fetched: record in (header -> loader); full: payload in (loader -> decode warps);
+  // done: chunk decoded, its record and ring bytes free (decode warps -> header, loader)
+  uint64_t fetched[kRecs], full[kRecs], done[kRecs];
 };
 
 // Bytes of a tile from its 8 header bytes: sum of S_b (Eq. 3) + 4 for a centred tile.
@@ -91,6 +120,13 @@ __device__ __forceinline__ bool header_reserved_bits_set(uint64_t h) {
   return (h & 0x20u) || (h & 0xE0E0E0E0E0E0E000ULL);
 }
 
+// Byte permute with the generic mode's sign replication (a selector nibble with bit 3 set
+// fills the result byte with the top bit of the byte it selects).
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
+}
 __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
   uint32_t v;
   asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
@@ -119,11 +155,19 @@ __device__ __forceinline__ float4 lds128(uint32_t addr) {
 template <bool kAny>
 __device__ __forceinline__ void tile_prefix(uint32_t (&x)[32], const uint32_t add, const bool indep,
                                             const bool apply) {
+  // the lane's prefix as four independent 8-element runs (short dependency chains), the
+  // runs' offsets folded into the final additions
+  uint32_t o1 = 0, o2 = 0, o3 = 0, tot = 0;
   if (apply) {
 #pragma unroll
-    for (int i = 1; i < 32; ++i) x[i] += x[i - 1];
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int i = 1; i < 8; ++i) x[8 * k + i] += x[8 * k + i - 1];
+    o1 = x[7];
+    o2 = o1 + x[15];
+    o3 = o2 + x[23];
+    tot = o3 + x[31];
   }
-  const uint32_t tot = x[31];
   uint32_t inc = tot;
 #pragma unroll
   for (int o = 1; o < 8; o <<= 1) inc = scan_step_up<8>(inc, o);
@@ -131,8 +175,9 @@ __device__ __forceinline__ void tile_prefix(uint32_t (&x)[32], const uint32_t ad
   if (kAny && indep) ex = 0;
   ex += add;
   if (apply) {
+    const uint32_t e[4] = {ex, ex + o1, ex + o2, ex + o3};
 #pragma unroll
-    for (int i = 0; i < 32; ++i) x[i] += ex;
+    for (int i = 0; i < 32; ++i) x[i] += e[i >> 3];
   }
 }
 
@@ -149,7 +194,6 @@ __device__ __forceinline__ bool decompress_quad(const uint64_t h, const uint64_t
   const int g = lane & 7;
   const bool second = (h & 0x80u) != 0, centred = (h & 0x40u) != 0;
   const int Rg = live ? int((h >> (8 * g)) & 31u) : 0;
-  const int nw = Rg > 0 ? Rg + 1 : 0;  // block g's words: sign map + Rg planes
   // d2: block offsets by a byte-wise prefix sum (done by the header warp)
   const uint32_t blk = tp + (centred ? 4u : 0u) + 4u * uint32_t((boff >> (8 * g)) & 0xFFu);
   bool good = true;
@@ -163,34 +207,68 @@ __device__ __forceinline__ bool decompress_quad(const uint64_t h, const uint64_t
       if (__int2float_rn(mu) != muf) good = false;
     }
   }
-  // d4: the block's words, back through the plane network, into sign-magnitude words v
-  uint32_t v[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = 0u;
+  // d4: the block's planes (sign map, then the magnitude bits) become the planes of the
+  // two's-complement residuals by a bit-sliced negation of the negative elements,
+  // x = (m ^ S) + S over all 32 elements at once (S the sign map); the planes above the
+  // rate then all equal the result's sign plane. They go back through the plane network,
+  // and each element is gathered from its bytes by permutes that replicate the top byte's
+  // sign, which sign-extends it.
   const int Rmax = int(__reduce_max_sync(FULL, uint32_t(Rg)));
-  if (Rmax > 0) {
-    const int nch = (Rmax + 8) >> 3;
+  const int nch = Rmax > 0 ? (Rmax + 8) >> 3 : 0;
+  uint32_t X[4][8];
+  {
+    const uint32_t S = Rg > 0 ? lds32(blk) : 0u;
+    uint32_t carry = S;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       if (c < nch) {
-        uint32_t X[8];
 #pragma unroll
-        for (int b = 0; b < 8; ++b) X[b] = 8 * c + b < nw ? lds32(blk + 4u * uint32_t(8 * c + b)) : 0u;
-        swap_planes(X);
-        // byte m of X[k] is byte c of element 8 m + 7 - k
-        const uint32_t keep = 0x3210u & ~(0xFu << (4 * c));
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-#pragma unroll
-          for (int m = 0; m < 4; ++m)
-            v[8 * m + 7 - k] = __byte_perm(v[8 * m + 7 - k], X[k], keep | ((4u + m) << (4 * c)));
+        for (int b = 0; b < 8; ++b) {
+          const int j = 8 * c + b;  // plane j of x: magnitude plane j is the block's word j + 1
+          const uint32_t M = j < Rg ? lds32(blk + 4u * uint32_t(j + 1)) : 0u;
+          const uint32_t y = M ^ S;
+          X[c][b] = y ^ carry;
+          carry &= y;
+        }
+        swap_planes(X[c]);
       }
     }
   }
-  // sign-magnitude back to residuals (two's-complement wrap-around arithmetic)
+  // byte m of X[c][k] is byte c of element 8 m + 7 - k
   uint32_t x[32];
+  if (nch == 0) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i) x[i] = uint32_t(mad_s32(int(v[i] >> 1), mad_s32(int(v[i] & 1u), -2, 1), 0));
+    for (int i = 0; i < 32; ++i) x[i] = 0u;
+  } else if (nch == 1) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        x[8 * m + 7 - k] = prmt(X[0][k], 0u, m | ((8 | m) << 4) | ((8 | m) << 8) | ((8 | m) << 12));
+  } else if (nch == 2) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        x[8 * m + 7 - k] = prmt(X[0][k], X[1][k], m | ((4 + m) << 4) | ((12 + m) << 8) | ((12 + m) << 12));
+  } else if (nch == 3) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const uint32_t t = prmt(X[0][k], X[1][k], m | ((4 + m) << 4));
+        x[8 * m + 7 - k] = prmt(t, X[2][k], 0x0010u | ((4 + m) << 8) | ((12 + m) << 12));
+      }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const uint32_t t = prmt(X[0][k], X[1][k], m | ((4 + m) << 4));
+        const uint32_t u = prmt(X[2][k], X[3][k], (m << 8) | ((4 + m) << 12));
+        x[8 * m + 7 - k] = prmt(t, u, 0x7610u);
+      }
+  }
   // d5: inverse prediction. With zero predecessors, LZ1's q_i = l_i + q_{i-1} is an
   // inclusive prefix sum over the tile; LZ2's q_i = l_i + 2 q_{i-1} - q_{i-2} is the prefix
   // sum of the prefix sum (the first sum rebuilds the LZ1 residuals); then + mu. The
@@ -218,11 +296,8 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
   if (tid == 0) {
     for (int k = 0; k < kRecs; ++k) {
       mbar_init(&S.fetched[k], 1);
-      mbar_init(&S.recfree[k], kDecodeWarps);
-    }
-    for (int k = 0; k < kStages; ++k) {
       mbar_init(&S.full[k], 1);
-      mbar_init(&S.empty[k], kDecodeWarps);
+      mbar_init(&S.done[k], kDecodeWarps);
     }
     fence_mbar_init();
   }
@@ -231,80 +306,126 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
   if (warp == kHeaderWarp) {
     // ---------------------------------------------------------------- header warp
     const bool single = a.ctrl->nfields == 1;
-    for (uint32_t seq = 0;; ++seq) {
-      const int r = int(seq % kRecs);
-      if (seq >= uint32_t(kRecs) && !mbar_wait(&S.recfree[r], ((seq / kRecs) - 1) & 1u, wait_ns)) {
+    for (uint32_t seq = 0;; seq += kTicketChunks) {
+      // the group's records must be free: their previous chunks decoded
+      bool ok = true;
+#pragma unroll
+      for (int g = 0; g < kTicketChunks; ++g) {
+        const uint32_t sg = seq + g;
+        if (ok && sg >= uint32_t(kRecs))
+          ok = mbar_wait(&S.done[sg % kRecs], ((sg / kRecs) - 1) & 1u, wait_ns);
+      }
+      if (!ok) {
         if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
         return;
       }
-      ChunkRec& q = S.rec[r];
-      uint32_t c = 0;
-      if (lane == 0) c = atomicAdd(&a.ctrl->ticket, 1u);
-      c = __shfl_sync(FULL, c, 0);
-      if (c >= total) {
-        if (lane == 0) {
-          q.chunk = kNoneChunk;
-          mbar_arrive(&S.fetched[r]);
-        }
-        return;
-      }
-      FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
-      const uint64_t first = fi->chunk_first;
-      const uint64_t lc = c - first;
-      const uint64_t T = fi->T;
-      const uint64_t tile0 = lc * kDChunkTiles;
-      const int ntiles = int(min(uint64_t(kDChunkTiles), T - tile0));
-      const uint8_t* sin = fi->sin;
-      uint64_t hb = 0;
-      if (lane < ntiles) hb = __ldg(reinterpret_cast<const unsigned long long*>(sin + 64) + tile0 + lane);
-      if (lane < kDChunkTiles) {
-        q.hdr[lane] = hb;
-        q.boff[lane] = block_word_offsets(hb);
-      }
-      // a tile may not use a feature the stream has switched off
-      const uint32_t foff = fi->features_off;
-      const uint64_t forbid = ((foff & kOffLz2) ? 0x80u : 0u) | ((foff & kOffCenter) ? 0x40u : 0u);
-      // streams without the cross-block state are decoded by the kAny instance only
-      const bool unsupported = !kAny && (foff & kOffCross);
-      if (unsupported && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_INVALID_ARG);
-      const bool bad_hdr = unsupported ||
-          __any_sync(FULL, lane < ntiles && (header_reserved_bits_set(hb) || (hb & forbid)));
-      const uint32_t mine = lane < ntiles ? tile_bytes_from_header(hb) : 0u;
-      uint32_t inc = mine;
+      // (tickets only go to running CTAs: a CTA that is not resident yet, e.g. behind
+      // another stream's kernel, holds no chunk that the others' lookbacks wait for)
+      uint32_t t = 0;
+      if (lane == 0) t = atomicAdd(&a.ctrl->ticket, 1u);
+      t = __shfl_sync(FULL, t, 0);
+      const uint64_t c0 = uint64_t(t) * kTicketChunks;
+      // field, position and rate header of each chunk of the group (loads issued together)
+      FieldInfo* fis[kTicketChunks];
+      uint64_t hbs[kTicketChunks];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += y;
+      for (int g = 0; g < kTicketChunks; ++g) {
+        const uint64_t c = c0 + g;
+        fis[g] = nullptr;
+        hbs[g] = 0;
+        if (c < total) {
+          FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
+          fis[g] = fi;
+          const uint64_t tile0 = (c - fi->chunk_first) * kDChunkTiles;
+          if (tile0 + lane < fi->T)
+            hbs[g] = __ldg(reinterpret_cast<const unsigned long long*>(fi->sin + 64) + tile0 + lane);
+        }
       }
-      if (lane < kDChunkTiles) q.toff[lane] = inc - mine;
-      const uint32_t tot = __shfl_sync(FULL, inc, 31);
-      if (lane == 0) {
-        if (uint64_t(c) != a.skip_chunk) st_flag(a.flags + uint64_t(c) * kFlagStride, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
-        q.chunk = c;
-        q.lc = uint32_t(lc);
-        q.last = (lc + 1 == fi->nchunks) ? 1u : 0u;
-        q.tot = tot;
-        q.bad = bad_hdr ? 1u : 0u;
-        q.fi = fi;
-        q.sin = sin;
-        q.in_bytes = fi->in_bytes;
-        q.data_bytes = fi->data_bytes;
-        q.data_base = 64 + 8 * T;
-        q.dout = fi->dout + tile0 * kTile;
-        q.ntiles = uint32_t(ntiles);
-        q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kDChunkElems)));
-        q.step = fi->s;
-        q.indep = (foff & kOffCross) ? 1u : 0u;
+      bool end = false;
+      uint64_t prev_lc = 0;
+#pragma unroll
+      for (int g = 0; g < kTicketChunks; ++g) {
+        const uint32_t sg = seq + g;
+        const int r = int(sg % kRecs);
+        ChunkRec& q = S.rec[r];
+        const uint64_t c = c0 + g;
+        if (end) continue;
+        if (c >= total) {
+          if (lane == 0) {
+            q.chunk = kNoneChunk;
+            mbar_arrive(&S.fetched[r]);
+          }
+          end = true;
+          continue;
+        }
+        FieldInfo* fi = fis[g];
+        const uint64_t hb = hbs[g];
+        const uint64_t first = fi->chunk_first;
+        const uint64_t lc = c - first;
+        const uint64_t T = fi->T;
+        const uint64_t tile0 = lc * kDChunkTiles;
+        const int ntiles = int(min(uint64_t(kDChunkTiles), T - tile0));
+        if (lane < kDChunkTiles) {
+          q.hdr[lane] = hb;
+          q.boff[lane] = block_word_offsets(hb);
+        }
+        // a tile may not use a feature the stream has switched off
+        const uint32_t foff = fi->features_off;
+        const uint64_t forbid = ((foff & kOffLz2) ? 0x80u : 0u) | ((foff & kOffCenter) ? 0x40u : 0u);
+        // streams without the cross-block state are decoded by the kAny instance only
+        const bool unsupported = !kAny && (foff & kOffCross);
+        if (unsupported && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_INVALID_ARG);
+        const bool bad_hdr = unsupported ||
+            __any_sync(FULL, lane < ntiles && (header_reserved_bits_set(hb) || (hb & forbid)));
+        const uint32_t mine = lane < ntiles ? tile_bytes_from_header(hb) : 0u;
+        uint32_t inc = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(FULL, inc, o);
+          if (lane >= o) inc += y;
+        }
+        if (lane < kDChunkTiles) q.toff[lane] = inc - mine;
+        const uint32_t tot = __shfl_sync(FULL, inc, 31);
+        // the chunk follows the group's previous one (unless that one is held back by the
+        // test hook, whose successors must meet its missing flag)
+        const bool chain = g > 0 && fis[g - 1] == fi && lc == prev_lc + 1 && c - 1 != a.skip_chunk;
+        prev_lc = lc;
+        if (lane == 0) {
+          if (c != a.skip_chunk) st_flag(a.flags + c * kFlagStride, (lc == 0 ? kFlagIncl : kFlagAgg) | tot);
+          q.chunk = uint32_t(c);
+          q.lc = uint32_t(lc);
+          q.last = (lc + 1 == fi->nchunks) ? 1u : 0u;
+          q.tot = tot;
+          q.bad = bad_hdr ? 1u : 0u;
+          q.fi = fi;
+          q.sin = fi->sin;
+          q.in_bytes = fi->in_bytes;
+          q.data_bytes = fi->data_bytes;
+          q.data_base = 64 + 8 * T;
+          q.dout = fi->dout + tile0 * kTile;
+          q.ntiles = uint32_t(ntiles);
+          q.cnt = uint32_t(min(fi->n - tile0 * kTile, uint64_t(kDChunkElems)));
+          q.step = fi->s;
+          q.indep = (foff & kOffCross) ? 1u : 0u;
+          q.chain = chain ? 1u : 0u;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.fetched[r]);
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.fetched[r]);
+      if (end) return;
     }
   }
 
   if (warp == kLoaderWarp) {
     // ---------------------------------------------------------------- loader warp
+    // Ring positions count bytes modulo 2^32: head = where the next payload goes, freed =
+    // how far the decoded chunks have released. Chunks take and release space in ticket
+    // order, so the bytes in use are head - freed.
+    uint32_t head = 0, freed = 0;
+    uint32_t oldest = 0;  // the oldest chunk whose bytes are not yet known to be released
+    uint64_t prev_excl = 0, prev_tot = 0;  // the previous record's chunk: offset and bytes
     for (uint32_t seq = 0;; ++seq) {
-      const int r = int(seq % kRecs), p = int(seq % kStages);
+      const int r = int(seq % kRecs);
       if (!mbar_wait(&S.fetched[r], (seq / kRecs) & 1u, wait_ns)) {
         if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
         return;
@@ -318,20 +439,20 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
       uint64_t excl = 0;
       if (!none && q.lc != 0) {
         bool to = false;
-        excl = lookback<kLookbackPerLane>(a.flags, int64_t(c), int64_t(c) - int64_t(q.lc),
-                                          globaltimer_ns() + a.timeout_ns, &to);
+        if (q.chain)  // d3 from the group's previous chunk, resolved just before
+          excl = prev_excl + prev_tot;
+        else
+          excl = lookback<kLookbackPerLane>(a.flags, int64_t(c), int64_t(c) - int64_t(q.lc),
+                                            globaltimer_ns() + a.timeout_ns, &to);
         if (lane == 0) {
           if (to) set_error(a.ctrl, fi, FSZ_ERR_TIMEOUT);
           if (!skip) st_flag(a.flags + uint64_t(c) * kFlagStride, kFlagIncl | (excl + tot));
         }
       }
-      // The payload stage frees once the decode warps are through chunk seq - kStages.
-      if (seq >= uint32_t(kStages) && !mbar_wait(&S.empty[p], ((seq / kStages) - 1) & 1u, wait_ns)) {
-        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
-        return;
-      }
+      prev_excl = excl;
+      prev_tot = tot;
       if (none) {
-        if (lane == 0) mbar_arrive(&S.full[p]);
+        if (lane == 0) mbar_arrive(&S.full[r]);
         return;
       }
       bool valid = q.bad == 0 && !skip;
@@ -345,14 +466,42 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
       const uint64_t end_up = (src + tot + 15) & ~uint64_t(15);
       const uint64_t a1 = end_up <= base + q.in_bytes ? end_up : ((src + tot) & ~uint64_t(15));
       const uint32_t bulk = (valid && a1 > a0) ? uint32_t(a1 - a0) : 0u;
+      // ring space: the payload from a0, rounded up to 16 bytes, in one piece (a payload
+      // that would run past the ring's end starts at the ring's start instead)
+      const uint32_t need = valid ? (uint32_t(src - a0) + tot + 15u) & ~15u : 0u;
+      uint32_t start = head;
+      if ((start & (kRingBytes - 1)) + need > kRingBytes) start += kRingBytes - (start & (kRingBytes - 1));
+      // Chunks seq - kRecs and older are decoded: the header warp reused their records.
+      while (oldest + uint32_t(kRecs) <= seq) freed = S.ring_end[oldest++ % kRecs];
+      bool space = true;
+      while (start + need - freed > kRingBytes) {
+        if (oldest == seq) {  // nothing in flight: the skipped end of the ring is free too
+          freed = start;
+          break;
+        }
+        // wait for the oldest chunk in flight; its record is not reused before it is done
+        if (!mbar_wait(&S.done[oldest % kRecs], (oldest / kRecs) & 1u, wait_ns)) {
+          space = false;
+          break;
+        }
+        freed = S.ring_end[oldest % kRecs];
+        ++oldest;
+      }
+      if (!space) {
+        if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+        return;
+      }
+      head = start + need;
+      if (lane == 0) S.ring_end[r] = head;
+      const uint32_t phys = start & (kRingBytes - 1);
       if (lane == 0) {
         if (!valid && !skip) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
-        q.shift = uint32_t(src - a0);
+        q.pay = phys + uint32_t(src - a0);
         q.valid = valid ? 1u : 0u;
         if (bulk) {
           fence_proxy_async();
-          mbar_expect_tx(&S.full[p], bulk);
-          tma_load_1d(S.payload[p], reinterpret_cast<const void*>(a0), bulk, &S.full[p]);
+          mbar_expect_tx(&S.full[r], bulk);
+          tma_load_1d(S.ring + phys, reinterpret_cast<const void*>(a0), bulk, &S.full[r]);
         }
       }
       if (valid) {
@@ -360,11 +509,11 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
         const uint32_t lo = uint32_t(max(a1, src) - a0), hi = uint32_t(src + tot - a0);
         const uint8_t* gb = reinterpret_cast<const uint8_t*>(a0);
         for (uint32_t k = lo + 4 * uint32_t(lane); k < hi; k += 128)
-          *reinterpret_cast<uint32_t*>(S.payload[p] + k) = *reinterpret_cast<const uint32_t*>(gb + k);
+          *reinterpret_cast<uint32_t*>(S.ring + phys + k) = *reinterpret_cast<const uint32_t*>(gb + k);
       }
       __threadfence_block();  // every lane's tail bytes before lane 0's arrival
       __syncwarp();
-      if (lane == 0) mbar_arrive(&S.full[p]);
+      if (lane == 0) mbar_arrive(&S.full[r]);
     }
   }
 
@@ -372,8 +521,8 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
   const uint32_t obuf = smem_u32(S.out[warp]);
   bool good = true;
   for (uint32_t seq = 0;; ++seq) {
-    const int r = int(seq % kRecs), p = int(seq % kStages);
-    if (!mbar_wait(&S.full[p], (seq / kStages) & 1u, wait_ns)) {
+    const int r = int(seq % kRecs);
+    if (!mbar_wait(&S.full[r], (seq / kRecs) & 1u, wait_ns)) {
       if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
       break;
     }
@@ -386,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
       const int ntiles = int(st.ntiles);
       const uint32_t cnt = st.cnt;
       float* dout = st.dout;
-      const uint32_t pay = smem_u32(S.payload[p]) + st.shift;
+      const uint32_t pay = smem_u32(S.ring) + st.pay;
       const int nquads = (ntiles + kQuadTiles - 1) / kQuadTiles;
       for (int qd = warp; qd < nquads; qd += kDecodeWarps) {
         const int t = kQuadTiles * qd + (lane >> 3);
@@ -432,10 +581,7 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
     if (!good && lane == 0) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
     good = true;
     __syncwarp();
-    if (lane == 0) {
-      mbar_arrive(&S.empty[p]);
-      mbar_arrive(&S.recfree[r]);
-    }
+    if (lane == 0) mbar_arrive(&S.done[r]);
   }
 }
 

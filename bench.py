@@ -294,7 +294,7 @@ def run_batched(fsz, inputs, dev, reps: int = 3):
     pf_out = db.arena.clone()
     t_b_d = timed(lambda: db.launch_graph())
     exact = exact and torch.equal(pf_out, db.arena) and cb.status()[0] == fsz.OK and db.status()[0] == fsz.OK
-    fsz.fsz_set_schedule(0, 0, 0)
+    tune.apply(None)
     comp_bytes = sum(sizes)
     out = {"workload": "512 fields, seed 3: log-uniform 64 KiB-64 MiB, 1-3-D, 40% k^-3 GRF / "
                        "40% particle-like / 20% zero-slab, REL in {1e-2,1e-3,1e-4}",

@@ -274,6 +274,33 @@ fsz_status fsz_set_schedule(uint32_t stats_ctas_per_sm, uint32_t compress_ctas_p
 fsz_status fsz_get_schedule_limits(uint32_t* stats_max, uint32_t* compress_max,
                                    uint32_t* decompress_max, uint32_t* sms);
 
+/* The full launch schedule (no counterpart in the paper, which fixes one tile-to-block
+ * mapping; none of it changes a stream). The persistent kernels hand out work by atomic
+ * tickets; a ticket covers `*_ticket_chunks` consecutive chunks of 32 tiles (1-4), the
+ * unit of work a CTA takes, and in each of its chunks after the first the chunk's byte
+ * offset follows from the previous one without a lookback (Sec. 4.4). Compression takes
+ * tickets up to `compress_ticket_lead` chunks (1-3) ahead of its compute warps;
+ * decompression keeps up to `decompress_records` chunks (2 x ticket chunks .. 16) between
+ * ticket and decode per CTA. `reserved` must be 0. Defaults: CTAs 0 (as many as fit),
+ * compression 2 chunks per ticket with lead 2, decompression 3 chunks per ticket and 12
+ * records. Read by every later call of this process at launch (a CUDA graph keeps the
+ * schedule it was captured with). Used by the autotuner; not thread-safe. */
+typedef struct fsz_schedule {
+  uint32_t stats_ctas_per_sm;
+  uint32_t compress_ctas_per_sm;
+  uint32_t decompress_ctas_per_sm;
+  uint32_t compress_ticket_chunks;
+  uint32_t compress_ticket_lead;
+  uint32_t decompress_ticket_chunks;
+  uint32_t decompress_records;
+  uint32_t reserved;
+} fsz_schedule;
+/* Installs `s` (NULL: the defaults). FSZ_ERR_INVALID_ARG if a field is out of range; the
+ * schedule in force is then unchanged. */
+fsz_status fsz_set_schedule_ex(const fsz_schedule* s);
+/* The schedule in force (host pointer). */
+fsz_status fsz_get_schedule(fsz_schedule* out);
+
 /* ------------------------------------------------------------------ status and metadata */
 
 /* Waits for `stream`, then returns the first device-detected error recorded in the

@@ -11,7 +11,7 @@ static_assert(sizeof(fsz_dims) == 32 && sizeof(fsz_cfield) == 80 && sizeof(fsz_d
               "C ABI struct layouts");
 
 namespace fsz {
-int g_sched[3] = {0, 0, 0};
+Schedule g_schedule = {{0, 0, 0}, 2, 2, 3, 12};
 }
 
 // A captured batched call (fsz_graph in the C ABI).
@@ -349,9 +349,44 @@ fsz_status fsz_set_schedule(uint32_t stats_ctas_per_sm, uint32_t compress_ctas_p
                             uint32_t decompress_ctas_per_sm) {
   if (stats_ctas_per_sm > 64 || compress_ctas_per_sm > 64 || decompress_ctas_per_sm > 64)
     return FSZ_ERR_INVALID_ARG;
-  g_sched[kSchedStats] = int(stats_ctas_per_sm);
-  g_sched[kSchedCompress] = int(compress_ctas_per_sm);
-  g_sched[kSchedDecompress] = int(decompress_ctas_per_sm);
+  g_schedule.ctas[kSchedStats] = int(stats_ctas_per_sm);
+  g_schedule.ctas[kSchedCompress] = int(compress_ctas_per_sm);
+  g_schedule.ctas[kSchedDecompress] = int(decompress_ctas_per_sm);
+  return FSZ_OK;
+}
+
+fsz_status fsz_set_schedule_ex(const fsz_schedule* sc) {
+  if (sc == nullptr) {  // the defaults
+    g_schedule = Schedule{{0, 0, 0}, 2, 2, 3, 12};
+    return FSZ_OK;
+  }
+  if (sc->stats_ctas_per_sm > 64 || sc->compress_ctas_per_sm > 64 || sc->decompress_ctas_per_sm > 64 ||
+      sc->compress_ticket_chunks < 1 || sc->compress_ticket_chunks > uint32_t(kMaxTicketChunks) ||
+      sc->compress_ticket_lead < 1 || sc->compress_ticket_lead > uint32_t(kMaxCompressLead) ||
+      sc->decompress_ticket_chunks < 1 || sc->decompress_ticket_chunks > uint32_t(kMaxTicketChunks) ||
+      sc->decompress_records < 2 * sc->decompress_ticket_chunks ||
+      sc->decompress_records > uint32_t(kMaxDecRecords) || sc->reserved != 0)
+    return FSZ_ERR_INVALID_ARG;
+  g_schedule.ctas[kSchedStats] = int(sc->stats_ctas_per_sm);
+  g_schedule.ctas[kSchedCompress] = int(sc->compress_ctas_per_sm);
+  g_schedule.ctas[kSchedDecompress] = int(sc->decompress_ctas_per_sm);
+  g_schedule.c_ticket_chunks = int(sc->compress_ticket_chunks);
+  g_schedule.c_ticket_lead = int(sc->compress_ticket_lead);
+  g_schedule.d_ticket_chunks = int(sc->decompress_ticket_chunks);
+  g_schedule.d_records = int(sc->decompress_records);
+  return FSZ_OK;
+}
+
+fsz_status fsz_get_schedule(fsz_schedule* out) {
+  if (out == nullptr) return FSZ_ERR_INVALID_ARG;
+  out->stats_ctas_per_sm = uint32_t(g_schedule.ctas[kSchedStats]);
+  out->compress_ctas_per_sm = uint32_t(g_schedule.ctas[kSchedCompress]);
+  out->decompress_ctas_per_sm = uint32_t(g_schedule.ctas[kSchedDecompress]);
+  out->compress_ticket_chunks = uint32_t(g_schedule.c_ticket_chunks);
+  out->compress_ticket_lead = uint32_t(g_schedule.c_ticket_lead);
+  out->decompress_ticket_chunks = uint32_t(g_schedule.d_ticket_chunks);
+  out->decompress_records = uint32_t(g_schedule.d_records);
+  out->reserved = 0;
   return FSZ_OK;
 }
 

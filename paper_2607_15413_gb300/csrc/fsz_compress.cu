@@ -42,12 +42,12 @@ constexpr int kThreads = (kWarps + 2) * 32;
 #define FSZ_RING_BYTES 6144
 #endif
 constexpr int kSets = FSZ_COMPRESS_SETS;           // chunk slots per CTA
-#ifndef FSZ_TICKET_LEAD
-#define FSZ_TICKET_LEAD 2
-#endif
-// The ticket of chunk seq is taken when the compute warps begin chunk seq - kTicketLead.
-constexpr int kTicketLead = FSZ_TICKET_LEAD;
-static_assert(kTicketLead >= 1 && kTicketLead < FSZ_COMPRESS_SETS, "ticket lead");
+// The schedule's work assignment (kernel arguments): a ticket hands a CTA ticket_chunks
+// consecutive chunks, and a chunk that follows the CTA's previous chunk in the same field
+// takes its byte offset from it (the previous offset plus its size) instead of looking
+// back; the ticket of chunk seq is taken when the compute warps begin chunk
+// seq - ticket_lead.
+static_assert(kMaxTicketChunks + kMaxCompressLead <= FSZ_COMPRESS_SETS, "schedule limits");
 #ifndef FSZ_COMPRESS_CTAS
 #define FSZ_COMPRESS_CTAS 2
 #endif
@@ -436,55 +436,58 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
     // ---------------------------------------------------------------- host
     // Tickets and placement, polled in turn:
     //  * the ticket of chunk seq is taken once the compute warps have begun chunk
-    //    seq - kTicketLead (so the chunk order across the grid stays close to the ticket
+    //    seq - lead (so the chunk order across the grid stays close to the ticket
     //    order) and its slot is free (chunk seq - kSets placed); lane 0 reads the field
     //    record and leaves the chunk's parameters in the slot;
     //  * chunk p is placed, in this CTA's order, once its offset is resolved and every
     //    compute warp has encoded its quad: each warp's run is copied from its ring to the
     //    stream and the ring space is given back.
     const bool single = a.ctrl->nfields == 1;
+    const uint32_t group = a.ticket_chunks, lead = a.ticket_lead;
     uint32_t seq_t = 0, p = 0, end_seq = kNone;
     uint64_t deadline = globaltimer_ns() + wait_ns;
     for (;;) {
       bool progress = false;
-      if (end_seq == kNone && seq_t - p < uint32_t(kSets) &&
-          (seq_t < uint32_t(kTicketLead) ||
-           mbar_test(&S.started[(seq_t - kTicketLead) % kSets], ((seq_t - kTicketLead) / kSets) & 1u))) {
-        const int b = int(seq_t % kSets);
-        uint32_t c = 0;
-        if (lane == 0) {
-          ChunkInfo& ci = S.meta[b];
-          c = atomicAdd(&a.ctrl->ticket, 1u);
-          if (c >= total) {
-            ci.chunk = kNone;
-          } else {
-            FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
-            const uint64_t first = fi->chunk_first;
-            const uint64_t lc = c - first;
-            const uint64_t tile0 = lc * kCChunkTiles;
-            const uint64_t e0 = tile0 * kTile;
-            const uint64_t T = fi->T;
-            ci.chunk = c;
-            ci.in = fi->in + e0;
-            ci.out = fi->out;
-            ci.fi = fi;
-            ci.tile0 = tile0;
-            ci.data_base = 64 + 8 * T;
-            ci.cap = fi->cap;
-            ci.chunk_first = first;
-            ci.ntiles = uint32_t(min(uint64_t(kCChunkTiles), T - tile0));
-            ci.cnt = uint32_t(min(fi->n - e0, uint64_t(kCChunkElems)));
-            ci.r = fi->r;
-            ci.off = fi->features_off;
-            ci.flags = (fi->s > 0.0f ? kInfoOk : 0u) |  // a field without a step has nothing to load
-                       (lc + 1 == fi->nchunks ? kInfoLast : 0u) | (lc == 0 ? kInfoFirst : 0u) |
-                       (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
+      if (end_seq == kNone && seq_t + group - p <= uint32_t(kSets) &&
+          (seq_t < lead || mbar_test(&S.started[(seq_t - lead) % kSets], ((seq_t - lead) / kSets) & 1u))) {
+        uint32_t t = 0;
+        if (lane == 0) t = atomicAdd(&a.ctrl->ticket, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        for (uint32_t g = 0; g < group && end_seq == kNone; ++g) {
+          const int b = int((seq_t + g) % kSets);
+          const uint32_t c = t * group + g;
+          if (lane == 0) {
+            ChunkInfo& ci = S.meta[b];
+            if (c >= total) {
+              ci.chunk = kNone;
+            } else {
+              FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
+              const uint64_t first = fi->chunk_first;
+              const uint64_t lc = c - first;
+              const uint64_t tile0 = lc * kCChunkTiles;
+              const uint64_t e0 = tile0 * kTile;
+              const uint64_t T = fi->T;
+              ci.chunk = c;
+              ci.in = fi->in + e0;
+              ci.out = fi->out;
+              ci.fi = fi;
+              ci.tile0 = tile0;
+              ci.data_base = 64 + 8 * T;
+              ci.cap = fi->cap;
+              ci.chunk_first = first;
+              ci.ntiles = uint32_t(min(uint64_t(kCChunkTiles), T - tile0));
+              ci.cnt = uint32_t(min(fi->n - e0, uint64_t(kCChunkElems)));
+              ci.r = fi->r;
+              ci.off = fi->features_off;
+              ci.flags = (fi->s > 0.0f ? kInfoOk : 0u) |  // a field without a step has nothing to load
+                         (lc + 1 == fi->nchunks ? kInfoLast : 0u) | (lc == 0 ? kInfoFirst : 0u) |
+                         (uint64_t(c) == a.skip_chunk ? kInfoSkip : 0u);
+            }
+            mbar_arrive(&S.info[b]);
           }
-          mbar_arrive(&S.info[b]);
+          if (c >= total) end_seq = seq_t + g;
         }
-        c = __shfl_sync(FULL, c, 0);
-        if (c >= total) end_seq = seq_t;
-        ++seq_t;
+        seq_t = end_seq != kNone ? end_seq + 1 : seq_t + group;
         progress = true;
       }
       if (p < seq_t && p != end_seq) {
@@ -549,6 +552,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
     // ---------------------------------------------------------------- resolver
     // Step 4 at device level, one chunk after another in this CTA's ticket order, as soon
     // as the chunk's aggregate is out: the compute warps keep encoding meanwhile.
+    uint32_t prev_c = kNone, prev_tot = 0;
+    const FieldInfo* prev_fi = nullptr;
+    uint64_t prev_excl = 0;
+    bool prev_held = true;  // the previous chunk's flags are held back (test hook)
     for (uint32_t seq = 0;; ++seq) {
       const int b = int(seq % kSets);
       if (!mbar_wait_idle(&S.computed[b], (seq / kSets) & 1u, wait_ns, kResolverSleepNs)) {
@@ -562,14 +569,22 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       uint64_t excl = 0;
       if (!(flags & kInfoFirst)) {
         bool to = false;
-        excl = lookback<kLookbackPerLane>(a.flags, int64_t(c), int64_t(ci.chunk_first),
-                                          globaltimer_ns() + a.timeout_ns, &to);
+        if (c == prev_c + 1 && ci.fi == prev_fi && !prev_held)
+          excl = prev_excl + prev_tot;  // the CTA's previous chunk is the one before
+        else
+          excl = lookback<kLookbackPerLane>(a.flags, int64_t(c), int64_t(ci.chunk_first),
+                                            globaltimer_ns() + a.timeout_ns, &to);
         if (lane == 0) {
           if (to) set_error(a.ctrl, ci.fi, FSZ_ERR_TIMEOUT);
           if (!(flags & kInfoSkip))
             st_flag(a.flags + uint64_t(c) * kFlagStride, kFlagIncl | (excl + S.set_tot[b]));
         }
       }
+      prev_c = c;
+      prev_fi = ci.fi;
+      prev_excl = excl;
+      prev_tot = S.set_tot[b];
+      prev_held = (flags & kInfoSkip) != 0;
       __syncwarp();
       if (lane == 0) {
         S.set_excl[b] = excl;
@@ -737,9 +752,12 @@ LaunchCfg compress_cfg() {
   });
 }
 
-void launch_compress(const KernelArgs& a, cudaStream_t st, CompressKind kind) {
+void launch_compress(const KernelArgs& args, cudaStream_t st, CompressKind kind) {
   const LaunchCfg c = compress_cfg();
   const int g = sched_grid(c, kSchedCompress);
+  KernelArgs a = args;
+  a.ticket_chunks = uint32_t(g_schedule.c_ticket_chunks);
+  a.ticket_lead = uint32_t(g_schedule.c_ticket_lead);
   if (kind == kCompressFeatures)
     fsz_compress_kernel<false, true><<<g, kThreads, c.smem, st>>>(a);
   else if (kind == kCompressGiven)

@@ -5,7 +5,7 @@
 //   header warp   takes a ticket, d1 reads the chunk's rate header, d2 derives the tile
 //                 sizes and scans them, publishes the chunk's aggregate flag at once and
 //                 leaves the chunk's record (headers, offsets, field parameters) in a ring
-//                 of kRecs records, running ahead of decoding;
+//                 of records, running ahead of decoding;
 //   loader warp   d3 looks back for the chunk's byte offset (decoupled lookback) as soon
 //                 as the record is in, publishes the inclusive prefix, then takes the
 //                 chunk's payload bytes (its actual size, not the worst case) from a byte
@@ -30,13 +30,10 @@ constexpr int kDecodeWarps = 8;
 constexpr int kHeaderWarp = kDecodeWarps;
 constexpr int kLoaderWarp = kDecodeWarps + 1;
 constexpr int kThreads = (kDecodeWarps + 2) * 32;
-#ifndef FSZ_DEC_RECS
-#define FSZ_DEC_RECS 12
-#endif
 #ifndef FSZ_DEC_RING_BYTES
 #define FSZ_DEC_RING_BYTES 65536
 #endif
-constexpr int kRecs = FSZ_DEC_RECS;  // chunk records in flight (fetched .. decoded)
+constexpr int kMaxRecs = kMaxDecRecords;  // chunk records (fetched .. decoded): up to
 constexpr uint32_t kRingBytes = FSZ_DEC_RING_BYTES;  // payload byte ring
 constexpr int kQuadTiles = 4;  // tiles per decode warp and iteration
 // Ring bytes a chunk can take: its payload (at most kDChunkTiles header-valid tiles) from
@@ -45,22 +42,18 @@ constexpr uint32_t kMaxChunkRingBytes = kDChunkTiles * kMaxDecTileBytes + 32;
 static_assert(kDChunkTiles <= 32, "one lane per tile in the chunk scan");
 static_assert((kRingBytes & (kRingBytes - 1)) == 0 && kRingBytes >= kMaxChunkRingBytes,
               "the ring is a power of two that holds the largest chunk");
-static_assert(kRecs >= 2 && kRecs <= 16, "records in flight");
+
 constexpr uint32_t kNoneChunk = 0xffffffffu;
 #ifndef FSZ_DEC_LOOKBACK_K
 #define FSZ_DEC_LOOKBACK_K 4
 #endif
-#ifndef FSZ_DEC_TICKET_CHUNKS
-#define FSZ_DEC_TICKET_CHUNKS 3
-#endif
 constexpr int kLookbackPerLane = FSZ_DEC_LOOKBACK_K;  // lookback window: 32 K flags
-// Chunks per ticket: a ticket hands a CTA kTicketChunks consecutive chunks. Their rate
-// headers are read together, and a chunk that follows its group's previous chunk in the
-// same field takes its byte offset from that chunk (no lookback), so the atomics and the
-// lookbacks per chunk drop by that factor.
-constexpr int kTicketChunks = FSZ_DEC_TICKET_CHUNKS;
-static_assert(kTicketChunks >= 1 && kTicketChunks <= 4 && kRecs >= 2 * kTicketChunks,
-              "chunks per ticket");
+// The schedule's work assignment (kernel arguments): a ticket hands a CTA ticket_chunks
+// consecutive chunks (at most kMaxTicketChunks). Their rate headers are read together,
+// and a chunk that follows its group's previous chunk in the same field takes its byte
+// offset from that chunk (no lookback), so the atomics and the lookbacks per chunk drop by
+// that factor. A CTA holds `records` chunks (2 x ticket_chunks .. kMaxRecs) between
+// ticket and decode.
 
 // A chunk's header and parameters, from the header warp to the loader and the decode
 // warps through shared memory (keeps dependent global loads off the decode path).
@@ -92,12 +85,14 @@ struct ChunkRec {
 struct __align__(16) DecompressSmem {
   uint8_t ring[kRingBytes];
   float out[kDecodeWarps][kQuadTiles * kTile];  // per-warp re-layout of a quad's floats
-  ChunkRec rec[kRecs];
-  uint32_t ring_end[kRecs];  // loader only: ring position (mod 2^32) after each chunk's bytes
+  ChunkRec rec[kMaxRecs];
+  uint32_t ring_end[kMaxRecs];  // loader only: ring position (mod 2^32) after each chunk's bytes
   // fetched: record in (header -> loader); full: payload in (loader -> decode warps);
   // done: chunk decoded, its record and ring bytes free (decode warps -> header, loader)
-  uint64_t fetched[kRecs], full[kRecs], done[kRecs];
+  uint64_t fetched[kMaxRecs], full[kMaxRecs], done[kMaxRecs];
 };
+// two CTAs per SM (228 KiB of shared memory, 1 KiB of it reserved per CTA)
+static_assert(sizeof(DecompressSmem) <= 113 * 1024, "shared memory of one CTA");
 
 // Bytes of a tile from its 8 header bytes: sum of S_b (Eq. 3) + 4 for a centred tile.
 __device__ __forceinline__ uint32_t tile_bytes_from_header(uint64_t h) {
@@ -292,9 +287,10 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t total = a.ctrl->total_chunks;
   const uint64_t wait_ns = 4 * a.timeout_ns;
+  const uint32_t group = a.ticket_chunks, recs = a.records;
 
   if (tid == 0) {
-    for (int k = 0; k < kRecs; ++k) {
+    for (int k = 0; k < kMaxRecs; ++k) {
       mbar_init(&S.fetched[k], 1);
       mbar_init(&S.full[k], 1);
       mbar_init(&S.done[k], kDecodeWarps);
@@ -306,14 +302,12 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
   if (warp == kHeaderWarp) {
     // ---------------------------------------------------------------- header warp
     const bool single = a.ctrl->nfields == 1;
-    for (uint32_t seq = 0;; seq += kTicketChunks) {
+    for (uint32_t seq = 0;; seq += group) {
       // the group's records must be free: their previous chunks decoded
       bool ok = true;
-#pragma unroll
-      for (int g = 0; g < kTicketChunks; ++g) {
+      for (uint32_t g = 0; g < group; ++g) {
         const uint32_t sg = seq + g;
-        if (ok && sg >= uint32_t(kRecs))
-          ok = mbar_wait(&S.done[sg % kRecs], ((sg / kRecs) - 1) & 1u, wait_ns);
+        if (ok && sg >= recs) ok = mbar_wait(&S.done[sg % recs], ((sg / recs) - 1) & 1u, wait_ns);
       }
       if (!ok) {
         if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
@@ -324,16 +318,16 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
       uint32_t t = 0;
       if (lane == 0) t = atomicAdd(&a.ctrl->ticket, 1u);
       t = __shfl_sync(FULL, t, 0);
-      const uint64_t c0 = uint64_t(t) * kTicketChunks;
+      const uint64_t c0 = uint64_t(t) * group;
       // field, position and rate header of each chunk of the group (loads issued together)
-      FieldInfo* fis[kTicketChunks];
-      uint64_t hbs[kTicketChunks];
+      FieldInfo* fis[kMaxTicketChunks];
+      uint64_t hbs[kMaxTicketChunks];
 #pragma unroll
-      for (int g = 0; g < kTicketChunks; ++g) {
+      for (int g = 0; g < kMaxTicketChunks; ++g) {
         const uint64_t c = c0 + g;
         fis[g] = nullptr;
         hbs[g] = 0;
-        if (c < total) {
+        if (uint32_t(g) < group && c < total) {
           FieldInfo* fi = single ? a.fields : a.fields + a.chunk_field[c];
           fis[g] = fi;
           const uint64_t tile0 = (c - fi->chunk_first) * kDChunkTiles;
@@ -344,9 +338,10 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
       bool end = false;
       uint64_t prev_lc = 0;
 #pragma unroll
-      for (int g = 0; g < kTicketChunks; ++g) {
+      for (int g = 0; g < kMaxTicketChunks; ++g) {
+        if (uint32_t(g) >= group) break;
         const uint32_t sg = seq + g;
-        const int r = int(sg % kRecs);
+        const int r = int(sg % recs);
         ChunkRec& q = S.rec[r];
         const uint64_t c = c0 + g;
         if (end) continue;
@@ -425,8 +420,8 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
     uint32_t oldest = 0;  // the oldest chunk whose bytes are not yet known to be released
     uint64_t prev_excl = 0, prev_tot = 0;  // the previous record's chunk: offset and bytes
     for (uint32_t seq = 0;; ++seq) {
-      const int r = int(seq % kRecs);
-      if (!mbar_wait(&S.fetched[r], (seq / kRecs) & 1u, wait_ns)) {
+      const int r = int(seq % recs);
+      if (!mbar_wait(&S.fetched[r], (seq / recs) & 1u, wait_ns)) {
         if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
         return;
       }
@@ -471,8 +466,8 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
       const uint32_t need = valid ? (uint32_t(src - a0) + tot + 15u) & ~15u : 0u;
       uint32_t start = head;
       if ((start & (kRingBytes - 1)) + need > kRingBytes) start += kRingBytes - (start & (kRingBytes - 1));
-      // Chunks seq - kRecs and older are decoded: the header warp reused their records.
-      while (oldest + uint32_t(kRecs) <= seq) freed = S.ring_end[oldest++ % kRecs];
+      // Chunks seq - recs and older are decoded: the header warp reused their records.
+      while (oldest + recs <= seq) freed = S.ring_end[oldest++ % recs];
       bool space = true;
       while (start + need - freed > kRingBytes) {
         if (oldest == seq) {  // nothing in flight: the skipped end of the ring is free too
@@ -480,11 +475,11 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
           break;
         }
         // wait for the oldest chunk in flight; its record is not reused before it is done
-        if (!mbar_wait(&S.done[oldest % kRecs], (oldest / kRecs) & 1u, wait_ns)) {
+        if (!mbar_wait(&S.done[oldest % recs], (oldest / recs) & 1u, wait_ns)) {
           space = false;
           break;
         }
-        freed = S.ring_end[oldest % kRecs];
+        freed = S.ring_end[oldest % recs];
         ++oldest;
       }
       if (!space) {
@@ -521,8 +516,8 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
   const uint32_t obuf = smem_u32(S.out[warp]);
   bool good = true;
   for (uint32_t seq = 0;; ++seq) {
-    const int r = int(seq % kRecs);
-    if (!mbar_wait(&S.full[r], (seq / kRecs) & 1u, wait_ns)) {
+    const int r = int(seq % recs);
+    if (!mbar_wait(&S.full[r], (seq / recs) & 1u, wait_ns)) {
       if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
       break;
     }
@@ -610,9 +605,12 @@ LaunchCfg decompress_cfg() {
   });
 }
 
-void launch_decompress(const KernelArgs& a, cudaStream_t st, DecompressKind kind) {
+void launch_decompress(const KernelArgs& args, cudaStream_t st, DecompressKind kind) {
   const LaunchCfg c = decompress_cfg();
   const int g = sched_grid(c, kSchedDecompress);
+  KernelArgs a = args;
+  a.ticket_chunks = uint32_t(g_schedule.d_ticket_chunks);
+  a.records = uint32_t(g_schedule.d_records);
   if (kind == kDecompressAny)
     fsz_decompress_kernel<true, false><<<g, kThreads, c.smem, st>>>(a);
   else if (kind == kDecompressPrezeroed)

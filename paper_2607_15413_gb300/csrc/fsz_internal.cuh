@@ -139,6 +139,10 @@ struct KernelArgs {
   // per variant), from which the encoding pass selects
   const uint32_t* given_costs = nullptr;
   uint64_t given_T = 0;
+  // work assignment (from the schedule, set by the launch functions)
+  uint32_t ticket_chunks = 1;  // consecutive chunks per ticket
+  uint32_t ticket_lead = 1;    // compression: tickets taken ahead of the compute warps
+  uint32_t records = 0;        // decompression: chunks in flight per CTA
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -547,9 +551,22 @@ struct DeviceCfgCache {
 
 // Persistent CTAs per SM chosen by fsz_set_schedule (0 = as many as fit), per kernel.
 enum { kSchedStats = 0, kSchedCompress = 1, kSchedDecompress = 2 };
-extern int g_sched[3];
+// Work assignment of the persistent kernels (set through fsz_set_schedule*; none of it
+// changes a stream): CTAs per SM (0 = as many as fit) and, for compression and
+// decompression, how many consecutive 32-tile chunks one ticket hands a CTA. Compression
+// also sets how many tickets ahead of its compute warps a CTA takes, decompression how
+// many chunks a CTA holds between ticket and decode.
+constexpr int kMaxTicketChunks = 4;
+constexpr int kMaxCompressLead = 3;
+constexpr int kMaxDecRecords = 16;
+struct Schedule {
+  int ctas[3];
+  int c_ticket_chunks, c_ticket_lead;
+  int d_ticket_chunks, d_records;
+};
+extern Schedule g_schedule;
 inline int sched_grid(const LaunchCfg& c, int which) {
-  const int want = g_sched[which];
+  const int want = g_schedule.ctas[which];
   const int per = (want > 0 && want < c.per) ? want : c.per;
   return c.sms * (per > 0 ? per : 1);
 }

@@ -35,10 +35,19 @@ EXPORTS = ["fsz_compress_bound", "fsz_workspace_bytes", "fsz_batch_workspace_byt
            "fsz_decompress_batched", "fsz_check", "fsz_check_batched", "fsz_read_header",
            "fsz_set_test_hooks", "fsz_version", "fsz_compress_noalloc",
            "fsz_graph_compress_batched", "fsz_graph_decompress_batched", "fsz_graph_launch",
-           "fsz_graph_destroy", "fsz_set_schedule", "fsz_get_schedule_limits",
+           "fsz_graph_destroy", "fsz_set_schedule", "fsz_get_schedule_limits", "fsz_set_schedule_ex",
+           "fsz_get_schedule",
            "fsz_server_request_cost", "fsz_server_create", "fsz_server_submit", "fsz_server_poll",
            "fsz_server_submit_many", "fsz_server_release_many", "fsz_server_release", "fsz_server_get_stats", "fsz_server_stop", "fsz_server_destroy", "fsz_copy_device"]
 REQ_COMPRESS, REQ_DECOMPRESS = 0, 1
+# fsz_schedule, in its field order
+SCHEDULE_FIELDS = ("stats_ctas_per_sm", "compress_ctas_per_sm", "decompress_ctas_per_sm",
+                   "compress_ticket_chunks", "compress_ticket_lead", "decompress_ticket_chunks",
+                   "decompress_records")
+
+
+class FszSchedule(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint32) for name in SCHEDULE_FIELDS] + [("reserved", ctypes.c_uint32)]
 
 
 class FszDims(ctypes.Structure):
@@ -187,6 +196,10 @@ def lib():
             L.fsz_set_schedule.restype = i32
             L.fsz_get_schedule_limits.argtypes = [P, P, P, P]
             L.fsz_get_schedule_limits.restype = i32
+            L.fsz_set_schedule_ex.argtypes = [P]
+            L.fsz_set_schedule_ex.restype = i32
+            L.fsz_get_schedule.argtypes = [P]
+            L.fsz_get_schedule.restype = i32
             L.fsz_version.argtypes = []
             L.fsz_version.restype = ctypes.c_char_p
             L.fsz_server_request_cost.argtypes = [P]
@@ -329,6 +342,23 @@ def fsz_graph_destroy(g) -> None:
 def fsz_set_schedule(stats_ctas_per_sm: int, compress_ctas_per_sm: int,
                      decompress_ctas_per_sm: int) -> int:
     return lib().fsz_set_schedule(stats_ctas_per_sm, compress_ctas_per_sm, decompress_ctas_per_sm)
+
+
+def fsz_set_schedule_ex(schedule: dict | None) -> int:
+    """Installs a full schedule (a dict with the SCHEDULE_FIELDS keys; missing keys keep
+    the schedule in force), or the defaults for None. Returns the status."""
+    if schedule is None:
+        return lib().fsz_set_schedule_ex(None)
+    cur = fsz_get_schedule()
+    cur.update({k: int(v) for k, v in schedule.items() if k in SCHEDULE_FIELDS})
+    sc = FszSchedule(*[cur[k] for k in SCHEDULE_FIELDS], 0)
+    return lib().fsz_set_schedule_ex(ctypes.byref(sc))
+
+
+def fsz_get_schedule() -> dict:
+    sc = FszSchedule()
+    _check(lib().fsz_get_schedule(ctypes.byref(sc)), "fsz_get_schedule")
+    return {k: int(getattr(sc, k)) for k in SCHEDULE_FIELDS}
 
 
 def fsz_get_schedule_limits():

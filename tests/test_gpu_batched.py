@@ -135,21 +135,52 @@ def test_graph_replays_batched_calls(fszlib, oracle):
             assert np.array_equal(dbatch.output(i).cpu().numpy().view(np.uint32), ref.view(np.uint32))
 
 
-@pytest.mark.parametrize("sched", [(1, 1, 1), (2, 2, 2), (0, 0, 0)])
+SCHEDULES = [
+    None,                                                                  # the defaults
+    dict(stats_ctas_per_sm=1, compress_ctas_per_sm=1, decompress_ctas_per_sm=1),
+    dict(stats_ctas_per_sm=2, compress_ctas_per_sm=2, decompress_ctas_per_sm=2),
+    dict(compress_ticket_chunks=1, compress_ticket_lead=1, decompress_ticket_chunks=1,
+         decompress_records=2),                                            # smallest items
+    dict(compress_ticket_chunks=4, compress_ticket_lead=3, decompress_ticket_chunks=4,
+         decompress_records=8),                                            # largest items
+    dict(compress_ctas_per_sm=1, compress_ticket_chunks=3, compress_ticket_lead=1,
+         decompress_ctas_per_sm=1, decompress_ticket_chunks=2, decompress_records=16),
+]
+
+
+@pytest.mark.parametrize("sched", SCHEDULES)
 def test_schedules_give_identical_streams(fszlib, oracle, sched):
+    """Every schedule (CTAs per SM, chunks per ticket, ticket lead, chunks in flight)
+    gives the oracle's stream and reconstruction, for one field (with a ragged end) and
+    for a batch of fields of several sizes, some a few chunks long."""
     dev = _dev()
     lim = fszlib.fsz_get_schedule_limits()
     assert lim["compress"] >= 1 and lim["decompress"] >= 1 and lim["sms"] > 0
     x = inputs.particles(3 * (1 << 20) + 77, seed=9, ncenters=500)
     ref = oracle.compress(x, 1e-4, 1)
+    rng = np.random.default_rng(21)
+    fields = [(torch.from_numpy(inputs.sinusoids(int(n), seed=int(n) % 97)).to(dev), (int(n),),
+               fszlib.EB_REL, rel)
+              for n, rel in zip(rng.integers(1, 40 * 8192, 12), [1e-2, 1e-3, 1e-4] * 4)]
     try:
-        assert fszlib.fsz_set_schedule(*sched) == fszlib.OK
+        assert fszlib.fsz_set_schedule_ex(sched) == fszlib.OK
         sb, nb = fszlib.compress(torch.from_numpy(x).to(dev), 1e-4, 1)
         assert sb.cpu().numpy().tobytes() == ref
         y = fszlib.decompress(sb, n=x.size).cpu().numpy()
         assert np.array_equal(y.view(np.uint32), oracle.decompress(ref).view(np.uint32))
+        cb = fszlib.CompressBatch(fields, dev)
+        assert cb.run() == fszlib.OK and cb.status()[0] == fszlib.OK
+        sizes = cb.sizes.cpu().tolist()
+        streams = [cb.stream(i, sizes) for i in range(len(fields))]
+        for i, (f, _, _, rel) in enumerate(fields):
+            assert streams[i].cpu().numpy().tobytes() == oracle.compress(f.cpu().numpy(), rel, 1), i
+        db = fszlib.DecompressBatch(streams, [f.numel() for f, *_ in fields], dev)
+        assert db.run() == fszlib.OK and db.status()[0] == fszlib.OK
+        for i, (f, *_) in enumerate(fields):
+            ref_i = oracle.decompress(streams[i].cpu().numpy().tobytes())
+            assert np.array_equal(db.output(i).cpu().numpy().view(np.uint32), ref_i.view(np.uint32)), i
     finally:
-        fszlib.fsz_set_schedule(0, 0, 0)
+        fszlib.fsz_set_schedule_ex(None)
 
 
 def test_config4_all_512_fields_against_the_oracle(fszlib, oracle):

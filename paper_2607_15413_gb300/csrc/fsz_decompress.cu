@@ -554,20 +554,31 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
         const uint32_t tmask = __ballot_sync(FULL, write_tile && (lane & 7) == 0);
         __syncwarp();
         const uint32_t e0 = uint32_t(kQuadTiles * qd) * kTile;  // the quad's first element
+        if (tmask == 0x01010101u && e0 + kQuadTiles * kTile <= cnt) {
+          // every tile of the quad is written in full: no per-store guards
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const uint32_t P = uint32_t(32 * j + lane);   // piece: row P >> 3, column P & 7
-          const uint32_t rw = P >> 3;
-          const float4 val = lds128(obuf + rw * 128u + (((P & 7u) ^ (rw & 7u)) << 4));
-          const uint32_t e = e0 + 4 * P;
-          if (!((tmask >> (8 * (rw >> 3))) & 1u)) continue;  // (a tile not written)
-          if (e + 4 <= cnt) {
-            *reinterpret_cast<float4*>(dout + e) = val;
-          } else {
-            const float vals[4] = {val.x, val.y, val.z, val.w};
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t P = uint32_t(32 * j + lane);   // piece: row P >> 3, column P & 7
+            const uint32_t rw = P >> 3;
+            const float4 val = lds128(obuf + rw * 128u + (((P & 7u) ^ (rw & 7u)) << 4));
+            *reinterpret_cast<float4*>(dout + e0 + 4 * P) = val;
+          }
+        } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-              if (e + i < cnt) dout[e + i] = vals[i];
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t P = uint32_t(32 * j + lane);
+            const uint32_t rw = P >> 3;
+            const float4 val = lds128(obuf + rw * 128u + (((P & 7u) ^ (rw & 7u)) << 4));
+            const uint32_t e = e0 + 4 * P;
+            if (!((tmask >> (8 * (rw >> 3))) & 1u)) continue;  // (a tile not written)
+            if (e + 4 <= cnt) {
+              *reinterpret_cast<float4*>(dout + e) = val;
+            } else {
+              const float vals[4] = {val.x, val.y, val.z, val.w};
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                if (e + i < cnt) dout[e + i] = vals[i];
+            }
           }
         }
         __syncwarp();  // the buffer is read before the next quad overwrites it

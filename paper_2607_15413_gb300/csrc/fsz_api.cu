@@ -104,9 +104,8 @@ fsz_status prepare_one(const float* d_in, fsz_dims dims, fsz_eb_mode mode, doubl
   if (st != FSZ_OK) return st;
   call.desc.out_bytes = d_out_bytes;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(d_ws, 0, call.L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
   const KernelArgs a = make_args(d_ws, call.L);
-  launch_setup_compress(a, call.desc, s);
+  launch_setup_compress(a, call.desc, call.L.chunk_cap, s);  // (clears the workspace it uses)
   if (call.desc.nchunks > 0) launch_stats(a, s);
   return launched();
 }
@@ -121,7 +120,6 @@ fsz_status decompress_one(const void* d_in, uint64_t in_bytes, float* d_out,
   const WsLayout L = ws_layout((out_capacity_elems + kTile - 1) / kTile, 1);
   if (ws_bytes < L.bytes) return FSZ_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaMemsetAsync(d_ws, 0, L.bytes, s) != cudaSuccess) return FSZ_ERR_CUDA;
   const KernelArgs a = make_args(d_ws, L);
   launch_setup_decompress(a, static_cast<const uint8_t*>(d_in), in_bytes, d_out, out_capacity_elems,
                           L.chunk_cap, s);

@@ -58,7 +58,7 @@ constexpr int kMaxQuadOut = kQuadTiles * kMaxTileBytes;
 constexpr int kRing = FSZ_RING_BYTES;              // logical ring bytes per compute warp
 constexpr int kRingAlloc = kRing + kMaxQuadOut;    // + room for a run that crosses the end
 #ifndef FSZ_LOOKBACK_K
-#define FSZ_LOOKBACK_K 4
+#define FSZ_LOOKBACK_K 2
 #endif
 constexpr int kLookbackPerLane = FSZ_LOOKBACK_K;   // lookback window: 32 K flags
 constexpr uint32_t kNone = 0xffffffffu;

@@ -45,7 +45,7 @@ static_assert((kRingBytes & (kRingBytes - 1)) == 0 && kRingBytes >= kMaxChunkRin
 
 constexpr uint32_t kNoneChunk = 0xffffffffu;
 #ifndef FSZ_DEC_LOOKBACK_K
-#define FSZ_DEC_LOOKBACK_K 4
+#define FSZ_DEC_LOOKBACK_K 1
 #endif
 constexpr int kLookbackPerLane = FSZ_DEC_LOOKBACK_K;  // lookback window: 32 K flags
 // The schedule's work assignment (kernel arguments): a ticket hands a CTA ticket_chunks

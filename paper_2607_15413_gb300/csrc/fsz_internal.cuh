@@ -590,7 +590,9 @@ void launch_cost_pass(const KernelArgs& a, int variant, uint32_t* costs, cudaStr
 enum DecompressKind { kDecompressFull = 0, kDecompressAny = 1, kDecompressPrezeroed = 2 };
 void launch_decompress(const KernelArgs& a, cudaStream_t st,
                        DecompressKind kind = kDecompressFull);
-void launch_setup_compress(const KernelArgs& a, const FieldInfo& fi, cudaStream_t st);
+// Single-field set-up (clears the control words, the field record and chunk_cap lookback
+// flags of the workspace, then fills in the field): no memset of the workspace needed.
+void launch_setup_compress(const KernelArgs& a, const FieldInfo& fi, uint64_t chunk_cap, cudaStream_t st);
 void launch_setup_decompress(const KernelArgs& a, const uint8_t* in, uint64_t in_bytes, float* out,
                              uint64_t cap_elems, uint64_t chunk_cap, cudaStream_t st);
 void launch_plan_compress(const KernelArgs& a, const fsz_cfield* d_fields, uint32_t nfields,

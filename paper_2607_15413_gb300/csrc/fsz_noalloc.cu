@@ -105,7 +105,7 @@ extern "C" fsz_status fsz_compress_noalloc(const float* d_in, fsz_dims dims, fsz
   a.flags = reinterpret_cast<uint64_t*>(base + L.flags_off);
   a.skip_chunk = ~uint64_t(0);
   a.timeout_ns = kDefaultTimeoutNs;
-  launch_setup_compress(a, desc, s);
+  launch_setup_compress(a, desc, L.chunk_cap, s);
   if (desc.nchunks > 0) {
     launch_stats(a, s);
     launch_compress(a, s);

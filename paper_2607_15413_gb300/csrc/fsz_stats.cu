@@ -120,9 +120,10 @@ __global__ void __launch_bounds__(kStatsThreads) fsz_stats_kernel(KernelArgs a) 
     my_items = 0;
   };
 
+  const bool single = a.ctrl->nfields == 1;  // (a single field's workspace has no chunk map)
   uint32_t cur_f = 0xffffffffu;
   for (uint64_t g = blockIdx.x; g < total; g += gridDim.x) {
-    const uint32_t f = a.chunk_field[g];
+    const uint32_t f = single ? 0u : a.chunk_field[g];
     if (f != cur_f) {
       if (cur_f != 0xffffffffu) flush(cur_f);
       cur_f = f;
@@ -261,8 +262,30 @@ __device__ void finish_empty_field(Ctrl* ctrl, FieldInfo* fi) {
 
 // One-field set-up for compression: the descriptor is validated on the host, so this
 // copies it into the workspace.
-__global__ void fsz_setup_compress_kernel(KernelArgs a, FieldInfo desc) {
-  if (threadIdx.x != 0) return;
+// Set-up of a single-field call: thread 0 of CTA 0 clears the control words and the field
+// record and fills them in; every other thread clears the lookback flags (nflags words),
+// so that the call needs no separate memset.
+constexpr int kSetupThreads = 256;
+static_assert(sizeof(Ctrl) <= 256 && sizeof(Ctrl) % 8 == 0 && sizeof(FieldInfo) % 8 == 0,
+              "control words and field record clear as 8-byte words");
+
+__device__ __forceinline__ bool setup_clear(const KernelArgs& a, uint64_t nflags) {
+  const uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    uint64_t* c = reinterpret_cast<uint64_t*>(a.ctrl);
+    for (uint32_t k = 0; k < sizeof(Ctrl) / 8; ++k) c[k] = 0;
+    uint64_t* f = reinterpret_cast<uint64_t*>(a.fields);
+    for (uint32_t k = 0; k < sizeof(FieldInfo) / 8; ++k) f[k] = 0;
+    return true;
+  }
+  const uint64_t nthreads = uint64_t(gridDim.x) * blockDim.x - 1;
+  for (uint64_t k = t - 1; k < nflags; k += nthreads) a.flags[k] = 0;
+  return false;
+}
+
+__global__ void __launch_bounds__(kSetupThreads) fsz_setup_compress_kernel(KernelArgs a, FieldInfo desc,
+                                                                           uint64_t nflags) {
+  if (!setup_clear(a, nflags)) return;
   FieldInfo* fi = a.fields;
   fi->in = desc.in; fi->out = desc.out; fi->cap = desc.cap; fi->out_bytes = desc.out_bytes;
   fi->n = desc.n; fi->T = desc.T;
@@ -276,9 +299,10 @@ __global__ void fsz_setup_compress_kernel(KernelArgs a, FieldInfo desc) {
   if (desc.n == 0) finish_empty_field(a.ctrl, fi);
 }
 
-__global__ void fsz_setup_decompress_kernel(KernelArgs a, const uint8_t* in, uint64_t in_bytes,
-                                            float* out, uint64_t cap_elems, uint64_t chunk_cap) {
-  if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(kSetupThreads) fsz_setup_decompress_kernel(
+    KernelArgs a, const uint8_t* in, uint64_t in_bytes, float* out, uint64_t cap_elems,
+    uint64_t chunk_cap, uint64_t nflags) {
+  if (!setup_clear(a, nflags)) return;
   FieldInfo* fi = a.fields;
   uint32_t st = plan_dfield(fi, in, in_bytes, out, cap_elems);
   if (st == FSZ_OK && fi->nchunks > chunk_cap) st = FSZ_ERR_WORKSPACE;
@@ -289,6 +313,12 @@ __global__ void fsz_setup_decompress_kernel(KernelArgs a, const uint8_t* in, uin
   fi->chunk_first = 0;
   a.ctrl->nfields = 1;
   a.ctrl->total_chunks = fi->nchunks;
+}
+
+// CTAs of a set-up launch: one plus one per 2048 flag words, at most 152.
+inline int setup_grid(uint64_t nflags) {
+  const uint64_t g = 1 + nflags / (8 * kSetupThreads);
+  return int(g < 152 ? g : 152);
 }
 
 constexpr int kPlanThreads = 1024;
@@ -396,13 +426,16 @@ void launch_stats(const KernelArgs& a, cudaStream_t st) {
   fsz_stats_kernel<<<sched_grid(stats_cfg(), kSchedStats), kStatsThreads, 0, st>>>(a);
 }
 
-void launch_setup_compress(const KernelArgs& a, const FieldInfo& fi, cudaStream_t st) {
-  fsz_setup_compress_kernel<<<1, 32, 0, st>>>(a, fi);
+void launch_setup_compress(const KernelArgs& a, const FieldInfo& fi, uint64_t chunk_cap, cudaStream_t st) {
+  const uint64_t nflags = kFlagStride * chunk_cap;
+  fsz_setup_compress_kernel<<<setup_grid(nflags), kSetupThreads, 0, st>>>(a, fi, nflags);
 }
 
 void launch_setup_decompress(const KernelArgs& a, const uint8_t* in, uint64_t in_bytes, float* out,
                              uint64_t cap_elems, uint64_t chunk_cap, cudaStream_t st) {
-  fsz_setup_decompress_kernel<<<1, 32, 0, st>>>(a, in, in_bytes, out, cap_elems, chunk_cap);
+  const uint64_t nflags = kFlagStride * chunk_cap;
+  fsz_setup_decompress_kernel<<<setup_grid(nflags), kSetupThreads, 0, st>>>(a, in, in_bytes, out,
+                                                                            cap_elems, chunk_cap, nflags);
 }
 
 void launch_plan_compress(const KernelArgs& a, const fsz_cfield* d_fields, uint32_t nfields,

@@ -55,8 +55,10 @@ constexpr int kCtasPerSm = FSZ_COMPRESS_CTAS;
 constexpr int kQuadElems = kQuadTiles * kTile;     // 1024
 constexpr int kQuadBytes = 4 * kQuadElems;         // 4096: a warp's staging buffer
 constexpr int kMaxQuadOut = kQuadTiles * kMaxTileBytes;
-constexpr int kRing = FSZ_RING_BYTES;              // logical ring bytes per compute warp
-constexpr int kRingAlloc = kRing + kMaxQuadOut;    // + room for a run that crosses the end
+// Ring bytes per compute warp. A run is contiguous: one that would run past the end
+// starts at the ring's start instead, and the bytes it skips count as its own until it
+// is placed.
+constexpr int kRingAlloc = FSZ_RING_BYTES + kMaxQuadOut;
 #ifndef FSZ_LOOKBACK_K
 #define FSZ_LOOKBACK_K 2
 #endif
@@ -77,7 +79,7 @@ constexpr uint32_t kHostSleepNs = FSZ_HOST_SLEEP_NS;
 constexpr uint32_t kResolverSleepNs = FSZ_RESOLVER_SLEEP_NS;
 constexpr uint32_t kComputeSleepNs = FSZ_COMPUTE_SLEEP_NS;
 static_assert(kCChunkTiles == kWarps * kQuadTiles, "a chunk is one quad per compute warp");
-static_assert(kRing >= kMaxQuadOut, "a worst-case quad fits the ring");
+static_assert(kRingAlloc >= 2 * kMaxQuadOut, "worst-case quads fit the ring");
 static_assert(kRingAlloc % 16 == 0 && kQuadBytes % 1024 == 0, "alignment of the buffers");
 static_assert(kWarps <= 32, "one lane per quad in the chunk scan");
 
@@ -107,7 +109,8 @@ struct __align__(1024) CompressSmem {
   uint64_t set_excl[kSets];                       // a resolved chunk's exclusive offset
   uint32_t qlen[kSets][kWarps];                   // each warp's quad run: bytes,
   uint32_t qoff[kSets][kWarps];                   // ... offset inside the chunk,
-  uint32_t qpos[kSets][kWarps];                   // ... position in the warp's ring
+  uint32_t qpos[kSets][kWarps];                   // ... position in the warp's ring,
+  uint32_t qalloc[kSets][kWarps];                 // ... ring bytes it holds (run + skipped end)
   uint32_t set_tot[kSets];
   uint32_t done_cnt[kSets];
   uint32_t ring_tail[kWarps];                     // ring bytes given back, per compute warp
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
           __syncwarp();
           if (lane < kWarps) {
             __threadfence_block();
-            st_release_cta(&S.ring_tail[lane], S.ring_tail[lane] + S.qlen[b][lane]);
+            st_release_cta(&S.ring_tail[lane], S.ring_tail[lane] + S.qalloc[b][lane]);
           }
           __syncwarp();
           ++p;
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
   const uint32_t buf = smem_u32(S.stage[warp]);
   const uint32_t ring_u32 = smem_u32(S.ring[warp]);
   uint32_t head = 0;  // bytes this warp has written to its ring (warp-uniform, wrapping)
-  uint32_t pos = 0;   // ... its logical write position, head mod kRing
+  uint32_t pos = 0;   // ... the position in the ring where the next run goes
 
   // The quad of a chunk that this warp loads: valid elements (0: nothing to load).
   auto quad_valid = [&](const ChunkInfo& ci) -> uint32_t {
@@ -701,9 +704,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       }
     }
     // room for the run in the ring (logical bytes), given back by the host as it places
-    if (any && kRing - (head - ld_acquire_cta(&S.ring_tail[warp])) < qlen) {
+    // the run's place: contiguous, from the ring's start if it would run past the end
+    uint32_t skip = 0;
+    if (pos + qlen > uint32_t(kRingAlloc)) {
+      skip = uint32_t(kRingAlloc) - pos;
+      pos = 0;
+    }
+    const uint32_t alloc = skip + qlen;  // (pos stays head mod kRingAlloc)
+    if (any && uint32_t(kRingAlloc) - (head - ld_acquire_cta(&S.ring_tail[warp])) < alloc) {
       const uint64_t deadline = globaltimer_ns() + wait_ns;
-      while (kRing - (head - ld_acquire_cta(&S.ring_tail[warp])) < qlen) {
+      while (uint32_t(kRingAlloc) - (head - ld_acquire_cta(&S.ring_tail[warp])) < alloc) {
         __nanosleep(kComputeSleepNs);
         if (globaltimer_ns() > deadline) {
           if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
@@ -717,10 +727,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       if (P.mu_slot) sts32(run + P.mu_off, __float_as_uint(__int2float_rn(P.mu)));
       encode_block(P, run + P.off);
     }
-    if (lane == 0) S.qpos[b][warp] = pos;
-    head += qlen;
+    if (lane == 0) {
+      S.qpos[b][warp] = pos;
+      S.qalloc[b][warp] = alloc;
+    }
+    head += alloc;
     pos += qlen;
-    if (pos >= uint32_t(kRing)) pos -= kRing;
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.encoded[b]);  // this warp's run of the chunk is in its ring
   }

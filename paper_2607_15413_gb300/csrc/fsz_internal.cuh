@@ -322,18 +322,6 @@ __device__ __forceinline__ uint32_t shl_fma(uint32_t x, int k) {
   return uint32_t(mad_s32(int(x), 1 << k, 0));
 }
 
-// 8x8 bit-matrix transpose of the 64-bit word hi:lo: bit 8r + c <-> bit 8c + r.
-// Three delta swaps (Hacker's Delight, "transposing a bit matrix"), on 32-bit halves; the
-// left shifts are multiplies (shl_fma).
-__device__ __forceinline__ void transpose8x8(uint32_t& lo, uint32_t& hi) {
-  uint32_t t;
-  t = (lo ^ (lo >> 7)) & 0x00AA00AAu; lo = lo ^ t ^ shl_fma(t, 7);
-  t = (hi ^ (hi >> 7)) & 0x00AA00AAu; hi = hi ^ t ^ shl_fma(t, 7);
-  t = (lo ^ (lo >> 14)) & 0x0000CCCCu; lo = lo ^ t ^ shl_fma(t, 14);
-  t = (hi ^ (hi >> 14)) & 0x0000CCCCu; hi = hi ^ t ^ shl_fma(t, 14);
-  t = (lo ^ shl_fma(hi, 4)) & 0xF0F0F0F0u; lo ^= t; hi ^= (t >> 4);
-}
-
 // The bit-plane network of both kernels. X[k] (k = 0..7) holds 4 bytes, byte m of X[k]
 // standing for bits 0..7 of some element e(m, k); three delta swaps between register
 // pairs (k, k ^ 2^t), t = 0, 1, 2, exchange bit t of the register index k with bit t of
@@ -369,17 +357,6 @@ __device__ __forceinline__ uint32_t scan_step_up(uint32_t v, int o) {
       : "+r"(v)
       : "r"(o), "n"((32 - kWidth) << 8));
   return v;
-}
-
-
-// 4x4 byte transpose across the 4 lanes of a group (t = lane & 3): afterwards byte k of
-// lane t's word is byte t of lane k's word. Two exchange steps (xor 1, xor 2).
-__device__ __forceinline__ uint32_t transpose4x4_bytes(uint32_t w, int t) {
-  uint32_t x = __shfl_xor_sync(0xffffffffu, w, 1);
-  w = __byte_perm(w, x, (t & 1) ? 0x3715 : 0x6240);
-  x = __shfl_xor_sync(0xffffffffu, w, 2);
-  w = __byte_perm(w, x, (t & 2) ? 0x3276 : 0x5410);
-  return w;
 }
 
 __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {

@@ -282,7 +282,7 @@ fsz_status fsz_get_schedule_limits(uint32_t* stats_max, uint32_t* compress_max,
  * tickets up to `compress_ticket_lead` chunks (1-3) ahead of its compute warps;
  * decompression keeps up to `decompress_records` chunks (2 x ticket chunks .. 16) between
  * ticket and decode per CTA. `reserved` must be 0. Defaults: CTAs 0 (as many as fit),
- * compression 2 chunks per ticket with lead 2, decompression 3 chunks per ticket and 12
+ * compression 2 chunks per ticket with lead 2, decompression 4 chunks per ticket and 16
  * records. Read by every later call of this process at launch (a CUDA graph keeps the
  * schedule it was captured with). Used by the autotuner; not thread-safe. */
 typedef struct fsz_schedule {

@@ -11,7 +11,23 @@ static_assert(sizeof(fsz_dims) == 32 && sizeof(fsz_cfield) == 80 && sizeof(fsz_d
               "C ABI struct layouts");
 
 namespace fsz {
-Schedule g_schedule = {{0, 0, 0}, 2, 2, 3, 12};
+// The default schedule: CTAs per SM (0 = as many as fit), compression's chunks per ticket
+// and ticket lead, decompression's chunks per ticket and chunks in flight.
+#ifndef FSZ_DEF_C_CHUNKS
+#define FSZ_DEF_C_CHUNKS 2
+#endif
+#ifndef FSZ_DEF_C_LEAD
+#define FSZ_DEF_C_LEAD 2
+#endif
+#ifndef FSZ_DEF_D_CHUNKS
+#define FSZ_DEF_D_CHUNKS 4
+#endif
+#ifndef FSZ_DEF_D_RECORDS
+#define FSZ_DEF_D_RECORDS 16
+#endif
+constexpr Schedule kDefaultSchedule = {{0, 0, 0}, FSZ_DEF_C_CHUNKS, FSZ_DEF_C_LEAD, FSZ_DEF_D_CHUNKS,
+                                       FSZ_DEF_D_RECORDS};
+Schedule g_schedule = kDefaultSchedule;
 }
 
 // A captured batched call (fsz_graph in the C ABI).
@@ -355,7 +371,7 @@ fsz_status fsz_set_schedule(uint32_t stats_ctas_per_sm, uint32_t compress_ctas_p
 
 fsz_status fsz_set_schedule_ex(const fsz_schedule* sc) {
   if (sc == nullptr) {  // the defaults
-    g_schedule = Schedule{{0, 0, 0}, 2, 2, 3, 12};
+    g_schedule = kDefaultSchedule;
     return FSZ_OK;
   }
   if (sc->stats_ctas_per_sm > 64 || sc->compress_ctas_per_sm > 64 || sc->decompress_ctas_per_sm > 64 ||

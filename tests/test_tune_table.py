@@ -39,8 +39,8 @@ def test_apply_default_installs_the_table(fszlib):
 
 
 DEFAULTS = {"stats_ctas_per_sm": 0, "compress_ctas_per_sm": 0, "decompress_ctas_per_sm": 0,
-            "compress_ticket_chunks": 2, "compress_ticket_lead": 2, "decompress_ticket_chunks": 3,
-            "decompress_records": 12}
+            "compress_ticket_chunks": 2, "compress_ticket_lead": 2, "decompress_ticket_chunks": 4,
+            "decompress_records": 16}
 
 
 def test_schedule_round_trip_and_defaults(fszlib):

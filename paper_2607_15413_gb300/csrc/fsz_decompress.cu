@@ -40,8 +40,7 @@ constexpr int kQuadTiles = 4;  // tiles per decode warp and iteration
 // the 16-byte boundary below its start, rounded up to 16 bytes.
 constexpr uint32_t kMaxChunkRingBytes = kDChunkTiles * kMaxDecTileBytes + 32;
 static_assert(kDChunkTiles <= 32, "one lane per tile in the chunk scan");
-static_assert((kRingBytes & (kRingBytes - 1)) == 0 && kRingBytes >= kMaxChunkRingBytes,
-              "the ring is a power of two that holds the largest chunk");
+static_assert(kRingBytes % 16 == 0 && kRingBytes >= kMaxChunkRingBytes, "the ring holds the largest chunk");
 
 constexpr uint32_t kNoneChunk = 0xffffffffu;
 #ifndef FSZ_DEC_LOOKBACK_K
@@ -415,8 +414,8 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
     // ---------------------------------------------------------------- loader warp
     // Ring positions count bytes modulo 2^32: head = where the next payload goes, freed =
     // how far the decoded chunks have released. Chunks take and release space in ticket
-    // order, so the bytes in use are head - freed.
-    uint32_t head = 0, freed = 0;
+    // order, so the bytes in use are head - freed; pos is head's place in the ring.
+    uint32_t head = 0, freed = 0, pos = 0;
     uint32_t oldest = 0;  // the oldest chunk whose bytes are not yet known to be released
     uint64_t prev_excl = 0, prev_tot = 0;  // the previous record's chunk: offset and bytes
     for (uint32_t seq = 0;; ++seq) {
@@ -464,8 +463,11 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
       // ring space: the payload from a0, rounded up to 16 bytes, in one piece (a payload
       // that would run past the ring's end starts at the ring's start instead)
       const uint32_t need = valid ? (uint32_t(src - a0) + tot + 15u) & ~15u : 0u;
-      uint32_t start = head;
-      if ((start & (kRingBytes - 1)) + need > kRingBytes) start += kRingBytes - (start & (kRingBytes - 1));
+      uint32_t start = head, phys = pos;
+      if (pos + need > kRingBytes) {
+        start += kRingBytes - pos;
+        phys = 0;
+      }
       // Chunks seq - recs and older are decoded: the header warp reused their records.
       while (oldest + recs <= seq) freed = S.ring_end[oldest++ % recs];
       bool space = true;
@@ -487,8 +489,8 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
         return;
       }
       head = start + need;
+      pos = phys + need;
       if (lane == 0) S.ring_end[r] = head;
-      const uint32_t phys = start & (kRingBytes - 1);
       if (lane == 0) {
         if (!valid && !skip) set_error(a.ctrl, fi, FSZ_ERR_CORRUPT);
         q.pay = phys + uint32_t(src - a0);

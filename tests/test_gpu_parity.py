@@ -460,3 +460,34 @@ def test_field_past_2p32_elements(fszlib, oracle):
         rh, rd = oracle.compress_tiles(xs, p.r, 0, t1 - t0)
         assert sb[64 + 8 * t0:64 + 8 * t1].cpu().numpy().tobytes() == rh, t0
         assert sb[data0 + int(offs[t0]):data0 + int(offs[t1])].cpu().numpy().tobytes() == rd, t0
+
+
+def test_workspace_reused_across_calls(fszlib, oracle):
+    """One workspace for a run of calls of different sizes, a batched call among them: a
+    single-field call clears what it uses in its set-up kernel (control words, field
+    record, lookback flags), so whatever an earlier call left there does not leak into its
+    stream or reconstruction."""
+    dev = _cuda()
+    big = 3 * (1 << 20) + 4097
+    ws = fszlib.Workspace(big, dev)
+    rng = np.random.default_rng(33)
+    sizes = [big, 1000, 70_000, 8192 * 41 + 5, 257, big - 12345]
+    for k, n in enumerate(sizes):
+        x = inputs.sinusoids(n, seed=100 + k) if k % 2 else rng.normal(0, 1, n).astype(np.float32)
+        ref = oracle.compress(x, 1e-3, oracle.REL)
+        sb, nb = fszlib.compress(torch.from_numpy(x).to(dev), 1e-3, fszlib.EB_REL, ws=ws)
+        assert sb.cpu().numpy().tobytes() == ref, (k, n)
+        y = fszlib.decompress(sb, n=n, ws=ws).cpu().numpy()
+        assert np.array_equal(y.view(np.uint32), oracle.decompress(ref).view(np.uint32)), (k, n)
+        if k == 2:  # a batched call through the same memory in between
+            bytes_needed = fszlib.fsz_batch_workspace_bytes(2 * 50_000, 2)
+            assert bytes_needed <= ws.bytes
+            fields = [(torch.from_numpy(inputs.sinusoids(50_000, seed=7 + j)).to(dev), (50_000,),
+                       fszlib.EB_REL, 1e-2) for j in range(2)]
+            cb = fszlib.CompressBatch(fields, dev)
+            cb.ws, cb.ws_bytes = ws.buf, ws.bytes  # through the shared workspace
+            assert cb.run() == fszlib.OK and cb.status()[0] == fszlib.OK
+            sizes_b = cb.sizes.cpu().tolist()
+            for j, (f, *_) in enumerate(fields):
+                assert cb.stream(j, sizes_b).cpu().numpy().tobytes() == oracle.compress(
+                    f.cpu().numpy(), 1e-2, oracle.REL), j

@@ -875,6 +875,31 @@ def main():
     bytes_step = 2 * len(jobs) * 4 * n
     value, ms_step = job_throughput(world, bytes_step, total_ms / args.steps)
 
+    # Each kernel alone right after an L2 flush (a 256 MiB scratch write), so that neither
+    # its input nor its stream can come from L2; median of 3 per job, outside the timed steps.
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    enc_fl, dec_fl = [[] for _ in jobs], [[] for _ in jobs]
+    for rep in range(3):
+        for j, (name, x, rel) in enumerate(jobs):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            st = L.fsz_compress_prepare(x.data_ptr(), dims, fsz.EB_REL, rel, outs[j].data_ptr(), cap,
+                                        nbytes[j:].data_ptr(), ws.data_ptr(), wsb, sp)
+            flush.fill_(rep + 1)
+            e[0].record(stream)
+            st |= L.fsz_compress_encode(x.data_ptr(), dims, fsz.EB_REL, rel, outs[j].data_ptr(), cap,
+                                        nbytes[j:].data_ptr(), ws.data_ptr(), wsb, sp)
+            e[1].record(stream)
+            flush.fill_(rep + 2)
+            e[2].record(stream)
+            st |= L.fsz_decompress(outs[j].data_ptr(), cap, recon.data_ptr(), n, ws.data_ptr(), wsb, sp)
+            e[3].record(stream)
+            if st:
+                raise fsz.FszError(st, "L2-flushed run")
+            torch.cuda.synchronize(dev)
+            enc_fl[j].append(e[0].elapsed_time(e[1]))
+            dec_fl[j].append(e[2].elapsed_time(e[3]))
+    del flush
+
     # e2e: the same calls with pinned host buffers. Copies run on their own streams (one
     # per direction) and overlap the kernels, as a pipeline feeding the GPU would:
     # inputs in -> compress -> streams out and back in -> decompress -> reconstructions out.
@@ -1024,7 +1049,10 @@ def main():
                         # the same over the mean step instead of the median one
                         "compress_gbs_mean": 4 * n / statistics.mean(comp_ms[j]) / 1e6,
                         "encode_kernel_gbs_mean": 4 * n / statistics.mean(enc_ms[j]) / 1e6,
-                        "decompress_gbs_mean": 4 * n / statistics.mean(dec_ms[j]) / 1e6})
+                        "decompress_gbs_mean": 4 * n / statistics.mean(dec_ms[j]) / 1e6,
+                        # each kernel alone after a 256 MiB L2 flush (median of 3)
+                        "encode_kernel_hbm_gbs_l2flushed": (4 * n + sizes[j]) / med(enc_fl[j]) / 1e6,
+                        "decompress_hbm_gbs_l2flushed": (4 * n + sizes[j]) / med(dec_fl[j]) / 1e6})
     njobs, nfields_main = len(jobs), len(fields)
     clock_summary = clocks.summary()
     ablation = None
@@ -1053,7 +1081,8 @@ def main():
                            f"subset: fields {args.fields}, REL {args.rels} of: " + WORKLOAD,
                            "n_per_field": n, "fields": nfields_main, "rels": rels,
                            "parallelism": f"replicas x{world} (no data-path collective)",
-                           "l2": "inputs 512 MiB > L2; streams read back after >= 2.5 GB of traffic",
+                           "l2": "inputs 512 MiB > L2; streams read back after >= 2.5 GB of traffic; "
+                                 "jobs[].*_l2flushed: each kernel alone after a 256 MiB scratch write",
                            "schedule": main_schedule},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches_per_step * args.steps,

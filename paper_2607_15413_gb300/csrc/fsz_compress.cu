@@ -13,12 +13,14 @@
 //                  quad as one contiguous run into the warp's ring in shared memory
 //                  (step 5). The last warp to size a chunk scans the quads' sizes and
 //                  publishes the chunk's aggregate flag before any warp has encoded it;
-//   resolver warp  looks back for each chunk's exclusive byte offset (step 4, Sec. 4.4)
-//                  and publishes the inclusive prefix;
+//   resolver warp  looks back for each chunk's exclusive byte offset (step 4, Sec. 4.4),
+//                  publishes the inclusive prefix, and copies the runs of the first
+//                  kResolverRuns compute warps to the stream before handing the chunk to
+//                  the host warp;
 //   host warp      takes a ticket per chunk just ahead of its use and leaves the chunk's
 //                  parameters in one of kSets chunk slots; and places each chunk, once it
-//                  is resolved and encoded, by copying the compute warps' runs from their
-//                  rings to the stream and giving the ring space back.
+//                  is resolved and encoded, by copying the other compute warps' runs from
+//                  their rings to the stream and giving the ring space back.
 // The rings decouple encoding from the device-wide scan: chunks finish out of ticket order
 // across the grid, and a chunk's offset is known only when every earlier chunk has
 // published its size. Keeping the placement out of the compute warps keeps them within 96
@@ -35,6 +37,12 @@ constexpr int kWarps = kCChunkTiles / kQuadTiles;  // compute warps per CTA
 constexpr int kHostWarp = kWarps;                  // tickets and placement
 constexpr int kResolverWarp = kWarps + 1;
 constexpr int kThreads = (kWarps + 2) * 32;
+#ifndef FSZ_RESOLVER_RUNS
+#define FSZ_RESOLVER_RUNS 4
+#endif
+// Placement split: the resolver copies the runs of compute warps 0 .. kResolverRuns - 1 of
+// each chunk it resolves, before handing the chunk to the host, which copies the others.
+constexpr int kResolverRuns = FSZ_RESOLVER_RUNS;
 #ifndef FSZ_COMPRESS_SETS
 #define FSZ_COMPRESS_SETS 12
 #endif
@@ -505,7 +513,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
               if (lane == 0) set_error(a.ctrl, ci.fi, FSZ_ERR_CAPACITY);
             } else {
               uint8_t* const base = ci.out + ci.data_base + excl;
-              for (int w = 0; w < kWarps; ++w) {
+              for (int w = kResolverRuns; w < kWarps; ++w) {
                 const uint32_t nw = S.qlen[b][w] >> 2;
                 const uint32_t src = smem_u32(S.ring[w]) + S.qpos[b][w];
                 uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.qoff[b][w]);
@@ -528,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
           }
           // the runs are read: their ring space goes back to the compute warps
           __syncwarp();
-          if (lane < kWarps) {
+          if (lane >= kResolverRuns && lane < kWarps) {
             __threadfence_block();
             st_release_cta(&S.ring_tail[lane], S.ring_tail[lane] + S.qalloc[b][lane]);
           }
@@ -588,6 +596,41 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
       prev_excl = excl;
       prev_tot = S.set_tot[b];
       prev_held = (flags & kInfoSkip) != 0;
+      if constexpr (kResolverRuns > 0) {
+        // copy this warp's share of the runs once they are all encoded (the host copies
+        // the rest after the chunk is handed over)
+        if (!mbar_wait_idle(&S.encoded[b], (seq / kSets) & 1u, wait_ns, kResolverSleepNs)) {
+          if (lane == 0) set_error(a.ctrl, nullptr, FSZ_ERR_TIMEOUT);
+          return;
+        }
+        const uint32_t tot = S.set_tot[b];
+        if ((flags & (kInfoOk | kInfoSkip)) == kInfoOk && ci.data_base + excl + tot <= ci.cap) {
+          uint8_t* const base = ci.out + ci.data_base + excl;
+          for (int w = 0; w < kResolverRuns; ++w) {
+            const uint32_t nw = S.qlen[b][w] >> 2;
+            const uint32_t src = smem_u32(S.ring[w]) + S.qpos[b][w];
+            uint32_t* dst = reinterpret_cast<uint32_t*>(base + S.qoff[b][w]);
+            for (uint32_t q0 = 0; q0 < nw; q0 += 128) {
+              uint32_t v[4];
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const uint32_t q = q0 + 32 * k + lane;
+                if (q < nw) v[k] = lds32(src + 4 * q);
+              }
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const uint32_t q = q0 + 32 * k + lane;
+                if (q < nw) dst[q] = v[k];
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane < kResolverRuns) {
+          __threadfence_block();
+          st_release_cta(&S.ring_tail[lane], S.ring_tail[lane] + S.qalloc[b][lane]);
+        }
+      }
       __syncwarp();
       if (lane == 0) {
         S.set_excl[b] = excl;

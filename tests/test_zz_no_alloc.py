@@ -54,3 +54,46 @@ def test_noalloc_rejects_fields_beyond_its_scratch(fszlib):
     dims = fszlib.make_dims((1 << 14, 1 << 14, 2))   # 2^29 elements > FSZ_NOALLOC_MAX_ELEMS
     st = fszlib.fsz_compress_noalloc(0x10000, dims, fszlib.EB_REL, 1e-3, 0x20000, 1 << 40, 0, 0, 0)
     assert st == fszlib.ERR_WORKSPACE
+
+
+def test_noalloc_inside_a_global_mode_capture(fszlib):
+    """The entry point's use inside a stream capture in global mode: after one call outside
+    any capture (the device's one-time set-up), a captured call replays to the regular
+    entry point's stream, and replays again after the input changes in place."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    dev = torch.device("cuda:0")
+    n = 24 * 8192 + 321
+    x = torch.from_numpy(inputs.particles(n, seed=13, ncenters=64)).to(dev)
+    x2 = torch.from_numpy(inputs.sinusoids(n, seed=14)).to(dev)
+    cap = fszlib.fsz_compress_bound(n)
+    out = torch.zeros(cap, dtype=torch.uint8, device=dev)
+    nb = torch.zeros(1, dtype=torch.int64, device=dev)
+    status = torch.full((1,), 12345, dtype=torch.int32, device=dev)
+    dims = fszlib.make_dims((n,))
+
+    def call(stream_ptr):
+        return fszlib.fsz_compress_noalloc(x.data_ptr(), dims, fszlib.EB_REL, 1e-3, out.data_ptr(), cap,
+                                           nb.data_ptr(), status.data_ptr(), stream_ptr)
+
+    assert call(torch.cuda.current_stream().cuda_stream) == fszlib.OK   # outside any capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=side, capture_error_mode="global"):
+        st = call(torch.cuda.current_stream().cuda_stream)
+    assert st == fszlib.OK
+    for src in (None, x2):
+        if src is not None:
+            x.copy_(src)                  # the graph reads the same input pointer
+        ref, k = fszlib.compress(x, 1e-3, fszlib.EB_REL)
+        out.zero_()
+        nb.zero_()
+        status.fill_(12345)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(status.item()) == fszlib.OK
+        assert int(nb.item()) == k
+        assert out[:k].cpu().numpy().tobytes() == ref.cpu().numpy().tobytes()

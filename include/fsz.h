@@ -281,10 +281,14 @@ fsz_status fsz_get_schedule_limits(uint32_t* stats_max, uint32_t* compress_max,
  * offset follows from the previous one without a lookback (Sec. 4.4). Compression takes
  * tickets up to `compress_ticket_lead` chunks (1-3) ahead of its compute warps;
  * decompression keeps up to `decompress_records` chunks (2 x ticket chunks .. 16) between
- * ticket and decode per CTA. `reserved` must be 0. Defaults: CTAs 0 (as many as fit),
- * compression 2 chunks per ticket with lead 2, decompression 4 chunks per ticket and 16
- * records. Read by every later call of this process at launch (a CUDA graph keeps the
- * schedule it was captured with). Used by the autotuner; not thread-safe. */
+ * ticket and decode per CTA. A launch whose chunks would give fewer than
+ * `min_tickets_per_cta` tickets per CTA (0-64) at the requested ticket size takes tickets
+ * of fewer chunks (down to 1), so that small fields and small batches still spread over
+ * every CTA; 0 keeps the requested size at every launch size. Defaults: CTAs 0 (as many
+ * as fit), compression 2 chunks per ticket with lead 2, decompression 4 chunks per ticket
+ * and 16 records, 4 tickets per CTA. Read by every later call of this process at launch
+ * (a CUDA graph keeps the schedule it was captured with). Used by the autotuner; not
+ * thread-safe. */
 typedef struct fsz_schedule {
   uint32_t stats_ctas_per_sm;
   uint32_t compress_ctas_per_sm;
@@ -293,7 +297,7 @@ typedef struct fsz_schedule {
   uint32_t compress_ticket_lead;
   uint32_t decompress_ticket_chunks;
   uint32_t decompress_records;
-  uint32_t reserved;
+  uint32_t min_tickets_per_cta;
 } fsz_schedule;
 /* Installs `s` (NULL: the defaults). FSZ_ERR_INVALID_ARG if a field is out of range; the
  * schedule in force is then unchanged. */

@@ -12,7 +12,8 @@ static_assert(sizeof(fsz_dims) == 32 && sizeof(fsz_cfield) == 80 && sizeof(fsz_d
 
 namespace fsz {
 // The default schedule: CTAs per SM (0 = as many as fit), compression's chunks per ticket
-// and ticket lead, decompression's chunks per ticket and chunks in flight.
+// and ticket lead, decompression's chunks per ticket and chunks in flight, and the tickets
+// per CTA below which a launch takes smaller tickets.
 #ifndef FSZ_DEF_C_CHUNKS
 #define FSZ_DEF_C_CHUNKS 2
 #endif
@@ -25,8 +26,11 @@ namespace fsz {
 #ifndef FSZ_DEF_D_RECORDS
 #define FSZ_DEF_D_RECORDS 16
 #endif
+#ifndef FSZ_DEF_MIN_TICKETS
+#define FSZ_DEF_MIN_TICKETS 4
+#endif
 constexpr Schedule kDefaultSchedule = {{0, 0, 0}, FSZ_DEF_C_CHUNKS, FSZ_DEF_C_LEAD, FSZ_DEF_D_CHUNKS,
-                                       FSZ_DEF_D_RECORDS};
+                                       FSZ_DEF_D_RECORDS, FSZ_DEF_MIN_TICKETS};
 Schedule g_schedule = kDefaultSchedule;
 }
 
@@ -379,7 +383,7 @@ fsz_status fsz_set_schedule_ex(const fsz_schedule* sc) {
       sc->compress_ticket_lead < 1 || sc->compress_ticket_lead > uint32_t(kMaxCompressLead) ||
       sc->decompress_ticket_chunks < 1 || sc->decompress_ticket_chunks > uint32_t(kMaxTicketChunks) ||
       sc->decompress_records < 2 * sc->decompress_ticket_chunks ||
-      sc->decompress_records > uint32_t(kMaxDecRecords) || sc->reserved != 0)
+      sc->decompress_records > uint32_t(kMaxDecRecords) || sc->min_tickets_per_cta > 64)
     return FSZ_ERR_INVALID_ARG;
   g_schedule.ctas[kSchedStats] = int(sc->stats_ctas_per_sm);
   g_schedule.ctas[kSchedCompress] = int(sc->compress_ctas_per_sm);
@@ -388,6 +392,7 @@ fsz_status fsz_set_schedule_ex(const fsz_schedule* sc) {
   g_schedule.c_ticket_lead = int(sc->compress_ticket_lead);
   g_schedule.d_ticket_chunks = int(sc->decompress_ticket_chunks);
   g_schedule.d_records = int(sc->decompress_records);
+  g_schedule.min_tickets = int(sc->min_tickets_per_cta);
   return FSZ_OK;
 }
 
@@ -400,7 +405,7 @@ fsz_status fsz_get_schedule(fsz_schedule* out) {
   out->compress_ticket_lead = uint32_t(g_schedule.c_ticket_lead);
   out->decompress_ticket_chunks = uint32_t(g_schedule.d_ticket_chunks);
   out->decompress_records = uint32_t(g_schedule.d_records);
-  out->reserved = 0;
+  out->min_tickets_per_cta = uint32_t(g_schedule.min_tickets);
   return FSZ_OK;
 }
 

@@ -454,7 +454,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) fsz_compress_kernel(Kern
     //    compute warp has encoded its quad: each warp's run is copied from its ring to the
     //    stream and the ring space is given back.
     const bool single = a.ctrl->nfields == 1;
-    const uint32_t group = a.ticket_chunks, lead = a.ticket_lead;
+    const uint32_t group = launch_ticket_chunks(a.ticket_chunks, a.min_tickets, total, gridDim.x);
+    const uint32_t lead = a.ticket_lead;
     uint32_t seq_t = 0, p = 0, end_seq = kNone;
     uint64_t deadline = globaltimer_ns() + wait_ns;
     for (;;) {
@@ -813,6 +814,7 @@ void launch_compress(const KernelArgs& args, cudaStream_t st, CompressKind kind)
   KernelArgs a = args;
   a.ticket_chunks = uint32_t(g_schedule.c_ticket_chunks);
   a.ticket_lead = uint32_t(g_schedule.c_ticket_lead);
+  a.min_tickets = uint32_t(g_schedule.min_tickets);
   if (kind == kCompressFeatures)
     fsz_compress_kernel<false, true><<<g, kThreads, c.smem, st>>>(a);
   else if (kind == kCompressGiven)

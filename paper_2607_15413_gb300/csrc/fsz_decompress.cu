@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(kThreads, 2) fsz_decompress_kernel(KernelArgs 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint64_t total = a.ctrl->total_chunks;
   const uint64_t wait_ns = 4 * a.timeout_ns;
-  const uint32_t group = a.ticket_chunks, recs = a.records;
+  const uint32_t group = launch_ticket_chunks(a.ticket_chunks, a.min_tickets, total, gridDim.x);
+  const uint32_t recs = a.records;
 
   if (tid == 0) {
     for (int k = 0; k < kMaxRecs; ++k) {
@@ -624,6 +625,7 @@ void launch_decompress(const KernelArgs& args, cudaStream_t st, DecompressKind k
   KernelArgs a = args;
   a.ticket_chunks = uint32_t(g_schedule.d_ticket_chunks);
   a.records = uint32_t(g_schedule.d_records);
+  a.min_tickets = uint32_t(g_schedule.min_tickets);
   if (kind == kDecompressAny)
     fsz_decompress_kernel<true, false><<<g, kThreads, c.smem, st>>>(a);
   else if (kind == kDecompressPrezeroed)

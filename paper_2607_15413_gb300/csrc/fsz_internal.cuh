@@ -143,7 +143,19 @@ struct KernelArgs {
   uint32_t ticket_chunks = 1;  // consecutive chunks per ticket
   uint32_t ticket_lead = 1;    // compression: tickets taken ahead of the compute warps
   uint32_t records = 0;        // decompression: chunks in flight per CTA
+  uint32_t min_tickets = 0;    // tickets per CTA below which a launch takes smaller ones
 };
+
+// Chunks per ticket for one launch: the schedule's, or fewer (down to 1) while the launch
+// would hand out fewer than min_tickets tickets per CTA, so that a launch of few chunks
+// still spreads them over the grid and balances its end (min_tickets 0: always the
+// schedule's). Every CTA of the launch computes the same value.
+__device__ __forceinline__ uint32_t launch_ticket_chunks(uint32_t want, uint32_t min_tickets,
+                                                         uint64_t total_chunks, uint32_t ctas) {
+  uint32_t g = want;
+  while (g > 1 && total_chunks < uint64_t(ctas) * g * min_tickets) --g;
+  return g;
+}
 
 // ------------------------------------------------------------------ device helpers
 
@@ -540,6 +552,7 @@ struct Schedule {
   int ctas[3];
   int c_ticket_chunks, c_ticket_lead;
   int d_ticket_chunks, d_records;
+  int min_tickets;
 };
 extern Schedule g_schedule;
 inline int sched_grid(const LaunchCfg& c, int which) {

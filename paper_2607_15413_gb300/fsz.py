@@ -43,11 +43,11 @@ REQ_COMPRESS, REQ_DECOMPRESS = 0, 1
 # fsz_schedule, in its field order
 SCHEDULE_FIELDS = ("stats_ctas_per_sm", "compress_ctas_per_sm", "decompress_ctas_per_sm",
                    "compress_ticket_chunks", "compress_ticket_lead", "decompress_ticket_chunks",
-                   "decompress_records")
+                   "decompress_records", "min_tickets_per_cta")
 
 
 class FszSchedule(ctypes.Structure):
-    _fields_ = [(name, ctypes.c_uint32) for name in SCHEDULE_FIELDS] + [("reserved", ctypes.c_uint32)]
+    _fields_ = [(name, ctypes.c_uint32) for name in SCHEDULE_FIELDS]
 
 
 class FszDims(ctypes.Structure):
@@ -351,7 +351,7 @@ def fsz_set_schedule_ex(schedule: dict | None) -> int:
         return lib().fsz_set_schedule_ex(None)
     cur = fsz_get_schedule()
     cur.update({k: int(v) for k, v in schedule.items() if k in SCHEDULE_FIELDS})
-    sc = FszSchedule(*[cur[k] for k in SCHEDULE_FIELDS], 0)
+    sc = FszSchedule(*[cur[k] for k in SCHEDULE_FIELDS])
     return lib().fsz_set_schedule_ex(ctypes.byref(sc))
 
 

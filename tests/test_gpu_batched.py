@@ -135,24 +135,32 @@ def test_graph_replays_batched_calls(fszlib, oracle):
             assert np.array_equal(dbatch.output(i).cpu().numpy().view(np.uint32), ref.view(np.uint32))
 
 
+# These fields are a few hundred chunks at most, so under the default min_tickets_per_cta
+# every launch here takes 1-chunk tickets; the entries with min_tickets_per_cta=0 keep the
+# multi-chunk tickets they name.
 SCHEDULES = [
     None,                                                                  # the defaults
+    dict(min_tickets_per_cta=0),                                           # default tickets held
     dict(stats_ctas_per_sm=1, compress_ctas_per_sm=1, decompress_ctas_per_sm=1),
     dict(stats_ctas_per_sm=2, compress_ctas_per_sm=2, decompress_ctas_per_sm=2),
     dict(compress_ticket_chunks=1, compress_ticket_lead=1, decompress_ticket_chunks=1,
          decompress_records=2),                                            # smallest items
     dict(compress_ticket_chunks=4, compress_ticket_lead=3, decompress_ticket_chunks=4,
-         decompress_records=8),                                            # largest items
+         decompress_records=8, min_tickets_per_cta=0),                     # largest items
     dict(compress_ctas_per_sm=1, compress_ticket_chunks=3, compress_ticket_lead=1,
-         decompress_ctas_per_sm=1, decompress_ticket_chunks=2, decompress_records=16),
+         decompress_ctas_per_sm=1, decompress_ticket_chunks=2, decompress_records=16,
+         min_tickets_per_cta=0),
+    dict(compress_ticket_chunks=4, decompress_ticket_chunks=4, decompress_records=8,
+         min_tickets_per_cta=1),                                           # partly shrunk
 ]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES)
 def test_schedules_give_identical_streams(fszlib, oracle, sched):
-    """Every schedule (CTAs per SM, chunks per ticket, ticket lead, chunks in flight)
-    gives the oracle's stream and reconstruction, for one field (with a ragged end) and
-    for a batch of fields of several sizes, some a few chunks long."""
+    """Every schedule (CTAs per SM, chunks per ticket, ticket lead, chunks in flight, the
+    tickets per CTA below which tickets shrink) gives the oracle's stream and
+    reconstruction, for one field (with a ragged end) and for a batch of fields of several
+    sizes, some a few chunks long."""
     dev = _dev()
     lim = fszlib.fsz_get_schedule_limits()
     assert lim["compress"] >= 1 and lim["decompress"] >= 1 and lim["sms"] > 0

@@ -10,7 +10,8 @@ Every case draws, from one seeded generator:
   small noise, alternating signs, a ramp on a large offset);
 - a bound: REL, or ABS at the same relative magnitude, from 10^-4.5 to 10^-1.5 of the
   range (refusals, e.g. a bound too small for the float32 step, must match the oracle's);
-- a launch schedule (CTAs per SM, chunks per ticket, ticket lead, chunks in flight);
+- a launch schedule (CTAs per SM, chunks per ticket, ticket lead, chunks in flight, the
+  tickets per CTA below which tickets shrink);
 - a feature set (the ablation's switched-off features) for one case in three.
 
 The bar is the parity tests' one: the stream byte for byte, the reconstruction bit for
@@ -94,7 +95,8 @@ def soak_cases(seed=2607):
                      decompress_ctas_per_sm=int(rng.integers(0, 3)),
                      compress_ticket_chunks=tc, compress_ticket_lead=int(rng.integers(1, 4)),
                      decompress_ticket_chunks=dc,
-                     decompress_records=int(rng.integers(2 * dc, 17)))
+                     decompress_records=int(rng.integers(2 * dc, 17)),
+                     min_tickets_per_cta=int(rng.choice([0, 1, 4])))
         cases.append(dict(index=i, cls=cls, x=x, dims=tuple(int(d) for d in dims), mode=mode,
                           eb=eb, features_off=off, sched=sched))
     return cases

@@ -40,7 +40,7 @@ def test_apply_default_installs_the_table(fszlib):
 
 DEFAULTS = {"stats_ctas_per_sm": 0, "compress_ctas_per_sm": 0, "decompress_ctas_per_sm": 0,
             "compress_ticket_chunks": 2, "compress_ticket_lead": 2, "decompress_ticket_chunks": 4,
-            "decompress_records": 16}
+            "decompress_records": 16, "min_tickets_per_cta": 4}
 
 
 def test_schedule_round_trip_and_defaults(fszlib):
@@ -49,7 +49,7 @@ def test_schedule_round_trip_and_defaults(fszlib):
         assert fsz.fsz_get_schedule() == DEFAULTS
         want = {"stats_ctas_per_sm": 3, "compress_ctas_per_sm": 1, "decompress_ctas_per_sm": 2,
                 "compress_ticket_chunks": 4, "compress_ticket_lead": 3, "decompress_ticket_chunks": 1,
-                "decompress_records": 2}
+                "decompress_records": 2, "min_tickets_per_cta": 0}
         assert fsz.fsz_set_schedule_ex(want) == fsz.OK
         assert fsz.fsz_get_schedule() == want
         # the three-count call changes the CTA counts only
@@ -64,13 +64,14 @@ def test_schedule_round_trip_and_defaults(fszlib):
     {"compress_ticket_chunks": 0}, {"compress_ticket_chunks": 5}, {"compress_ticket_lead": 0},
     {"compress_ticket_lead": 4}, {"decompress_ticket_chunks": 0}, {"decompress_ticket_chunks": 5},
     {"decompress_ticket_chunks": 4, "decompress_records": 7}, {"decompress_records": 17},
-    {"decompress_records": 1}, {"stats_ctas_per_sm": 65}, {"compress_ctas_per_sm": 65}])
+    {"decompress_records": 1}, {"stats_ctas_per_sm": 65}, {"compress_ctas_per_sm": 65},
+    {"min_tickets_per_cta": 65}])
 def test_schedule_out_of_range_is_refused(fszlib, bad):
     try:
         assert fsz.fsz_set_schedule_ex(None) == fsz.OK
         assert fsz.fsz_set_schedule_ex(bad) == fsz.ERR_INVALID_ARG
         assert fsz.fsz_get_schedule() == DEFAULTS                    # unchanged
-        sc = fsz.FszSchedule(*[DEFAULTS[k] for k in fsz.SCHEDULE_FIELDS], 1)  # reserved != 0
+        sc = fsz.FszSchedule(*[bad.get(k, DEFAULTS[k]) for k in fsz.SCHEDULE_FIELDS])  # the raw call
         assert fszlib.lib().fsz_set_schedule_ex(ctypes.byref(sc)) == fsz.ERR_INVALID_ARG
     finally:
         fsz.fsz_set_schedule_ex(None)
